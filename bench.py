@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the B300 shortwave Monte Carlo tracer.
+
+Workload: the LES-like cumulus scene (256 x 256 x 128 cells, dx = dy = 50 m,
+dz = 25 m, seeded sum of 400 Gaussian blobs, 20 % cloud cover), solar zenith
+30 deg, 256 photons per column (16.8 M photons per step), TOA flux 1000 W m^-2.
+
+One step is the whole hot path through the C ABI, with inputs resident in HBM:
+optics derivation + validation, surface check, majorant grid, tally reset,
+the persistent transport kernel, and the FP64 output fields (3D absorption,
+surface direct/diffuse, top upward flux, heating rate) into device buffers.
+
+Prints one JSON line. `value` is majorant collision events per second over
+the timed steps (CUDA events on the tracer's stream); `e2e` is the same metric
+through the C ABI with host buffers (host->device inputs and device->host
+outputs inside the timed region). `roofline` uses the transport kernel's own
+CUDA-event duration. `cpu_baseline` times the FP64 CPU oracle on a bounded
+sample of the same scene.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "photon collision events/s & wall time to target RMS GHI/heating error, denoised vs plain"
+UNIT = "events/s"
+SZA, AZ, F0 = 30.0, 0.0, 1000.0
+SEED = 20220926
+COARSE = (4, 4, 4)
+# Algorithmic bytes of the transport kernel: 16 B optics record + 16 B FP64
+# tally read-modify-write per majorant event, 4 B majorant per coarse crossing.
+BYTES_PER_EVENT, BYTES_PER_CROSSING = 32, 4
+KERNELS_PER_STEP = 9   # derive, albedo check, majorant, transport, 4 field sums, heating rate
+PROFILE = os.path.join(ROOT, "profiles", "trace_kernel_cumulus256.md")
+
+
+def parse():
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--ppc", type=int, default=256, help="photons per column per step")
+    p.add_argument("--sza", type=float, default=SZA)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-ppc", type=int, default=16)
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload_config(args, world):
+    return {"workload": f"cumulus 256x256x128 (dx=dy=50 m, dz=25 m, 400 blobs, 20% cloud), "
+                        f"sza {args.sza:g}, {args.ppc} photons/column, {args.ppc * 65536} photons per GPU "
+                        f"per step, coarse grid {COARSE[0]}x{COARSE[1]}x{COARSE[2]}",
+            "photons_per_step": args.ppc * 65536 * world,
+            "l2": "inputs larger than L2: 168 MB optics + 134 MB derived records + 135 MB FP64 tallies",
+            "parallelism": f"photon ranges, {world} rank(s), no data-path collective"}
+
+
+# ---- clocks during the timed region ---------------------------------------------------
+
+class Clocks:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            self.sel = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            self.sel = str(device_index)
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.sel, "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) == 7:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[3:]) if v.lower() == "active"})
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("rt_device.cuh", "rt_kernels.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2208_05247_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it matches the source."""
+    try:
+        kv = {}
+        for line in open(PROFILE):
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                kv[k.strip()] = v.strip().strip("`")
+        if kv.get("source_hash") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ---- CPU oracle (baseline and reference arm) ------------------------------------------
+
+def oracle_sample(scene, ppc: int, seed: int):
+    import oracle
+    n = ppc * scene.ncol
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = oracle.trace(scene, SZA, AZ, F0, n, seed, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return r.totals, dt, cores
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2208_05247_b300 import scenes
+    scene = scenes.cumulus_scene(seed=1)
+    ppc = 1
+    for w in range(args.warmup):
+        oracle_sample(scene, ppc, SEED + w)
+    coll, photons, secs, cores = 0, 0, 0.0, 1
+    for k in range(args.steps):
+        tot, dt, cores = oracle_sample(scene, ppc, SEED + 100 + k)
+        coll += tot["collisions"]
+        photons += tot["photons"]
+        secs += dt
+    value = coll / secs
+    sample = (f"each step {ppc} photon/column ({ppc * scene.ncol} photons) of the benchmark scene; "
+              f"oracle collisions (analog: every collision is real)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "photons_per_s": photons / secs},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- our CUDA path --------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_2208_05247_b300 import build, rt, scenes
+    build.build()
+    scene = scenes.cumulus_scene(seed=1)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ncell, ncol = scene.ncell, scene.ncol
+    d_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in scene.fields()]
+    d_alb = torch.from_numpy(scene.albedo).to(dev)
+    d_out = {"abs3d": torch.empty(ncell, dtype=torch.float64, device=dev),
+             "hr": torch.empty(ncell, dtype=torch.float64, device=dev)}
+    for k in ("sfc_dir", "sfc_dif", "toa_up"):
+        d_out[k] = torch.empty(ncol, dtype=torch.float64, device=dev)
+    N = args.ppc * ncol
+    total = N * world
+    begin = N * rank
+
+    t = rt.Tracer(scene.nx, scene.ny, scene.nz, scene.dx, scene.dy, scene.dz, stream=stream)
+
+    def step(seed, ev=None, inputs=None, outputs=None):
+        src = inputs if inputs is not None else (d_in, d_alb)
+        out = outputs if outputs is not None else d_out
+        t.set_optics(*src[0])
+        t.set_surface(src[1])
+        t.build_accel(*COARSE)
+        t.reset()
+        if ev is not None:
+            ev[0].record(stream)
+        t.trace_range(args.sza, AZ, F0, begin, N, total, seed)
+        if ev is not None:
+            ev[1].record(stream)
+        rt.rt_fields(t.h, ncell, ncol, out["abs3d"], out["sfc_dir"], out["sfc_dif"], out["toa_up"])
+        rt.rt_heating_rate(t.h, ncell, out["hr"], 0)
+
+    for _ in range(max(1, args.warmup)):
+        step(SEED)
+    torch.cuda.synchronize()
+    ref_stats = t.stats()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    for k in range(args.steps):
+        step(SEED, evs[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    trace_ms = [a.elapsed_time(b) for a, b in evs]
+    st = t.stats()
+    assert st["events"] == ref_stats["events"], "event count changed between identical steps"
+    assert st["status"] == 0, "transport reported a capped photon"
+
+    events = st["events"]
+    crossings = st["crossings"]
+    ms_max, events_all = ms, events
+    if dist is not None:
+        v = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        ms_max = float(v.item())
+        e = torch.tensor([events], dtype=torch.float64, device=dev)
+        dist.all_reduce(e)
+        events_all = int(e.item())
+    value = events_all * args.steps / (ms_max / 1e3)
+
+    # transport kernel roofline (this rank)
+    tk = statistics.mean(trace_ms) / 1e3
+    alg_bytes = events * BYTES_PER_EVENT + crossings * BYTES_PER_CROSSING
+    peak, peak_src = peaks()
+    achieved = alg_bytes / tk / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": profiled_traffic(), "peak_source": peak_src,
+            "kernel": "trace_kernel<double>", "kernel_ms": 1e3 * tk,
+            "algorithmic_bytes_per_launch": alg_bytes}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in scene.fields()]
+        h_alb = torch.from_numpy(scene.albedo).pin_memory()
+        h_out = {k: torch.empty(v.numel(), dtype=torch.float64).pin_memory() for k, v in d_out.items()}
+        step(SEED, inputs=(h_in, h_alb), outputs=h_out)
+        torch.cuda.synchronize()
+        barrier()
+        k2 = max(3, args.steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            step(SEED, inputs=(h_in, h_alb), outputs=h_out)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        barrier()
+        if dist is not None:
+            v = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(v, op=dist.ReduceOp.MAX)
+            dt = float(v.item())
+        h2d = sum(a.numel() * 4 for a in h_in) + h_alb.numel() * 4
+        d2h = sum(v.numel() * 8 for v in h_out.values())
+        e2e = {"value": events_all * k2 / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * dt / k2}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        tot, dt, cores = oracle_sample(scene, args.cpu_sample_ppc, SEED + 7)
+        cpu = {"value": tot["collisions"] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_sample_ppc} photons/column ({tot['photons']} photons) of the benchmark "
+                         f"scene, {dt:.1f} s wall; oracle collisions are all real (analog tracer)",
+               "photons_per_s": tot["photons"] / dt}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args, world),
+            "photons_per_s": N * world * args.steps / (ms_max / 1e3),
+            "events_per_step": events_all, "real_scatter_fraction": st["scatters"] / max(1, events),
+            "trace_kernel_ms": 1e3 * tk, "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": KERNELS_PER_STEP * args.steps}
+    print(json.dumps(line), flush=True)
+    t.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * rt.h -- C ABI of the B300 shortwave Monte Carlo ray tracer.
+ *
+ * The method is that of Veerman, van Stratum & van Heerwaarden (2022),
+ * "Shallow cumulus convection over land in cloud-resolving simulations with a
+ * coupled ray tracer", Sec. 2.3 ("The ray tracer"): photons enter at the
+ * domain top, move by null-collision tracking over a coarse grid of maximum
+ * extinction, scatter by Rayleigh (gas) or Henyey-Greenstein (cloud) phase
+ * functions, lose weight by absorption at every event, are rescaled by
+ * Russian roulette below weight 0.5, reflect from a Lambertian surface, and
+ * are tallied into 3D absorption, upward flux at the domain top and surface
+ * direct and diffuse irradiance.
+ *
+ * Conventions used throughout
+ *   - Grids are [nz][ny][nx] with x fastest; 2D surface fields are [ny][nx].
+ *     x points east, y north, z up; cell (i,j,k) spans [i dx,(i+1) dx) x
+ *     [j dy,(j+1) dy) x [k dz,(k+1) dz). The domain is periodic in x and y, the
+ *     surface is z = 0 and the domain top z = nz dz.
+ *   - Angles are degrees. The solar zenith angle must lie in [0, 90). The
+ *     azimuth is clockwise from north and names where the sun stands (the
+ *     paper's "south-west" sun is 228.1), so photons travel along
+ *     (-sin sza sin az, -sin sza cos az, -cos sza).
+ *   - toa_flux is the solar flux normal to the beam [W m^-2]; the flux through
+ *     the horizontal domain top is toa_flux cos(sza).
+ *   - Output units: W m^-2 for surface and top fluxes, W m^-3 for absorption,
+ *     K day^-1 for heating rates.
+ *   - mem arguments say where a pointer lives: RT_HOST (pageable or pinned host
+ *     memory) or RT_DEVICE (device memory of the handle's GPU).
+ *
+ * Ownership and ordering
+ *   - A handle owns all device memory it allocates; rt_destroy frees it.
+ *   - Inputs are copied (host) or read (device) before the call returns to the
+ *     stream order, so the caller may free or overwrite them once the handle's
+ *     stream has passed the call.
+ *   - Every call is ordered on the handle's stream (rt_set_stream; default the
+ *     legacy default stream). Calls that write host memory synchronise it.
+ *   - A handle is not thread-safe; distinct handles may be used from distinct
+ *     threads.
+ *
+ * Errors
+ *   - Every int-returning call returns RT_OK (0) or a negative RT_E_* code and
+ *     records a message for rt_last_error() (thread-local).
+ *   - Conditions found on the device (an event budget exhausted) are recorded
+ *     in the handle's status and returned by rt_synchronize, rt_stats and
+ *     rt_fields; the kernels never trap and every loop in them is bounded.
+ */
+#ifndef RT_B300_H
+#define RT_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_scene *rt_handle;
+
+enum {
+    RT_OK = 0,
+    RT_E_INVAL = -1,   /* bad argument or invalid optical property */
+    RT_E_STATE = -2,   /* call made in the wrong order (e.g. trace before optics) */
+    RT_E_CUDA = -3,    /* CUDA runtime error */
+    RT_E_OOM = -4,     /* device allocation failed */
+    RT_E_BUDGET = -5   /* a photon hit the per-photon step cap; tallies are incomplete */
+};
+
+enum { RT_HOST = 0, RT_DEVICE = 1 };
+
+/* Choice of scatterer at a real scattering event. The paper (Sec. 2.3) gives
+ * the cloud probability as k_ext,cloud / k_ext; with separate gas and cloud
+ * single-scattering albedos the unbiased choice is k_sca,cloud / k_sca. */
+enum { RT_PCLD_SCATTERING = 0, RT_PCLD_EXTINCTION = 1 };
+
+/* Tally precision: FP64 global accumulators (default) or FP32 (precision study). */
+enum { RT_TALLY_FP64 = 0, RT_TALLY_FP32 = 1 };
+
+typedef struct {
+    int block_size;              /* threads per block of the transport kernel; 0 = 256 */
+    int blocks_per_sm;           /* resident blocks per SM; 0 = as many as fit */
+    int refill_chunk;            /* photon ids a warp takes from the queue at once; 0 = 32 */
+    uint32_t max_steps;          /* per-photon cap on events + cell crossings; 0 = 10,000,000 */
+    int pcld_mode;               /* RT_PCLD_*; applies from the next rt_set_optics */
+    int tally_precision;         /* RT_TALLY_*; applies from the next rt_reset_tallies */
+} rt_options;
+
+typedef struct {
+    uint64_t photons;            /* photons traced since the last reset */
+    uint64_t events;             /* majorant events (real scatterings + null collisions) */
+    uint64_t scatters;           /* real scattering events */
+    uint64_t crossings;          /* coarse-cell face crossings */
+    uint64_t surface_hits;
+    uint64_t roulette_kills;
+    uint64_t capped;             /* photons stopped by the step cap */
+    uint64_t max_events_photon;  /* largest event count of a single photon */
+    double energy_in;            /* W entering through the domain top */
+    double energy_toa_up;        /* W leaving through the domain top (from the tallies) */
+    double energy_atm_abs;       /* W absorbed in the atmosphere (from the tallies) */
+    double energy_sfc_abs;       /* W absorbed by the surface (from the tallies) */
+    double energy_created;       /* W added by roulette survivors (w -> 1) */
+    double energy_destroyed;     /* W removed by roulette kills */
+    double energy_capped;        /* W carried by photons stopped by the step cap */
+    int status;                  /* first device-side error (RT_OK or RT_E_BUDGET) */
+} rt_stats_t;
+
+/* Create a scene of nx*ny*nz cells of size dx*dy*dz metres on the current CUDA
+ * device. Sizes must be positive and nx*ny*nz < 2^31. Returns NULL on error
+ * (see rt_last_error). Allocates the derived optics, the tallies and the
+ * per-launch scratch (about 32 B per cell). */
+rt_handle rt_create(int nx, int ny, int nz, double dx, double dy, double dz);
+
+/* Free everything the handle owns. NULL is accepted. */
+int rt_destroy(rt_handle h);
+
+/* Order all following calls of this handle on `stream` (a cudaStream_t, e.g.
+ * torch.cuda.current_stream().cuda_stream); NULL selects the default stream. */
+int rt_set_stream(rt_handle h, void *stream);
+
+int rt_set_options(rt_handle h, const rt_options *opt);
+int rt_get_options(rt_handle h, rt_options *opt);
+
+/* Per-cell optics for one spectral quadrature point (Sec. 2.3: the tracer needs
+ * full-domain extinction, single-scattering albedo and asymmetry; gas and cloud
+ * are given separately). Five float arrays of nx*ny*nz values, layout
+ * [nz][ny][nx]: gas extinction [m^-1], gas single-scattering albedo, cloud
+ * extinction [m^-1], cloud single-scattering albedo, cloud asymmetry g.
+ * Validates (finite, extinction >= 0, albedos in [0,1], |g| < 1) and derives
+ * the per-cell record used by the transport kernel. Synchronises the stream to
+ * report RT_E_INVAL; after an error the handle holds no valid optics (rt_trace
+ * returns RT_E_STATE) until a call succeeds. Invalidates the acceleration grid. */
+int rt_set_optics(rt_handle h, const float *k_gas, const float *ssa_gas, const float *k_cld,
+                  const float *ssa_cld, const float *g_cld, int mem);
+
+/* Lambertian surface albedo per column (Sec. 2.3), nx*ny floats in [0,1]. */
+int rt_set_surface(rt_handle h, const float *albedo, int mem);
+
+/* Build the maximum-extinction acceleration grid (Sec. 2.3: a coarser grid whose
+ * cells hold the largest extinction of the fine cells they cover, used as the
+ * null-collision coefficient, without recursion). cx, cy, cz are the coarsening
+ * factors (fine cells per coarse cell); the last coarse cell along an axis
+ * covers the remainder. 0,0,0 selects 4,4,4 clipped to the grid. */
+int rt_build_accel(rt_handle h, int cx, int cy, int cz);
+
+/* Trace `photons` photons of one spectral quadrature point and ADD their
+ * contribution to the tallies (Sec. 2.3). Photon p starts in column
+ * p mod (nx*ny) (samples per pixel = photons / (nx*ny), Sec. 2.4) at a uniform
+ * position at the domain top, along the sun beam, with weight 1. Each photon
+ * carries toa_flux cos(sza) nx dx ny dy / photons watts, so calls for different
+ * quadrature points sum. `seed` keys the counter-based random streams: equal
+ * seeds and photon ids give equal histories. Requires optics, surface and an
+ * acceleration grid (RT_E_STATE otherwise). Asynchronous. */
+int rt_trace(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux,
+             uint64_t photons, uint64_t seed);
+
+/* As rt_trace for photon ids [photon_begin, photon_begin + photon_count) of a
+ * run of photons_total photons: disjoint ranges traced by separate calls (or
+ * separate GPUs) add up to the full run. */
+int rt_trace_range(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux,
+                   uint64_t photon_begin, uint64_t photon_count, uint64_t photons_total,
+                   uint64_t seed);
+
+/* Copy the accumulated fields out, normalised (Sec. 2.3 fluxes from mean
+ * weights; absorption per cell volume). abs3d: nx*ny*nz doubles [W m^-3], the
+ * sum of direct and diffuse absorption; sfc_dir, sfc_dif, toa_up: nx*ny doubles
+ * [W m^-2]. Any pointer may be NULL. With RT_HOST the call synchronises and
+ * returns the device status (RT_E_BUDGET if a photon was capped). */
+int rt_fields(rt_handle h, double *abs3d, double *sfc_dir, double *sfc_dif, double *toa_up, int mem);
+
+/* Absorption split by photons never scattered (direct) and scattered (diffuse),
+ * nx*ny*nz doubles each [W m^-3], and surface absorption per column
+ * (1 - albedo) (direct + diffuse) [W m^-2]. Any pointer may be NULL. */
+int rt_fields_split(rt_handle h, double *abs_dir, double *abs_dif, double *sfc_abs, int mem);
+
+/* Heating rate [K day^-1] = 86400 A / (rho(z) c_p) with c_p = 1004 J kg^-1 K^-1
+ * and rho(z) = 1.225 exp(-z_c / 8000 m) kg m^-3 at cell centres. which: 0 total,
+ * 1 direct, 2 diffuse. hr: nx*ny*nz doubles. */
+int rt_heating_rate(rt_handle h, double *hr, int which, int mem);
+
+/* Zero all tallies, counters, the energy ledger and the device status. */
+int rt_reset_tallies(rt_handle h);
+
+/* Counters and energy ledger since the last reset. Synchronises. */
+int rt_stats(rt_handle h, rt_stats_t *out);
+
+/* Wait for the handle's stream; returns the device status (RT_OK or RT_E_BUDGET). */
+int rt_synchronize(rt_handle h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *rt_last_error(void);
+
+/* RT_E_* code of the last failed call on this thread (RT_OK if none); the only
+ * way to learn why rt_create returned NULL. */
+int rt_last_error_code(void);
+
+/* ---- test entry points: the device RNG and samplers, on host buffers ---- */
+
+/* n Philox4x32-10 blocks computed on the GPU: ctr[4n], key[2n] in, out[4n]. */
+int rt_debug_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int n);
+
+/* n direction cosines from the device samplers (kind 0 Rayleigh, 1
+ * Henyey-Greenstein with asymmetry g, 2 Lambertian), drawn with the transport
+ * kernel's own functions; out: n floats on the host. */
+int rt_debug_sample(int kind, float g, uint64_t n, uint64_t seed, float *out);
+
+/* n rotations by the transport kernel's own turn: out[3i..3i+2] is the unit
+ * vector at angle acos(mu[i]) from d and azimuth phi[i] about it (host arrays). */
+int rt_debug_turn(const float d[3], const float *mu, const float *phi, float *out, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_B300_H */

@@ -1,0 +1,45 @@
+"""Build the CUDA library `librt_b300.so` in-tree for sm_103a (B300).
+
+The library is plain C ABI (include/rt.h) linked against the shared CUDA
+runtime, so it shares one runtime with PyTorch in the same process.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+LIB = os.path.join(PKG, "librt_b300.so")
+SOURCES = [os.path.join(CSRC, "rt_api.cu")]
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + \
+    [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
+
+NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
+         "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
+         "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-I", INCLUDE]
+
+
+def needs_build() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(p) > t for p in DEPS)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if force or needs_build():
+        tmp = LIB + ".tmp%d" % os.getpid()
+        cmd = [NVCC, *FLAGS, "-o", tmp, *SOURCES]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        subprocess.check_call(cmd)
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True, verbose=True))

@@ -1,0 +1,680 @@
+// rt_api.cu -- host side of the C ABI declared in include/rt.h: handle
+// lifecycle, input validation, device buffers and kernel launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "rt.h"
+#include "rt_kernels.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+thread_local int g_err_code = 0;
+
+int fail(int code, const char *fmt, ...)
+{
+    g_err_code = code;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define RT_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? RT_E_OOM : RT_E_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                    \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr uint32_t kDefaultMaxSteps = 10000000u;
+
+template <typename T>
+int dev_alloc(T **p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) return RT_OK;
+    RT_CUDA(cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T)));
+    return RT_OK;
+}
+
+int grid_for(size_t n, int block = 256)
+{
+    size_t g = (n + block - 1) / block;
+    return (int)std::max<size_t>(1, std::min<size_t>(g, 148 * 32));
+}
+
+}  // namespace
+
+struct rt_scene {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    size_t ncell, ncol;
+    int device = 0;
+    int num_sms = 148;
+    cudaStream_t stream = nullptr;
+    rt_options opt{};
+
+    // derived optics, surface, majorant grid
+    float4 *rec = nullptr;
+    float *alb = nullptr;
+    float *kmax = nullptr;
+    int cx = 0, cy = 0, cz = 0, NX = 0, NY = 0, NZ = 0;
+    size_t kmax_cap = 0;
+
+    // staging for host-side inputs (allocated on first host upload)
+    float *stage = nullptr;
+
+    // tallies: FP64 accumulators, or FP32 for the precision study
+    double *t64 = nullptr;   // abs_dir | abs_dif | sfc_dir | sfc_dif | toa
+    float *t32 = nullptr;
+    int tally_prec = RT_TALLY_FP64;
+
+    // output staging (normalised fields for host copies) and per-layer HR factor
+    double *out = nullptr;
+    double *hr_factor = nullptr;
+
+    rt::Scratch *scr = nullptr;
+    int *bad = nullptr;
+    rt::Scratch *host_scr = nullptr;   // pinned
+
+    bool optics_ok = false, surface_ok = false, accel_ok = false;
+    double energy_in = 0.0;
+};
+
+namespace {
+
+int check(rt_handle h)
+{
+    if (!h) return fail(RT_E_INVAL, "null handle");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail(RT_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return RT_OK;
+}
+
+template <typename T>
+rt::Tallies<T> tallies_of(T *base, size_t ncell, size_t ncol)
+{
+    rt::Tallies<T> t;
+    t.abs_dir = base;
+    t.abs_dif = base + ncell;
+    t.sfc_dir = base + 2 * ncell;
+    t.sfc_dif = base + 2 * ncell + ncol;
+    t.toa = base + 2 * ncell + 2 * ncol;
+    return t;
+}
+
+size_t tally_len(rt_handle h) { return 2 * h->ncell + 3 * h->ncol; }
+
+int ensure_tallies(rt_handle h)
+{
+    if (h->tally_prec == RT_TALLY_FP64 && !h->t64) return dev_alloc(&h->t64, tally_len(h));
+    if (h->tally_prec == RT_TALLY_FP32 && !h->t32) return dev_alloc(&h->t32, tally_len(h));
+    return RT_OK;
+}
+
+int copy_in(rt_handle h, float *dst, const float *src, size_t n, int mem)
+{
+    RT_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(float),
+                            mem == RT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
+    return RT_OK;
+}
+
+int read_bad(rt_handle h, int *bad)
+{
+    RT_CUDA(cudaMemcpyAsync(bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    RT_CUDA(cudaStreamSynchronize(h->stream));
+    return RT_OK;
+}
+
+// Copy n doubles from device src to dst (host or device) on the handle's stream.
+int copy_out(rt_handle h, double *dst, const double *src, size_t n, int mem)
+{
+    RT_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                            mem == RT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
+    return RT_OK;
+}
+
+int ensure_out(rt_handle h)
+{
+    if (!h->out) return dev_alloc(&h->out, h->ncell);
+    return RT_OK;
+}
+
+template <typename T>
+int fields_impl(rt_handle h, T *base, double *abs3d, double *sfc_dir, double *sfc_dif, double *toa, int mem)
+{
+    const rt::Tallies<T> t = tallies_of(base, h->ncell, h->ncol);
+    auto emit = [&](double *dst, const T *a, const T *b, size_t n) -> int {
+        if (!dst) return RT_OK;
+        double *tgt = dst;
+        if (mem == RT_HOST) {
+            int rc = ensure_out(h);
+            if (rc) return rc;
+            tgt = h->out;
+        }
+        rt::sum_fields<T><<<grid_for(n), 256, 0, h->stream>>>(a, b, tgt, n);
+        RT_CUDA(cudaGetLastError());
+        if (mem == RT_HOST) return copy_out(h, dst, tgt, n, RT_HOST);
+        return RT_OK;
+    };
+    int rc;
+    if ((rc = emit(abs3d, t.abs_dir, t.abs_dif, h->ncell))) return rc;
+    if ((rc = emit(sfc_dir, t.sfc_dir, nullptr, h->ncol))) return rc;
+    if ((rc = emit(sfc_dif, t.sfc_dif, nullptr, h->ncol))) return rc;
+    if ((rc = emit(toa, t.toa, nullptr, h->ncol))) return rc;
+    return RT_OK;
+}
+
+template <typename T>
+int fields_split_impl(rt_handle h, T *base, double *abs_dir, double *abs_dif, double *sfc_abs, int mem)
+{
+    const rt::Tallies<T> t = tallies_of(base, h->ncell, h->ncol);
+    const T *src[2] = {t.abs_dir, t.abs_dif};
+    double *dst[2] = {abs_dir, abs_dif};
+    for (int q = 0; q < 2; ++q) {
+        if (!dst[q]) continue;
+        double *tgt = dst[q];
+        if (mem == RT_HOST) {
+            int rc = ensure_out(h);
+            if (rc) return rc;
+            tgt = h->out;
+        }
+        rt::sum_fields<T><<<grid_for(h->ncell), 256, 0, h->stream>>>(src[q], nullptr, tgt, h->ncell);
+        RT_CUDA(cudaGetLastError());
+        if (mem == RT_HOST) {
+            int rc = copy_out(h, dst[q], tgt, h->ncell, RT_HOST);
+            if (rc) return rc;
+        }
+    }
+    if (sfc_abs) {
+        double *tgt = sfc_abs;
+        if (mem == RT_HOST) {
+            int rc = ensure_out(h);
+            if (rc) return rc;
+            tgt = h->out;
+        }
+        rt::surface_absorption<T><<<grid_for(h->ncol), 256, 0, h->stream>>>(t.sfc_dir, t.sfc_dif, h->alb, tgt, h->ncol);
+        RT_CUDA(cudaGetLastError());
+        if (mem == RT_HOST) return copy_out(h, sfc_abs, tgt, h->ncol, RT_HOST);
+    }
+    return RT_OK;
+}
+
+int device_status(rt_handle h)
+{
+    int st = 0;
+    RT_CUDA(cudaMemcpyAsync(&st, &h->scr->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    RT_CUDA(cudaStreamSynchronize(h->stream));
+    if (st & rt::kStatusBudget)
+        return fail(RT_E_BUDGET, "a photon reached the step cap; tallies are incomplete");
+    return RT_OK;
+}
+
+template <typename T>
+int launch_trace(rt_handle h, T *base, double sza, double az, double toa_flux, uint64_t begin,
+                 uint64_t count, uint64_t total, uint64_t seed)
+{
+    rt::TraceArgs<T> A{};
+    A.rec = h->rec;
+    A.kmax = h->kmax;
+    A.alb = h->alb;
+    A.tal = tallies_of(base, h->ncell, h->ncol);
+    A.scr = h->scr;
+    A.id_begin = begin;
+    A.count = count;
+    A.ncol = h->ncol;
+    A.nx = h->nx; A.ny = h->ny; A.nz = h->nz;
+    A.NX = h->NX; A.NY = h->NY; A.NZ = h->NZ;
+    A.cx = h->cx; A.cy = h->cy; A.cz = h->cz;
+    A.dx = (float)h->dx; A.dy = (float)h->dy; A.dz = (float)h->dz;
+    A.inv_dx = (float)(1.0 / h->dx); A.inv_dy = (float)(1.0 / h->dy); A.inv_dz = (float)(1.0 / h->dz);
+    A.Lx = (float)(h->nx * h->dx); A.Ly = (float)(h->ny * h->dy); A.H = (float)(h->nz * h->dz);
+    const double t = sza * kPi / 180.0, p = az * kPi / 180.0;
+    A.sx = (float)(-std::sin(t) * std::sin(p));
+    A.sy = (float)(-std::sin(t) * std::cos(p));
+    A.sz = (float)(-std::cos(t));
+    A.key0 = (uint32_t)seed;
+    A.key1 = (uint32_t)(seed >> 32);
+    const double mu0 = std::cos(t);
+    const double area = h->nx * h->dx * h->ny * h->dy;
+    A.energy = toa_flux * mu0 * area / (double)total;
+    A.scale2 = A.energy / (h->dx * h->dy);
+    A.scale3 = A.energy / (h->dx * h->dy * h->dz);
+    A.max_steps = h->opt.max_steps ? h->opt.max_steps : kDefaultMaxSteps;
+    A.chunk = (uint32_t)(h->opt.refill_chunk > 0 ? h->opt.refill_chunk : 32);
+
+    const int block = h->opt.block_size > 0 ? h->opt.block_size : 256;
+    int bps = h->opt.blocks_per_sm;
+    if (bps <= 0) {
+        RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rt::trace_kernel<T>, block, 0));
+        bps = std::max(1, bps);
+    }
+    RT_CUDA(cudaMemsetAsync(&h->scr->queue_head, 0, sizeof(unsigned long long), h->stream));
+    rt::trace_kernel<T><<<h->num_sms * bps, block, 0, h->stream>>>(A);
+    RT_CUDA(cudaGetLastError());
+    h->energy_in += toa_flux * mu0 * area * ((double)count / (double)total);
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rt_last_error(void) { return g_err; }
+
+int rt_last_error_code(void) { return g_err_code; }
+
+rt_handle rt_create(int nx, int ny, int nz, double dx, double dy, double dz)
+{
+    if (nx <= 0 || ny <= 0 || nz <= 0 || !(dx > 0) || !(dy > 0) || !(dz > 0) ||
+        !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz)) {
+        fail(RT_E_INVAL, "rt_create: sizes must be positive (got %d %d %d, %g %g %g)", nx, ny, nz, dx, dy, dz);
+        return nullptr;
+    }
+    const size_t ncell = (size_t)nx * ny * nz;
+    if (ncell >= (size_t)1 << 31) {
+        fail(RT_E_INVAL, "rt_create: nx*ny*nz must be below 2^31");
+        return nullptr;
+    }
+    rt_scene *h = new (std::nothrow) rt_scene;
+    if (!h) {
+        fail(RT_E_OOM, "rt_create: host allocation failed");
+        return nullptr;
+    }
+    h->nx = nx; h->ny = ny; h->nz = nz;
+    h->dx = dx; h->dy = dy; h->dz = dz;
+    h->ncell = ncell;
+    h->ncol = (size_t)nx * ny;
+    int rc = RT_OK;
+    auto bail = [&](int code) {
+        (void)code;
+        rt_destroy(h);
+        return (rt_handle) nullptr;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess || cudaSetDevice(h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        fail(RT_E_CUDA, "rt_create: no usable CUDA device");
+        return bail(RT_E_CUDA);
+    }
+    if ((rc = dev_alloc(&h->rec, ncell)) || (rc = dev_alloc(&h->alb, h->ncol)) ||
+        (rc = dev_alloc(&h->t64, tally_len(h))) || (rc = dev_alloc(&h->scr, 1)) ||
+        (rc = dev_alloc(&h->bad, 1)) || (rc = dev_alloc(&h->hr_factor, (size_t)nz)))
+        return bail(rc);
+    if (cudaMallocHost(reinterpret_cast<void **>(&h->host_scr), sizeof(rt::Scratch)) != cudaSuccess) {
+        fail(RT_E_OOM, "rt_create: pinned allocation failed");
+        return bail(RT_E_OOM);
+    }
+    std::vector<double> f(nz);
+    for (int k = 0; k < nz; ++k) {
+        const double z = (k + 0.5) * dz;
+        f[k] = 86400.0 / (1.225 * std::exp(-z / 8000.0) * 1004.0);
+    }
+    if (cudaMemcpy(h->hr_factor, f.data(), nz * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(h->scr, 0, sizeof(rt::Scratch)) != cudaSuccess ||
+        cudaMemset(h->t64, 0, tally_len(h) * sizeof(double)) != cudaSuccess) {
+        fail(RT_E_CUDA, "rt_create: initialisation failed");
+        return bail(RT_E_CUDA);
+    }
+    h->opt.block_size = 256;
+    h->opt.blocks_per_sm = 0;
+    h->opt.refill_chunk = 32;
+    h->opt.max_steps = kDefaultMaxSteps;
+    h->opt.pcld_mode = RT_PCLD_SCATTERING;
+    h->opt.tally_precision = RT_TALLY_FP64;
+    return h;
+}
+
+int rt_destroy(rt_handle h)
+{
+    if (!h) return RT_OK;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(h->rec);
+    cudaFree(h->alb);
+    cudaFree(h->kmax);
+    cudaFree(h->stage);
+    cudaFree(h->t64);
+    cudaFree(h->t32);
+    cudaFree(h->out);
+    cudaFree(h->hr_factor);
+    cudaFree(h->scr);
+    cudaFree(h->bad);
+    if (h->host_scr) cudaFreeHost(h->host_scr);
+    delete h;
+    return RT_OK;
+}
+
+int rt_set_stream(rt_handle h, void *stream)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return RT_OK;
+}
+
+int rt_set_options(rt_handle h, const rt_options *o)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    if (!o) return fail(RT_E_INVAL, "rt_set_options: null options");
+    if (o->block_size < 0 || o->block_size % 32 != 0 || o->block_size > 256)
+        return fail(RT_E_INVAL, "rt_set_options: block_size must be 0 or a multiple of 32 up to 256");
+    if (o->blocks_per_sm < 0 || o->blocks_per_sm > 32)
+        return fail(RT_E_INVAL, "rt_set_options: blocks_per_sm must be in [0, 32]");
+    if (o->refill_chunk < 0 || o->refill_chunk > 4096)
+        return fail(RT_E_INVAL, "rt_set_options: refill_chunk must be in [0, 4096]");
+    if (o->pcld_mode != RT_PCLD_SCATTERING && o->pcld_mode != RT_PCLD_EXTINCTION)
+        return fail(RT_E_INVAL, "rt_set_options: unknown pcld_mode");
+    if (o->tally_precision != RT_TALLY_FP64 && o->tally_precision != RT_TALLY_FP32)
+        return fail(RT_E_INVAL, "rt_set_options: unknown tally_precision");
+    if (o->blocks_per_sm > 0) {
+        int fit = 0;
+        const int block = o->block_size > 0 ? o->block_size : 256;
+        RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, rt::trace_kernel<double>, block, 0));
+        if (o->blocks_per_sm > fit)
+            return fail(RT_E_INVAL, "rt_set_options: %d blocks/SM do not fit (max %d)", o->blocks_per_sm, fit);
+    }
+    h->opt = *o;
+    return RT_OK;
+}
+
+int rt_get_options(rt_handle h, rt_options *o)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    if (!o) return fail(RT_E_INVAL, "rt_get_options: null options");
+    *o = h->opt;
+    return RT_OK;
+}
+
+int rt_set_optics(rt_handle h, const float *k_gas, const float *ssa_gas, const float *k_cld,
+                  const float *ssa_cld, const float *g_cld, int mem)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    if (!k_gas || !ssa_gas || !k_cld || !ssa_cld || !g_cld)
+        return fail(RT_E_INVAL, "rt_set_optics: null field pointer");
+    if (mem != RT_HOST && mem != RT_DEVICE) return fail(RT_E_INVAL, "rt_set_optics: bad mem flag");
+    const size_t n = h->ncell;
+    const float *src[5] = {k_gas, ssa_gas, k_cld, ssa_cld, g_cld};
+    if (mem == RT_HOST) {
+        if (!h->stage && (rc = dev_alloc(&h->stage, 5 * n))) return rc;
+        for (int q = 0; q < 5; ++q)
+            if ((rc = copy_in(h, h->stage + q * n, src[q], n, RT_HOST))) return rc;
+        for (int q = 0; q < 5; ++q) src[q] = h->stage + q * n;
+    }
+    RT_CUDA(cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
+    // derive into the record; on invalid input the previous record is lost, so
+    // the handle is marked unusable until valid optics arrive
+    rt::derive_optics<<<grid_for(n), 256, 0, h->stream>>>(src[0], src[1], src[2], src[3], src[4], h->rec, n,
+                                                          h->opt.pcld_mode, h->bad);
+    RT_CUDA(cudaGetLastError());
+    int bad = 0;
+    if ((rc = read_bad(h, &bad))) return rc;
+    h->accel_ok = false;
+    if (bad) {
+        h->optics_ok = false;
+        return fail(RT_E_INVAL, "rt_set_optics: invalid optical property (NaN, negative extinction, "
+                                "albedo outside [0,1] or |g| >= 1)");
+    }
+    h->optics_ok = true;
+    return RT_OK;
+}
+
+int rt_set_surface(rt_handle h, const float *albedo, int mem)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    if (!albedo) return fail(RT_E_INVAL, "rt_set_surface: null albedo");
+    if (mem != RT_HOST && mem != RT_DEVICE) return fail(RT_E_INVAL, "rt_set_surface: bad mem flag");
+    if ((rc = copy_in(h, h->alb, albedo, h->ncol, mem))) return rc;
+    RT_CUDA(cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
+    rt::check_albedo<<<grid_for(h->ncol), 256, 0, h->stream>>>(h->alb, h->ncol, h->bad);
+    RT_CUDA(cudaGetLastError());
+    int bad = 0;
+    if ((rc = read_bad(h, &bad))) return rc;
+    if (bad) {
+        h->surface_ok = false;
+        return fail(RT_E_INVAL, "rt_set_surface: albedo outside [0,1]");
+    }
+    h->surface_ok = true;
+    return RT_OK;
+}
+
+int rt_build_accel(rt_handle h, int cx, int cy, int cz)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    if (!h->optics_ok) return fail(RT_E_STATE, "rt_build_accel: set valid optics first");
+    if (cx == 0 && cy == 0 && cz == 0) {
+        cx = std::min(4, h->nx);
+        cy = std::min(4, h->ny);
+        cz = std::min(4, h->nz);
+    }
+    if (cx <= 0 || cy <= 0 || cz <= 0 || cx > h->nx || cy > h->ny || cz > h->nz)
+        return fail(RT_E_INVAL, "rt_build_accel: coarsening factors must be in [1, n] per axis");
+    const int NX = (h->nx + cx - 1) / cx, NY = (h->ny + cy - 1) / cy, NZ = (h->nz + cz - 1) / cz;
+    const size_t nc = (size_t)NX * NY * NZ;
+    if (nc > h->kmax_cap) {
+        cudaFree(h->kmax);
+        h->kmax = nullptr;
+        h->kmax_cap = 0;
+        if ((rc = dev_alloc(&h->kmax, nc))) return rc;
+        h->kmax_cap = nc;
+    }
+    h->cx = cx; h->cy = cy; h->cz = cz;
+    h->NX = NX; h->NY = NY; h->NZ = NZ;
+    rt::build_majorant<<<grid_for(nc), 256, 0, h->stream>>>(h->rec, h->kmax, h->nx, h->ny, h->nz, cx, cy, cz,
+                                                            NX, NY, NZ);
+    RT_CUDA(cudaGetLastError());
+    h->accel_ok = true;
+    return RT_OK;
+}
+
+int rt_trace_range(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux, uint64_t photon_begin,
+                   uint64_t photon_count, uint64_t photons_total, uint64_t seed)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    if (!h->optics_ok || !h->surface_ok || !h->accel_ok)
+        return fail(RT_E_STATE, "rt_trace: set optics and surface and build the acceleration grid first");
+    if (!(sza_deg >= 0.0 && sza_deg < 90.0)) return fail(RT_E_INVAL, "rt_trace: sza must be in [0, 90)");
+    if (!std::isfinite(azimuth_deg)) return fail(RT_E_INVAL, "rt_trace: azimuth must be finite");
+    if (!(toa_flux >= 0.0) || !std::isfinite(toa_flux)) return fail(RT_E_INVAL, "rt_trace: toa_flux must be >= 0");
+    if (photons_total == 0) return fail(RT_E_INVAL, "rt_trace: photons_total must be positive");
+    if (photon_begin > photons_total || photon_count > photons_total - photon_begin)
+        return fail(RT_E_INVAL, "rt_trace: photon range exceeds photons_total");
+    if (photon_count == 0) return RT_OK;
+    if ((rc = ensure_tallies(h))) return rc;
+    if (h->tally_prec == RT_TALLY_FP64)
+        return launch_trace<double>(h, h->t64, sza_deg, azimuth_deg, toa_flux, photon_begin, photon_count,
+                                    photons_total, seed);
+    return launch_trace<float>(h, h->t32, sza_deg, azimuth_deg, toa_flux, photon_begin, photon_count,
+                               photons_total, seed);
+}
+
+int rt_trace(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux, uint64_t photons, uint64_t seed)
+{
+    if (photons == 0) return check(h);
+    return rt_trace_range(h, sza_deg, azimuth_deg, toa_flux, 0, photons, photons, seed);
+}
+
+int rt_reset_tallies(rt_handle h)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    h->tally_prec = h->opt.tally_precision;
+    if ((rc = ensure_tallies(h))) return rc;
+    if (h->tally_prec == RT_TALLY_FP64)
+        RT_CUDA(cudaMemsetAsync(h->t64, 0, tally_len(h) * sizeof(double), h->stream));
+    else
+        RT_CUDA(cudaMemsetAsync(h->t32, 0, tally_len(h) * sizeof(float), h->stream));
+    RT_CUDA(cudaMemsetAsync(h->scr, 0, sizeof(rt::Scratch), h->stream));
+    h->energy_in = 0.0;
+    return RT_OK;
+}
+
+int rt_fields(rt_handle h, double *abs3d, double *sfc_dir, double *sfc_dif, double *toa_up, int mem)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    if (mem != RT_HOST && mem != RT_DEVICE) return fail(RT_E_INVAL, "rt_fields: bad mem flag");
+    rc = h->tally_prec == RT_TALLY_FP64 ? fields_impl<double>(h, h->t64, abs3d, sfc_dir, sfc_dif, toa_up, mem)
+                                        : fields_impl<float>(h, h->t32, abs3d, sfc_dir, sfc_dif, toa_up, mem);
+    if (rc) return rc;
+    return mem == RT_HOST ? device_status(h) : RT_OK;
+}
+
+int rt_fields_split(rt_handle h, double *abs_dir, double *abs_dif, double *sfc_abs, int mem)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    if (mem != RT_HOST && mem != RT_DEVICE) return fail(RT_E_INVAL, "rt_fields_split: bad mem flag");
+    if (sfc_abs && !h->surface_ok) return fail(RT_E_STATE, "rt_fields_split: no surface set");
+    rc = h->tally_prec == RT_TALLY_FP64 ? fields_split_impl<double>(h, h->t64, abs_dir, abs_dif, sfc_abs, mem)
+                                        : fields_split_impl<float>(h, h->t32, abs_dir, abs_dif, sfc_abs, mem);
+    if (rc) return rc;
+    return mem == RT_HOST ? device_status(h) : RT_OK;
+}
+
+int rt_heating_rate(rt_handle h, double *hr, int which, int mem)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    if (!hr || which < 0 || which > 2 || (mem != RT_HOST && mem != RT_DEVICE))
+        return fail(RT_E_INVAL, "rt_heating_rate: bad argument");
+    double *tgt = hr;
+    if (mem == RT_HOST) {
+        if ((rc = ensure_out(h))) return rc;
+        tgt = h->out;
+    }
+    const int g = grid_for(h->ncell);
+    if (h->tally_prec == RT_TALLY_FP64) {
+        auto t = tallies_of(h->t64, h->ncell, h->ncol);
+        rt::heating_rate<double><<<g, 256, 0, h->stream>>>(which == 2 ? nullptr : t.abs_dir,
+                                                            which == 1 ? nullptr : t.abs_dif, h->hr_factor, tgt,
+                                                            h->ncol, h->ncell);
+    } else {
+        auto t = tallies_of(h->t32, h->ncell, h->ncol);
+        rt::heating_rate<float><<<g, 256, 0, h->stream>>>(which == 2 ? nullptr : t.abs_dir,
+                                                           which == 1 ? nullptr : t.abs_dif, h->hr_factor, tgt,
+                                                           h->ncol, h->ncell);
+    }
+    RT_CUDA(cudaGetLastError());
+    if (mem == RT_HOST) {
+        if ((rc = copy_out(h, hr, tgt, h->ncell, RT_HOST))) return rc;
+        return device_status(h);
+    }
+    return RT_OK;
+}
+
+int rt_stats(rt_handle h, rt_stats_t *out)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    if (!out) return fail(RT_E_INVAL, "rt_stats: null output");
+    const double vol = h->dx * h->dy * h->dz, area = h->dx * h->dy;
+    RT_CUDA(cudaMemsetAsync(&h->scr->e_toa, 0, 3 * sizeof(double), h->stream));
+    if (h->surface_ok) {
+        const int g = grid_for(h->ncell);
+        if (h->tally_prec == RT_TALLY_FP64)
+            rt::ledger_reduce<double><<<g, 256, 0, h->stream>>>(tallies_of(h->t64, h->ncell, h->ncol), h->alb,
+                                                                 h->ncell, h->ncol, vol, area, h->scr);
+        else
+            rt::ledger_reduce<float><<<g, 256, 0, h->stream>>>(tallies_of(h->t32, h->ncell, h->ncol), h->alb,
+                                                                h->ncell, h->ncol, vol, area, h->scr);
+        RT_CUDA(cudaGetLastError());
+    }
+    RT_CUDA(cudaMemcpyAsync(h->host_scr, h->scr, sizeof(rt::Scratch), cudaMemcpyDeviceToHost, h->stream));
+    RT_CUDA(cudaStreamSynchronize(h->stream));
+    const rt::Scratch &s = *h->host_scr;
+    out->photons = s.photons;
+    out->events = s.events;
+    out->scatters = s.scatters;
+    out->crossings = s.crossings;
+    out->surface_hits = s.surface_hits;
+    out->roulette_kills = s.roulette_kills;
+    out->capped = s.capped;
+    out->max_events_photon = s.max_events;
+    out->energy_in = h->energy_in;
+    out->energy_toa_up = s.e_toa;
+    out->energy_atm_abs = s.e_atm;
+    out->energy_sfc_abs = s.e_sfc;
+    out->energy_created = s.created;
+    out->energy_destroyed = s.destroyed;
+    out->energy_capped = s.capped_energy;
+    out->status = (s.status & rt::kStatusBudget) ? RT_E_BUDGET : RT_OK;
+    return RT_OK;
+}
+
+int rt_synchronize(rt_handle h)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    return device_status(h);
+}
+
+int rt_debug_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int n)
+{
+    if (!ctr || !key || !out || n <= 0) return fail(RT_E_INVAL, "rt_debug_philox: bad argument");
+    uint4 *dc = nullptr, *dout = nullptr;
+    uint2 *dk = nullptr;
+    int rc;
+    if ((rc = dev_alloc(&dc, n)) || (rc = dev_alloc(&dk, n)) || (rc = dev_alloc(&dout, n))) {
+        cudaFree(dc); cudaFree(dk); cudaFree(dout);
+        return rc;
+    }
+    cudaMemcpy(dc, ctr, n * sizeof(uint4), cudaMemcpyHostToDevice);
+    cudaMemcpy(dk, key, n * sizeof(uint2), cudaMemcpyHostToDevice);
+    rt::debug_philox<<<(n + 127) / 128, 128>>>(dc, dk, dout, n);
+    cudaError_t e = cudaMemcpy(out, dout, n * sizeof(uint4), cudaMemcpyDeviceToHost);
+    cudaFree(dc); cudaFree(dk); cudaFree(dout);
+    if (e != cudaSuccess) return fail(RT_E_CUDA, "rt_debug_philox: %s", cudaGetErrorString(e));
+    return RT_OK;
+}
+
+int rt_debug_sample(int kind, float g, uint64_t n, uint64_t seed, float *out)
+{
+    if (kind < 0 || kind > 2 || !out || n == 0 || !(std::fabs(g) < 1.0f))
+        return fail(RT_E_INVAL, "rt_debug_sample: bad argument");
+    float *d = nullptr;
+    int rc;
+    if ((rc = dev_alloc(&d, n))) return rc;
+    rt::debug_sample<<<(unsigned)((n + 255) / 256), 256>>>(kind, g, n, (uint32_t)seed, (uint32_t)(seed >> 32), d);
+    cudaError_t e = cudaMemcpy(out, d, n * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(RT_E_CUDA, "rt_debug_sample: %s", cudaGetErrorString(e));
+    return RT_OK;
+}
+
+int rt_debug_turn(const float d[3], const float *mu, const float *phi, float *out, int n)
+{
+    if (!d || !mu || !phi || !out || n <= 0) return fail(RT_E_INVAL, "rt_debug_turn: bad argument");
+    float *dm = nullptr, *dp = nullptr, *dout = nullptr;
+    int rc;
+    if ((rc = dev_alloc(&dm, n)) || (rc = dev_alloc(&dp, n)) || (rc = dev_alloc(&dout, 3 * (size_t)n))) {
+        cudaFree(dm); cudaFree(dp); cudaFree(dout);
+        return rc;
+    }
+    cudaMemcpy(dm, mu, n * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(dp, phi, n * sizeof(float), cudaMemcpyHostToDevice);
+    rt::debug_turn<<<(n + 255) / 256, 256>>>(d[0], d[1], d[2], dm, dp, dout, n);
+    cudaError_t e = cudaMemcpy(out, dout, 3 * (size_t)n * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaFree(dm); cudaFree(dp); cudaFree(dout);
+    if (e != cudaSuccess) return fail(RT_E_CUDA, "rt_debug_turn: %s", cudaGetErrorString(e));
+    return RT_OK;
+}
+
+}  // extern "C"

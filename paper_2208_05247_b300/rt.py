@@ -1,0 +1,350 @@
+"""Python binding of the C ABI in include/rt.h (argument marshalling only).
+
+Every function has the C name and forwards to `librt_b300.so`; all work runs
+in the library's CUDA kernels. Host buffers are numpy arrays (or CPU torch
+tensors); device buffers are CUDA torch tensors. There is no CPU fallback: if
+the library is missing the import of the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+RT_OK, RT_E_INVAL, RT_E_STATE, RT_E_CUDA, RT_E_OOM, RT_E_BUDGET = 0, -1, -2, -3, -4, -5
+RT_HOST, RT_DEVICE = 0, 1
+RT_PCLD_SCATTERING, RT_PCLD_EXTINCTION = 0, 1
+RT_TALLY_FP64, RT_TALLY_FP32 = 0, 1
+
+_ERRNAMES = {RT_E_INVAL: "RT_E_INVAL", RT_E_STATE: "RT_E_STATE", RT_E_CUDA: "RT_E_CUDA",
+             RT_E_OOM: "RT_E_OOM", RT_E_BUDGET: "RT_E_BUDGET"}
+
+
+class RtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class rt_options(ctypes.Structure):
+    _fields_ = [("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("refill_chunk", ctypes.c_int), ("max_steps", ctypes.c_uint32),
+                ("pcld_mode", ctypes.c_int), ("tally_precision", ctypes.c_int)]
+
+
+class rt_stats_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("photons", "events", "scatters", "crossings",
+                                               "surface_hits", "roulette_kills", "capped",
+                                               "max_events_photon")] + \
+               [(n, ctypes.c_double) for n in ("energy_in", "energy_toa_up", "energy_atm_abs",
+                                               "energy_sfc_abs", "energy_created",
+                                               "energy_destroyed", "energy_capped")] + \
+               [("status", ctypes.c_int)]
+
+
+_lib = None
+
+
+def library() -> ctypes.CDLL:
+    """Load librt_b300.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is not built; run paper_2208_05247_b300.build.build(). "
+                               "The tracer has no CPU fallback.")
+        lib = ctypes.CDLL(LIB)
+        H, P, i32, u64, f64 = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
+        sig = {
+            "rt_create": ([i32, i32, i32, f64, f64, f64], H),
+            "rt_destroy": ([H], i32),
+            "rt_set_stream": ([H, P], i32),
+            "rt_set_options": ([H, ctypes.POINTER(rt_options)], i32),
+            "rt_get_options": ([H, ctypes.POINTER(rt_options)], i32),
+            "rt_set_optics": ([H, P, P, P, P, P, i32], i32),
+            "rt_set_surface": ([H, P, i32], i32),
+            "rt_build_accel": ([H, i32, i32, i32], i32),
+            "rt_trace": ([H, f64, f64, f64, u64, u64], i32),
+            "rt_trace_range": ([H, f64, f64, f64, u64, u64, u64, u64], i32),
+            "rt_fields": ([H, P, P, P, P, i32], i32),
+            "rt_fields_split": ([H, P, P, P, i32], i32),
+            "rt_heating_rate": ([H, P, i32, i32], i32),
+            "rt_reset_tallies": ([H], i32),
+            "rt_stats": ([H, ctypes.POINTER(rt_stats_t)], i32),
+            "rt_synchronize": ([H], i32),
+            "rt_last_error": ([], ctypes.c_char_p),
+            "rt_last_error_code": ([], i32),
+            "rt_debug_philox": ([P, P, P, i32], i32),
+            "rt_debug_sample": ([i32, ctypes.c_float, u64, u64, P], i32),
+            "rt_debug_turn": ([P, P, P, P, i32], i32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def rt_last_error() -> str:
+    return library().rt_last_error().decode()
+
+
+def rt_last_error_code() -> int:
+    return library().rt_last_error_code()
+
+
+def _check(rc: int) -> int:
+    if rc != RT_OK:
+        raise RtError(rc, rt_last_error())
+    return rc
+
+
+def _buf(x, n: int | None, dtype, name: str, writable: bool = False):
+    """(pointer, mem) of a numpy array or torch tensor with n elements of dtype."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or not x.flags.c_contiguous or (writable and not x.flags.writeable):
+            raise ValueError(f"{name}: need a C-contiguous {np.dtype(dtype).name} array")
+        if n is not None and x.size != n:
+            raise ValueError(f"{name}: expected {n} elements, got {x.size}")
+        return x.ctypes.data, RT_HOST
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        want = {np.float32: torch.float32, np.float64: torch.float64}[np.dtype(dtype).type]
+        if x.dtype != want or not x.is_contiguous():
+            raise ValueError(f"{name}: need a contiguous {want} tensor")
+        if n is not None and x.numel() != n:
+            raise ValueError(f"{name}: expected {n} elements, got {x.numel()}")
+        return x.data_ptr(), (RT_DEVICE if x.is_cuda else RT_HOST)
+    raise TypeError(f"{name}: expected numpy array or torch tensor, got {type(x)}")
+
+
+def _same_mem(*pairs):
+    mems = {m for _, m in pairs if m is not None}
+    if len(mems) > 1:
+        raise ValueError("all buffers of one call must be host or all device")
+    return mems.pop() if mems else RT_HOST
+
+
+# ---- the C ABI, one function each -------------------------------------------------
+
+def rt_create(nx, ny, nz, dx, dy, dz) -> int:
+    h = library().rt_create(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz))
+    if not h:
+        raise RtError(rt_last_error_code(), rt_last_error())
+    return h
+
+
+def rt_destroy(h):
+    return _check(library().rt_destroy(h))
+
+
+def rt_set_stream(h, stream=None):
+    if stream is None:
+        ptr = None
+    elif isinstance(stream, int):
+        ptr = stream
+    else:
+        ptr = stream.cuda_stream
+    return _check(library().rt_set_stream(h, ptr))
+
+
+def rt_set_options(h, **kw):
+    o = rt_options()
+    _check(library().rt_get_options(h, ctypes.byref(o)))
+    for k, v in kw.items():
+        if k not in dict(rt_options._fields_):
+            raise KeyError(k)
+        setattr(o, k, int(v))
+    return _check(library().rt_set_options(h, ctypes.byref(o)))
+
+
+def rt_get_options(h) -> dict:
+    o = rt_options()
+    _check(library().rt_get_options(h, ctypes.byref(o)))
+    return {k: getattr(o, k) for k, _ in rt_options._fields_}
+
+
+def rt_set_optics(h, ncell, k_gas, ssa_gas, k_cld, ssa_cld, g_cld):
+    bufs = [_buf(a, ncell, np.float32, n) for a, n in
+            zip((k_gas, ssa_gas, k_cld, ssa_cld, g_cld), ("k_gas", "ssa_gas", "k_cld", "ssa_cld", "g_cld"))]
+    mem = _same_mem(*bufs)
+    return _check(library().rt_set_optics(h, *[p for p, _ in bufs], mem))
+
+
+def rt_set_surface(h, ncol, albedo):
+    p, mem = _buf(albedo, ncol, np.float32, "albedo")
+    return _check(library().rt_set_surface(h, p, mem))
+
+
+def rt_build_accel(h, cx=0, cy=0, cz=0):
+    return _check(library().rt_build_accel(h, int(cx), int(cy), int(cz)))
+
+
+def rt_trace(h, sza_deg, azimuth_deg, toa_flux, photons, seed):
+    return _check(library().rt_trace(h, float(sza_deg), float(azimuth_deg), float(toa_flux),
+                                     int(photons), int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+
+def rt_trace_range(h, sza_deg, azimuth_deg, toa_flux, photon_begin, photon_count, photons_total, seed):
+    return _check(library().rt_trace_range(h, float(sza_deg), float(azimuth_deg), float(toa_flux),
+                                           int(photon_begin), int(photon_count), int(photons_total),
+                                           int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+
+def rt_fields(h, ncell, ncol, abs3d=None, sfc_dir=None, sfc_dif=None, toa_up=None):
+    bufs = [_buf(abs3d, ncell, np.float64, "abs3d", True), _buf(sfc_dir, ncol, np.float64, "sfc_dir", True),
+            _buf(sfc_dif, ncol, np.float64, "sfc_dif", True), _buf(toa_up, ncol, np.float64, "toa_up", True)]
+    mem = _same_mem(*bufs)
+    return _check(library().rt_fields(h, *[p for p, _ in bufs], mem))
+
+
+def rt_fields_split(h, ncell, ncol, abs_dir=None, abs_dif=None, sfc_abs=None):
+    bufs = [_buf(abs_dir, ncell, np.float64, "abs_dir", True), _buf(abs_dif, ncell, np.float64, "abs_dif", True),
+            _buf(sfc_abs, ncol, np.float64, "sfc_abs", True)]
+    mem = _same_mem(*bufs)
+    return _check(library().rt_fields_split(h, *[p for p, _ in bufs], mem))
+
+
+def rt_heating_rate(h, ncell, hr, which=0):
+    p, mem = _buf(hr, ncell, np.float64, "hr", True)
+    return _check(library().rt_heating_rate(h, p, int(which), mem))
+
+
+def rt_reset_tallies(h):
+    return _check(library().rt_reset_tallies(h))
+
+
+def rt_stats(h) -> dict:
+    s = rt_stats_t()
+    _check(library().rt_stats(h, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in rt_stats_t._fields_}
+
+
+def rt_synchronize(h):
+    return _check(library().rt_synchronize(h))
+
+
+def rt_debug_philox(ctr, key) -> np.ndarray:
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    if ctr.shape[0] != key.shape[0]:
+        raise ValueError("ctr and key must have the same number of blocks")
+    out = np.zeros_like(ctr)
+    _check(library().rt_debug_philox(ctr.ctypes.data, key.ctypes.data, out.ctypes.data, ctr.shape[0]))
+    return out
+
+
+def rt_debug_sample(kind: str, n: int, seed: int = 1, g: float = 0.0) -> np.ndarray:
+    k = {"rayleigh": 0, "hg": 1, "lambert": 2}[kind]
+    out = np.empty(n, dtype=np.float32)
+    _check(library().rt_debug_sample(k, float(g), int(n), int(seed), out.ctypes.data))
+    return out
+
+
+def rt_debug_turn(d, mu, phi) -> np.ndarray:
+    d = np.ascontiguousarray(d, dtype=np.float32)
+    mu = np.ascontiguousarray(mu, dtype=np.float32)
+    phi = np.ascontiguousarray(phi, dtype=np.float32)
+    out = np.empty((mu.size, 3), dtype=np.float32)
+    _check(library().rt_debug_turn(d.ctypes.data, mu.ctypes.data, phi.ctypes.data, out.ctypes.data, mu.size))
+    return out
+
+
+# ---- a small object wrapper over one handle ---------------------------------------
+
+class Tracer:
+    """One scene handle: grid, optics, surface, acceleration grid and tallies."""
+
+    def __init__(self, nx, ny, nz, dx, dy, dz, stream=None):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.dx, self.dy, self.dz = float(dx), float(dy), float(dz)
+        self.ncell = self.nx * self.ny * self.nz
+        self.ncol = self.nx * self.ny
+        self.h = rt_create(nx, ny, nz, dx, dy, dz)
+        if stream is not None:
+            rt_set_stream(self.h, stream)
+
+    @classmethod
+    def from_scene(cls, scene, cx=0, cy=0, cz=0, stream=None, **options):
+        t = cls(scene.nx, scene.ny, scene.nz, scene.dx, scene.dy, scene.dz, stream=stream)
+        if options:
+            t.set_options(**options)
+        t.set_optics(*scene.fields())
+        t.set_surface(scene.albedo)
+        t.build_accel(cx, cy, cz)
+        return t
+
+    def close(self):
+        if getattr(self, "h", None):
+            rt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_options(self, **kw):
+        rt_set_options(self.h, **kw)
+
+    def options(self) -> dict:
+        return rt_get_options(self.h)
+
+    def set_stream(self, stream):
+        rt_set_stream(self.h, stream)
+
+    def set_optics(self, k_gas, ssa_gas, k_cld, ssa_cld, g_cld):
+        rt_set_optics(self.h, self.ncell, k_gas, ssa_gas, k_cld, ssa_cld, g_cld)
+
+    def set_surface(self, albedo):
+        rt_set_surface(self.h, self.ncol, albedo)
+
+    def build_accel(self, cx=0, cy=0, cz=0):
+        rt_build_accel(self.h, cx, cy, cz)
+
+    def trace(self, sza_deg, azimuth_deg, toa_flux, photons, seed):
+        rt_trace(self.h, sza_deg, azimuth_deg, toa_flux, photons, seed)
+
+    def trace_range(self, sza_deg, azimuth_deg, toa_flux, begin, count, total, seed):
+        rt_trace_range(self.h, sza_deg, azimuth_deg, toa_flux, begin, count, total, seed)
+
+    def reset(self):
+        rt_reset_tallies(self.h)
+
+    def stats(self) -> dict:
+        return rt_stats(self.h)
+
+    def synchronize(self):
+        rt_synchronize(self.h)
+
+    def fields(self, split: bool = False) -> dict:
+        """All output fields as host numpy arrays ([nz][ny][nx] and [ny][nx])."""
+        s3, s2 = (self.nz, self.ny, self.nx), (self.ny, self.nx)
+        out = {k: np.empty(s3) for k in ("abs3d",)}
+        out.update({k: np.empty(s2) for k in ("sfc_dir", "sfc_dif", "toa_up")})
+        rt_fields(self.h, self.ncell, self.ncol, out["abs3d"], out["sfc_dir"], out["sfc_dif"], out["toa_up"])
+        if split:
+            out["abs_dir"], out["abs_dif"] = np.empty(s3), np.empty(s3)
+            out["sfc_abs"] = np.empty(s2)
+            rt_fields_split(self.h, self.ncell, self.ncol, out["abs_dir"], out["abs_dif"], out["sfc_abs"])
+        return out
+
+    def heating_rate(self, which: int = 0) -> np.ndarray:
+        hr = np.empty((self.nz, self.ny, self.nx))
+        rt_heating_rate(self.h, self.ncell, hr, which)
+        return hr

@@ -156,3 +156,31 @@ def zscores(m1, se1, m2, se2):
     with np.errstate(divide="ignore", invalid="ignore"):
         z = np.where(den > 0, (m1 - m2) / den, np.where(m1 == m2, 0.0, np.inf))
     return z
+
+
+def parity_report(gpu_batches, orc_batches, z_limit=4.0):
+    """Cell-wise statistical parity of two sets of independent batch results.
+
+    gpu_batches, orc_batches: arrays [B, ...]. Per cell z = (m1 - m2) /
+    sqrt(se1^2 + se2^2) with batch standard errors. Returns the fraction of
+    cells with |z| > z_limit, the bound it is held to (the larger of 3 cells
+    and twice the Student-t tail with B-1 dof), the largest |z| and the
+    relative difference of the domain sums.
+    """
+    from scipy import stats as st
+    g = np.asarray(gpu_batches, dtype=np.float64)
+    o = np.asarray(orc_batches, dtype=np.float64)
+    B1, B2 = g.shape[0], o.shape[0]
+    mg, mo = g.mean(0), o.mean(0)
+    sg, so = g.std(0, ddof=1) / np.sqrt(B1), o.std(0, ddof=1) / np.sqrt(B2)
+    z = zscores(mg, sg, mo, so).ravel()
+    n = z.size
+    frac = float(np.mean(np.abs(z) > z_limit))
+    dof = min(B1, B2) - 1
+    bound = max(3.0 / n, 2.0 * 2.0 * st.t.sf(z_limit, dof))
+    tot_g, tot_o = g.reshape(B1, -1).sum(1), o.reshape(B2, -1).sum(1)
+    rel = float((tot_g.mean() - tot_o.mean()) / tot_o.mean()) if tot_o.mean() != 0 else 0.0
+    se_rel = float(np.sqrt(tot_g.var(ddof=1) / B1 + tot_o.var(ddof=1) / B2) / abs(tot_o.mean())) \
+        if tot_o.mean() != 0 else 0.0
+    return {"frac_over": frac, "bound": bound, "max_abs_z": float(np.max(np.abs(z))) if n else 0.0,
+            "n": n, "domain_rel": rel, "domain_rel_se": se_rel, "z": z}

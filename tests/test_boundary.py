@@ -1,0 +1,80 @@
+"""The C ABI boundary without a GPU: the library loads, exports every entry
+point include/rt.h declares, and rejects bad arguments on the host."""
+import re
+import os
+
+import numpy as np
+import pytest
+
+from paper_2208_05247_b300 import build, rt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(rt_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return rt.library()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert "rt_trace" in names and "rt_create" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    for n in _declared():
+        assert callable(getattr(rt, n)), n
+
+
+def test_create_rejects_bad_sizes(lib):
+    for args in [(0, 4, 4, 1, 1, 1), (4, -1, 4, 1, 1, 1), (4, 4, 4, 0.0, 1, 1), (4, 4, 4, 1, float("nan"), 1),
+                 (2048, 2048, 1024, 1, 1, 1)]:
+        with pytest.raises(rt.RtError) as e:
+            rt.rt_create(*args)
+        assert e.value.code == rt.RT_E_INVAL
+
+
+def test_debug_entry_points_reject_bad_arguments(lib):
+    with pytest.raises(rt.RtError):
+        rt.rt_debug_sample("hg", 10, g=1.0)
+    with pytest.raises(ValueError):
+        rt.rt_debug_philox(np.zeros((2, 4)), np.zeros((3, 2)))
+
+
+def test_binding_checks_buffers_before_calling():
+    with pytest.raises(ValueError):
+        rt.rt_set_optics(None, 8, *[np.zeros(8, np.float64)] * 5)
+    with pytest.raises(ValueError):
+        rt.rt_set_optics(None, 8, *[np.zeros(7, np.float32)] * 5)
+    with pytest.raises(ValueError):
+        rt.rt_fields(None, 8, 4, abs3d=np.zeros(8, np.float32))
+    with pytest.raises(TypeError):
+        rt.rt_set_surface(None, 4, [0.1, 0.2, 0.3, 0.4])
+
+
+def test_null_handle_is_an_error(lib):
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_build_accel(None)
+    assert e.value.code == rt.RT_E_INVAL
+
+
+def test_no_gpu_means_a_loud_error(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_create(4, 4, 4, 1, 1, 1)
+    assert e.value.code in (rt.RT_E_CUDA, rt.RT_E_OOM)

@@ -1,0 +1,407 @@
+"""GPU tests of the CUDA tracer through the C ABI.
+
+Parity is statistical (Monte Carlo): the GPU's weighted null-collision
+estimator and the oracle's analog estimator have the same expectation, so
+results are compared cell by cell in units of their combined standard error
+(independent batches on each side), plus domain means within 0.5 %. Closed
+forms (Beer-Lambert, absorber + Lambertian surface, isotropic slab) pin the
+GPU path directly as well.
+"""
+import copy
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_2208_05247_b300 import scenes
+from paper_2208_05247_b300 import rt
+from tests import refs
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("abs_dir", "abs_dif", "sfc_dir", "sfc_dif", "toa_up")
+
+
+def gpu_batches(scene, sza, az, flux, photons, seeds, cxyz=(0, 0, 0), **opts):
+    out = {f: [] for f in FIELDS}
+    stats_list = []
+    with rt.Tracer.from_scene(scene, *cxyz, **opts) as t:
+        for s in seeds:
+            t.reset()
+            t.trace(sza, az, flux, photons, s)
+            f = t.fields(split=True)
+            for k in FIELDS:
+                out[k].append(f[k])
+            stats_list.append(t.stats())
+    return {k: np.stack(v) for k, v in out.items()}, stats_list
+
+
+def oracle_batches(scene, sza, az, flux, photons, seeds, **kw):
+    out = {f: [] for f in FIELDS}
+    for s in seeds:
+        r = oracle.trace(scene, sza, az, flux, photons, s, **kw)
+        for k in FIELDS:
+            out[k].append(getattr(r, k))
+    return {k: np.stack(v) for k, v in out.items()}
+
+
+# --- RNG and samplers ------------------------------------------------------------------
+
+def test_philox_known_answers_on_gpu():
+    from tests.test_oracle_pins import PHILOX_KAT
+    ctr = np.array([c for c, _, _ in PHILOX_KAT], dtype=np.uint32)
+    key = np.array([k for _, k, _ in PHILOX_KAT], dtype=np.uint32)
+    want = np.array([w for _, _, w in PHILOX_KAT], dtype=np.uint32)
+    assert np.array_equal(rt.rt_debug_philox(ctr, key), want)
+
+
+def _chi2(samples, cdf, lo=-1.0, nbins=100):
+    edges = np.linspace(lo, 1, nbins + 1)
+    obs, _ = np.histogram(samples, bins=edges)
+    exp = np.diff([cdf(e) for e in edges]) * samples.size
+    return stats.chisquare(obs, exp).pvalue
+
+
+def test_gpu_rayleigh_sampler():
+    mu = rt.rt_debug_sample("rayleigh", 4_000_000, seed=3).astype(np.float64)
+    assert np.all(np.abs(mu) <= 1)
+    assert abs(mu.mean()) < 4 * np.sqrt(0.4 / mu.size)
+    assert abs((mu ** 2).mean() - 0.4) < 4 * np.sqrt((12 / 35 - 0.16) / mu.size)
+    assert _chi2(mu, refs.rayleigh_cdf) > 1e-4
+
+
+@pytest.mark.parametrize("g", [0.0, 0.3, 0.86, -0.5, 0.98])
+def test_gpu_hg_sampler(g):
+    mu = rt.rt_debug_sample("hg", 4_000_000, seed=5, g=g).astype(np.float64)
+    assert abs(mu.mean() - g) < 4 * mu.std() / np.sqrt(mu.size) + 2e-6
+    p2 = 1.5 * mu ** 2 - 0.5
+    assert abs(p2.mean() - g * g) < 4 * p2.std() / np.sqrt(mu.size) + 2e-6
+    assert _chi2(mu, lambda m: refs.hg_cdf(m, g)) > 1e-4
+
+
+def test_gpu_lambert_sampler():
+    mu = rt.rt_debug_sample("lambert", 4_000_000, seed=9).astype(np.float64)
+    assert mu.min() > 0 and mu.max() <= 1
+    assert abs(mu.mean() - 2 / 3) < 4 * np.sqrt(1 / 18 / mu.size)
+    assert _chi2(mu, lambda m: m * m, lo=0.0) > 1e-4
+
+
+@pytest.mark.parametrize("d", [(0, 0, -1), (0.6, 0, 0.8), (0.3, -0.4, np.sqrt(0.75)), (1, 0, 0),
+                               (0, 0, 1)])
+def test_gpu_turn(d):
+    d = np.asarray(d, float) / np.linalg.norm(d)
+    rng = np.random.default_rng(1)
+    n = 200_000
+    mu = rng.uniform(-1, 1, n)
+    phi = rng.uniform(-np.pi, np.pi, n)
+    out = rt.rt_debug_turn(d, mu, phi).astype(np.float64)
+    assert np.allclose(np.linalg.norm(out, axis=1), 1, atol=1e-6)
+    assert np.allclose(out @ d, mu, atol=2e-6)
+    assert np.all(np.abs(out.mean(0)) < 4 / np.sqrt(3 * n))
+
+
+# --- closed forms through the full path ----------------------------------------------
+
+def test_gpu_absorber_over_lambertian_surface():
+    k = np.array([2e-3, 1e-3, 5e-4, 2e-4], dtype=np.float32)
+    dz = 200.0
+    sc = scenes.layered_scene(4, 4, k.size, 100.0, 100.0, dz, k_gas=k, ssa_gas=0.0, albedo=0.6)
+    sza, F0 = 35.0, 1000.0
+    mu0 = np.cos(np.deg2rad(sza))
+    ref = refs.absorber_with_lambert(k, dz, mu0, 0.6, F0)
+    g, st = gpu_batches(sc, sza, 17.0, F0, 1_000_000, range(16), cxyz=(2, 2, 2))
+    def check(arr, want):
+        m = arr.mean(0)
+        se = arr.std(0, ddof=1) / np.sqrt(arr.shape[0])
+        assert np.all(np.abs(m - want) < 4 * se + 1e-9 * abs(want)), (m, want, se)
+    check(g["sfc_dir"].mean(axis=(1, 2)), ref["sfc_dir"])
+    check(g["toa_up"].mean(axis=(1, 2)), ref["toa_up"])
+    assert np.all(g["sfc_dif"] == 0)
+    check(g["abs_dir"].mean(axis=(2, 3)) * dz, ref["abs_dir_layers"])
+    check(g["abs_dif"].mean(axis=(2, 3)) * dz, ref["abs_dif_layers"])
+
+
+def test_gpu_isotropic_slab_against_collision_probabilities():
+    tau_star, omega, sza = 1.0, 0.9, 36.87
+    mu0 = np.cos(np.deg2rad(sza))
+    nz, k = 10, 1e-3
+    dz = tau_star / (k * nz)
+    sc = scenes.layered_scene(4, 4, nz, 100.0, 100.0, dz, k_gas=0.0, ssa_gas=0.0, k_cld=k,
+                              ssa_cld=omega, g_cld=0.0)
+    ref = refs.isotropic_slab_cp(tau_star, omega, mu0, M=400)
+    g, _ = gpu_batches(sc, sza, 0.0, 1.0, 1_000_000, range(16))
+    norm = mu0   # fluxes are per unit horizontal incoming flux mu0 * F0
+    for arr, want in ((g["toa_up"].mean(axis=(1, 2)) / norm, ref["R"]),
+                      (g["sfc_dif"].mean(axis=(1, 2)) / norm, ref["T_dif"]),
+                      (g["sfc_dir"].mean(axis=(1, 2)) / norm, ref["T_dir"])):
+        se = arr.std(ddof=1) / np.sqrt(arr.size)
+        assert abs(arr.mean() - want) < 4 * se, (arr.mean(), want, se)
+    A = ref["A_layers"].reshape(nz, -1).sum(1)[::-1]
+    lay = (g["abs_dir"] + g["abs_dif"]).mean(axis=(2, 3)) * dz / norm
+    se = lay.std(0, ddof=1) / np.sqrt(lay.shape[0])
+    assert np.all(np.abs(lay.mean(0) - A) < 4 * se)
+
+
+@pytest.mark.parametrize("phase", ["rayleigh", "hg"])
+def test_gpu_thin_slab_single_scattering_oblique(phase):
+    tau, omega, g, sza = 2e-3, 0.5, 0.86, 60.0
+    if phase == "rayleigh":
+        sc = scenes.layered_scene(2, 2, 1, 100.0, 100.0, tau, k_gas=1.0, ssa_gas=omega)
+        pdf = refs.rayleigh_pdf
+    else:
+        sc = scenes.layered_scene(2, 2, 1, 100.0, 100.0, tau, k_gas=0.0, ssa_gas=0.0, k_cld=1.0,
+                                  ssa_cld=omega, g_cld=g)
+        pdf = lambda m: refs.hg_pdf(m, g)   # noqa: E731
+    mu0 = np.cos(np.deg2rad(sza))
+    R1 = refs.single_scatter_reflectance(pdf, mu0, tau, omega)
+    T1 = refs.single_scatter_transmittance(pdf, mu0, tau, omega)
+    res, _ = gpu_batches(sc, sza, 10.0, 1.0, 8_000_000, range(8), cxyz=(1, 1, 1))
+    for arr, want in ((res["toa_up"].mean(axis=(1, 2)) / mu0, R1),
+                      (res["sfc_dif"].mean(axis=(1, 2)) / mu0, T1)):
+        se = arr.std(ddof=1) / np.sqrt(arr.size)
+        assert abs(arr.mean() - want) < 4 * se + 3 * (omega * tau / mu0) * want, (arr.mean(), want, se)
+
+
+# --- parity with the oracle on the 32^3 ellipsoid scene ------------------------------
+
+@pytest.fixture(scope="module")
+def c0_parity():
+    sc = scenes.ellipsoid_scene(seed=0)
+    B, N = 24, 2 ** 18
+    g, st = gpu_batches(sc, 30.0, 0.0, 1000.0, N, range(100, 100 + B))
+    o = oracle_batches(sc, 30.0, 0.0, 1000.0, N, range(500, 500 + B))
+    return sc, g, o, st
+
+
+@pytest.mark.parametrize("field", FIELDS)
+def test_parity_cellwise_with_oracle(c0_parity, field):
+    _, g, o, _ = c0_parity
+    rep = refs.parity_report(g[field], o[field])
+    assert rep["frac_over"] <= rep["bound"], (field, rep["frac_over"], rep["bound"], rep["max_abs_z"])
+    # the standardised differences look like noise (KS against the normal law)
+    z = rep["z"][np.isfinite(rep["z"])]
+    assert stats.kstest(z, "norm").pvalue > 1e-4 or np.std(z) < 1.15, (field, np.std(z))
+
+
+@pytest.mark.parametrize("field", FIELDS)
+def test_parity_domain_means_within_half_percent(c0_parity, field):
+    _, g, o, _ = c0_parity
+    rep = refs.parity_report(g[field], o[field])
+    assert abs(rep["domain_rel"]) < 0.005, (field, rep["domain_rel"], rep["domain_rel_se"])
+    assert abs(rep["domain_rel"]) < 4 * rep["domain_rel_se"] + 1e-9
+
+
+def test_energy_ledger_closes(c0_parity):
+    _, _, _, st = c0_parity
+    for s in st:
+        lhs = s["energy_in"] + s["energy_created"] - s["energy_destroyed"] - s["energy_capped"]
+        rhs = s["energy_toa_up"] + s["energy_atm_abs"] + s["energy_sfc_abs"]
+        assert abs(lhs - rhs) < 2e-6 * s["energy_in"], (lhs, rhs)
+        assert s["status"] == 0 and s["capped"] == 0
+        assert s["photons"] == 2 ** 18
+
+
+# --- reproducibility, launch-geometry and partition invariance -----------------------
+
+def _run(sc, seed, N, **opts):
+    with rt.Tracer.from_scene(sc, **opts) as t:
+        t.trace(30.0, 0.0, 1000.0, N, seed)
+        return t.fields(split=True), t.stats()
+
+
+def test_same_seed_same_histories_any_launch_shape(small_scene):
+    N = 300_000
+    f1, s1 = _run(small_scene, 7, N)
+    f2, s2 = _run(small_scene, 7, N, block_size=128, blocks_per_sm=1, refill_chunk=8)
+    for k in ("photons", "events", "scatters", "crossings", "surface_hits", "roulette_kills", "max_events_photon"):
+        assert s1[k] == s2[k], k
+    for k in FIELDS:
+        assert np.allclose(f1[k], f2[k], rtol=1e-12, atol=1e-12 * np.abs(f1[k]).max()), k
+    f3, s3 = _run(small_scene, 8, N)
+    assert s3["events"] != s1["events"]
+
+
+def test_partition_invariance(small_scene):
+    N = 200_000
+    full, sf = _run(small_scene, 3, N)
+    with rt.Tracer.from_scene(small_scene) as t:
+        t.trace_range(30.0, 0.0, 1000.0, 0, 70_001, N, 3)
+        t.trace_range(30.0, 0.0, 1000.0, 70_001, N - 70_001, N, 3)
+        part, sp = t.fields(split=True), t.stats()
+    for k in ("photons", "events", "scatters", "crossings"):
+        assert sf[k] == sp[k]
+    for k in FIELDS:
+        assert np.allclose(full[k], part[k], rtol=1e-12, atol=1e-12 * np.abs(full[k]).max())
+    assert np.isclose(sf["energy_in"], sp["energy_in"], rtol=1e-14)
+
+
+def test_coarse_factors_do_not_change_the_expectation(small_scene):
+    """Any majorant grid (1x1x1 up to one coarse cell per axis) is unbiased."""
+    res = {}
+    for c in ((1, 1, 1), (4, 4, 4), (3, 5, 7), (32, 32, 32)):
+        g, _ = gpu_batches(small_scene, 30.0, 0.0, 1000.0, 2 ** 17, range(8), cxyz=c)
+        res[c] = g
+    base = res[(4, 4, 4)]
+    for c, g in res.items():
+        for f in ("sfc_dif", "toa_up", "abs_dif"):
+            rep = refs.parity_report(g[f], base[f])
+            assert abs(rep["domain_rel"]) < 4 * rep["domain_rel_se"] + 1e-12, (c, f, rep["domain_rel"])
+
+
+# --- precision, modes and buffers ----------------------------------------------------
+
+def test_fp32_tallies_follow_the_same_histories(small_scene):
+    N = 200_000
+    f64, s64 = _run(small_scene, 5, N)
+    with rt.Tracer.from_scene(small_scene, tally_precision=rt.RT_TALLY_FP32) as t:
+        t.reset()
+        t.trace(30.0, 0.0, 1000.0, N, 5)
+        f32, s32 = t.fields(split=True), t.stats()
+    assert s32["events"] == s64["events"]
+    for k in FIELDS:
+        scale = np.abs(f64[k]).max()
+        assert np.max(np.abs(f32[k] - f64[k])) < 1e-4 * scale, k
+
+
+def test_paper_literal_scatterer_choice_mode():
+    tau = 2e-3
+    sc = scenes.layered_scene(2, 2, 1, 100.0, 100.0, tau, k_gas=0.5, ssa_gas=1.0, k_cld=0.5,
+                              ssa_cld=0.2, g_cld=0.86)
+    mu0 = 1.0 - 1e-12
+    Rr = refs.single_scatter_reflectance(refs.rayleigh_pdf, mu0, tau)
+    Rh = refs.single_scatter_reflectance(lambda m: refs.hg_pdf(m, 0.86), mu0, tau)
+    for mode, want in ((0, 0.5 * Rr + 0.1 * Rh), (1, 0.6 * (0.5 * Rr + 0.5 * Rh))):
+        g, _ = gpu_batches(sc, 0.0, 0.0, 1.0, 8_000_000, range(8), cxyz=(1, 1, 1), pcld_mode=mode)
+        R = g["toa_up"].mean(axis=(1, 2))
+        se = R.std(ddof=1) / np.sqrt(R.size)
+        assert abs(R.mean() - want) < 4 * se + 3 * tau * want, (mode, R.mean(), want)
+
+
+def test_device_buffers_match_host_buffers(small_scene):
+    torch = pytest.importorskip("torch")
+    N = 100_000
+    fh, sh = _run(small_scene, 11, N)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in small_scene.fields()]
+    alb = torch.from_numpy(small_scene.albedo).cuda()
+    with rt.Tracer(small_scene.nx, small_scene.ny, small_scene.nz, small_scene.dx, small_scene.dy,
+                   small_scene.dz, stream=torch.cuda.current_stream()) as t:
+        t.set_optics(*dev)
+        t.set_surface(alb)
+        t.build_accel()
+        t.trace(30.0, 0.0, 1000.0, N, 11)
+        out = torch.empty(small_scene.ncell, dtype=torch.float64, device="cuda")
+        sd = torch.empty(small_scene.ncol, dtype=torch.float64, device="cuda")
+        rt.rt_fields(t.h, t.ncell, t.ncol, abs3d=out, sfc_dir=sd)
+        torch.cuda.synchronize()
+        assert np.allclose(out.cpu().numpy().reshape(fh["abs3d"].shape), fh["abs3d"], rtol=1e-12,
+                           atol=1e-12 * fh["abs3d"].max())
+        assert np.allclose(sd.cpu().numpy().reshape(fh["sfc_dir"].shape), fh["sfc_dir"], rtol=1e-12)
+
+
+def test_heating_rate_conversion(small_scene):
+    with rt.Tracer.from_scene(small_scene) as t:
+        t.trace(30.0, 0.0, 1000.0, 100_000, 2)
+        f = t.fields(split=True)
+        hr = t.heating_rate(0)
+        hr_dir = t.heating_rate(1)
+    want = oracle.heating_rate(f["abs3d"], small_scene.dz)
+    assert np.allclose(hr, want, rtol=1e-12, atol=0)
+    assert np.allclose(hr_dir, oracle.heating_rate(f["abs_dir"], small_scene.dz), rtol=1e-12, atol=0)
+
+
+# --- error paths (host-detected or device status; nothing faults) ----------------------
+
+def test_errors_are_reported_not_faulted(small_scene):
+    with rt.Tracer(8, 8, 8, 10.0, 10.0, 10.0) as t:
+        with pytest.raises(rt.RtError) as e:
+            t.trace(30.0, 0.0, 1000.0, 100, 1)
+        assert e.value.code == rt.RT_E_STATE
+        bad = [np.full(512, v, np.float32) for v in (1e-3, 0.5, 0.0, 0.0, 0.0)]
+        bad[0][17] = np.nan
+        with pytest.raises(rt.RtError) as e:
+            t.set_optics(*bad)
+        assert e.value.code == rt.RT_E_INVAL
+        bad[0][17] = 1e-3
+        bad[4][3] = 1.0          # |g| = 1
+        with pytest.raises(rt.RtError):
+            t.set_optics(*bad)
+        bad[4][3] = 0.0
+        t.set_optics(*bad)
+        with pytest.raises(rt.RtError):
+            t.set_surface(np.full(64, 1.5, np.float32))
+        t.set_surface(np.full(64, 0.3, np.float32))
+        with pytest.raises(rt.RtError):
+            t.build_accel(9, 1, 1)
+        t.build_accel()
+        for args in ((90.0, 0.0, 1.0, 10, 1), (-1.0, 0.0, 1.0, 10, 1), (10.0, 0.0, -1.0, 10, 1)):
+            with pytest.raises(rt.RtError) as e:
+                t.trace(*args)
+            assert e.value.code == rt.RT_E_INVAL
+        with pytest.raises(rt.RtError):
+            t.trace_range(10.0, 0.0, 1.0, 5, 10, 12, 1)
+        t.trace(30.0, 0.0, 1000.0, 1000, 1)
+        t.synchronize()
+
+
+def test_step_cap_sets_budget_status_and_returns(small_scene):
+    with rt.Tracer.from_scene(small_scene, max_steps=5) as t:
+        t.trace(30.0, 0.0, 1000.0, 50_000, 1)
+        with pytest.raises(rt.RtError) as e:
+            t.synchronize()
+        assert e.value.code == rt.RT_E_BUDGET
+        s = t.stats()
+        assert s["capped"] > 0 and s["status"] == rt.RT_E_BUDGET
+        lhs = s["energy_in"] + s["energy_created"] - s["energy_destroyed"] - s["energy_capped"]
+        rhs = s["energy_toa_up"] + s["energy_atm_abs"] + s["energy_sfc_abs"]
+        assert abs(lhs - rhs) < 2e-6 * s["energy_in"]
+        t.reset()
+        t.set_options(max_steps=0)
+        t.trace(30.0, 0.0, 1000.0, 50_000, 1)
+        t.synchronize()
+
+
+# --- the full-size LES-like scene, in the benchmark's launch configuration -------------
+
+@pytest.fixture(scope="module")
+def c1_scene():
+    return scenes.cumulus_scene(seed=1)
+
+
+def test_fullsize_cumulus_direct_beam_and_closure(c1_scene):
+    """256x256x128 scene at 64 photons per column, default launch shape: the
+    direct surface irradiance of 256 sampled columns matches the oracle's
+    deterministic Beer-Lambert transmittance, and the energy ledger closes."""
+    sc = c1_scene
+    sza, az, F0 = 30.0, 0.0, 1000.0
+    N = 64 * sc.ncol
+    B = 6
+    g, st = gpu_batches(sc, sza, az, F0, N, range(B))
+    for s in st:
+        lhs = s["energy_in"] + s["energy_created"] - s["energy_destroyed"] - s["energy_capped"]
+        rhs = s["energy_toa_up"] + s["energy_atm_abs"] + s["energy_sfc_abs"]
+        assert abs(lhs - rhs) < 2e-6 * s["energy_in"]
+        assert s["capped"] == 0
+    rng = np.random.default_rng(0)
+    cols = rng.choice(sc.ncol, 256, replace=False)
+    sub = copy.copy(sc)
+    T = oracle.direct_beam(sub, sza, az, nsub=16).ravel()[cols]
+    want = F0 * np.cos(np.deg2rad(sza)) * T
+    arr = g["sfc_dir"].reshape(B, -1)[:, cols]
+    m = arr.mean(0)
+    se = arr.std(0, ddof=1) / np.sqrt(B)
+    # per-column binomial SE floor for columns whose batches happen to agree
+    se = np.maximum(se, want / np.sqrt(64 * B) * 0.05)
+    z = (m - want) / se
+    assert np.mean(np.abs(z) > 4.5) <= 0.02, np.sort(np.abs(z))[-5:]
+    assert abs(m.mean() / want.mean() - 1) < 0.005
+
+
+def test_fullsize_cumulus_domain_means_match_oracle(c1_scene):
+    sc = c1_scene
+    N = sc.ncol
+    g, _ = gpu_batches(sc, 30.0, 0.0, 1000.0, 4 * N, range(8))
+    o = oracle_batches(sc, 30.0, 0.0, 1000.0, N, range(900, 916))
+    for f in FIELDS:
+        rep = refs.parity_report(g[f], o[f])
+        assert abs(rep["domain_rel"]) < max(0.005, 4 * rep["domain_rel_se"]), (f, rep["domain_rel"], rep["domain_rel_se"])
