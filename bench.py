@@ -222,9 +222,8 @@ def run_ours(args):
              "hr": torch.empty(ncell, dtype=torch.float64, device=dev)}
     for k in ("sfc_dir", "sfc_dif", "toa_up"):
         d_out[k] = torch.empty(ncol, dtype=torch.float64, device=dev)
-    N = args.ppc * ncol
-    total = N * world
-    begin = N * rank
+    from paper_2208_05247_b300 import shard
+    begin, N, total = shard.photon_range(rank, world, args.ppc * ncol)
 
     t = rt.Tracer(scene.nx, scene.ny, scene.nz, scene.dx, scene.dy, scene.dz, stream=stream)
 

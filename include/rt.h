@@ -82,6 +82,9 @@ typedef struct {
     uint32_t max_steps;          /* per-photon cap on events + cell crossings; 0 = 10,000,000 */
     int pcld_mode;               /* RT_PCLD_*; applies from the next rt_set_optics */
     int tally_precision;         /* RT_TALLY_*; applies from the next rt_reset_tallies */
+    int ready_threshold;         /* lanes of a warp that must have an event, surface hit or exit
+                                    pending before the warp handles them together; 0 = 24 */
+    int max_inner;               /* bound on face-crossing sweeps between two such passes; 0 = 16 */
 } rt_options;
 
 typedef struct {

@@ -1,0 +1,108 @@
+"""Launch-parameter autotuner for the transport kernel.
+
+Chooses the coarse-grid factors (majorant resolution), the event-batching
+threshold, the bound on face-crossing sweeps, the refill chunk and the block
+shape by coordinate descent. Each candidate is timed with CUDA events on the
+tracer's stream: majorant build plus one trace of the given photons.
+
+Candidates are ranked by PHOTONS per second, not events per second: a coarser
+majorant adds null collisions, which raises the event count without adding
+information. The returned options are applied to the tracer.
+"""
+from __future__ import annotations
+
+import itertools
+
+
+COARSE = [(2, 2, 2), (4, 4, 2), (4, 4, 4), (8, 8, 4), (4, 4, 8), (8, 8, 8), (16, 16, 4), (16, 16, 8)]
+THRESHOLDS = [8, 16, 24, 28, 32]
+MAX_INNER = [2, 4, 8, 16, 32, 64]
+CHUNKS = [32, 64, 128]
+BLOCKS = [(256, 0), (128, 0), (256, 2), (256, 3)]
+
+
+def _valid_coarse(c, t):
+    return all(1 <= f <= n for f, n in zip(c, (t.nx, t.ny, t.nz)))
+
+
+def time_config(tracer, sza, az, flux, photons, seed, coarse, repeats=2, **opts):
+    """Milliseconds of one majorant build + trace (best of `repeats`)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    tracer.set_stream(stream)
+    tracer.set_options(**opts)
+    best = None
+    for r in range(repeats + 1):
+        tracer.reset()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tracer.build_accel(*coarse)
+        tracer.trace(sza, az, flux, photons, seed + r)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        if r > 0:                        # the first run warms up
+            best = ms if best is None else min(best, ms)
+    st = tracer.stats()
+    return best, st
+
+
+def autotune(tracer, sza, az, flux, photons, seed=1, repeats=2, verbose=False):
+    """Coordinate descent over the launch parameters; returns (best, table).
+
+    `best` holds the coarse factors and the option values; `table` every
+    measurement as dicts (photons/s, events/s, ms).
+    """
+    table = []
+    cur = {"coarse": (4, 4, 4), "ready_threshold": 24, "max_inner": 16, "refill_chunk": 32,
+           "block_size": 256, "blocks_per_sm": 0}
+
+    def measure(cfg):
+        opts = {k: v for k, v in cfg.items() if k != "coarse"}
+        ms, st = time_config(tracer, sza, az, flux, photons, seed, cfg["coarse"], repeats, **opts)
+        row = dict(cfg, ms=ms, photons_per_s=photons / (ms / 1e3), events_per_s=st["events"] / (ms / 1e3),
+                   events=st["events"], crossings=st["crossings"])
+        table.append(row)
+        if verbose:
+            print(row, flush=True)
+        return row
+
+    best = measure(cur)
+    stages = [
+        ("coarse", [c for c in COARSE if _valid_coarse(c, tracer)]),
+        ("ready_threshold", THRESHOLDS),
+        ("max_inner", MAX_INNER),
+        ("refill_chunk", CHUNKS),
+        ("block", BLOCKS),
+    ]
+    for name, values in stages:
+        for v in values:
+            cfg = dict(best)
+            for k in ("ms", "photons_per_s", "events_per_s", "events", "crossings"):
+                cfg.pop(k, None)
+            if name == "block":
+                cfg["block_size"], cfg["blocks_per_sm"] = v
+            else:
+                cfg[name] = v
+            if all(cfg.get(k) == best.get(k) for k in cfg):
+                continue
+            try:
+                row = measure(cfg)
+            except Exception as e:   # e.g. a block shape that does not fit
+                if verbose:
+                    print("skip", cfg, e)
+                continue
+            if row["photons_per_s"] > best["photons_per_s"]:
+                best = row
+    final = {k: best[k] for k in ("coarse", "ready_threshold", "max_inner", "refill_chunk", "block_size",
+                                  "blocks_per_sm")}
+    tracer.set_options(**{k: v for k, v in final.items() if k != "coarse"})
+    tracer.build_accel(*final["coarse"])
+    return final, table
+
+
+def grid(**axes):
+    """Cartesian product helper for explicit sweeps."""
+    keys = list(axes)
+    for vals in itertools.product(*axes.values()):
+        yield dict(zip(keys, vals))

@@ -38,6 +38,8 @@ int fail(int code, const char *fmt, ...)
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr uint32_t kDefaultMaxSteps = 10000000u;
+constexpr int kDefaultReadyThreshold = 24;
+constexpr int kDefaultMaxInner = 16;
 
 template <typename T>
 int dev_alloc(T **p, size_t n)
@@ -240,6 +242,7 @@ int launch_trace(rt_handle h, T *base, double sza, double az, double toa_flux, u
     A.dx = (float)h->dx; A.dy = (float)h->dy; A.dz = (float)h->dz;
     A.inv_dx = (float)(1.0 / h->dx); A.inv_dy = (float)(1.0 / h->dy); A.inv_dz = (float)(1.0 / h->dz);
     A.Lx = (float)(h->nx * h->dx); A.Ly = (float)(h->ny * h->dy); A.H = (float)(h->nz * h->dz);
+    A.cdx = (float)(h->cx * h->dx); A.cdy = (float)(h->cy * h->dy); A.cdz = (float)(h->cz * h->dz);
     const double t = sza * kPi / 180.0, p = az * kPi / 180.0;
     A.sx = (float)(-std::sin(t) * std::sin(p));
     A.sy = (float)(-std::sin(t) * std::cos(p));
@@ -253,6 +256,8 @@ int launch_trace(rt_handle h, T *base, double sza, double az, double toa_flux, u
     A.scale3 = A.energy / (h->dx * h->dy * h->dz);
     A.max_steps = h->opt.max_steps ? h->opt.max_steps : kDefaultMaxSteps;
     A.chunk = (uint32_t)(h->opt.refill_chunk > 0 ? h->opt.refill_chunk : 32);
+    A.ready_threshold = h->opt.ready_threshold > 0 ? h->opt.ready_threshold : kDefaultReadyThreshold;
+    A.max_inner = h->opt.max_inner > 0 ? h->opt.max_inner : kDefaultMaxInner;
 
     const int block = h->opt.block_size > 0 ? h->opt.block_size : 256;
     int bps = h->opt.blocks_per_sm;
@@ -330,6 +335,8 @@ rt_handle rt_create(int nx, int ny, int nz, double dx, double dy, double dz)
     h->opt.blocks_per_sm = 0;
     h->opt.refill_chunk = 32;
     h->opt.max_steps = kDefaultMaxSteps;
+    h->opt.ready_threshold = kDefaultReadyThreshold;
+    h->opt.max_inner = kDefaultMaxInner;
     h->opt.pcld_mode = RT_PCLD_SCATTERING;
     h->opt.tally_precision = RT_TALLY_FP64;
     return h;
@@ -375,6 +382,10 @@ int rt_set_options(rt_handle h, const rt_options *o)
         return fail(RT_E_INVAL, "rt_set_options: blocks_per_sm must be in [0, 32]");
     if (o->refill_chunk < 0 || o->refill_chunk > 4096)
         return fail(RT_E_INVAL, "rt_set_options: refill_chunk must be in [0, 4096]");
+    if (o->ready_threshold < 0 || o->ready_threshold > 32)
+        return fail(RT_E_INVAL, "rt_set_options: ready_threshold must be in [0, 32]");
+    if (o->max_inner < 0 || o->max_inner > 4096)
+        return fail(RT_E_INVAL, "rt_set_options: max_inner must be in [0, 4096]");
     if (o->pcld_mode != RT_PCLD_SCATTERING && o->pcld_mode != RT_PCLD_EXTINCTION)
         return fail(RT_E_INVAL, "rt_set_options: unknown pcld_mode");
     if (o->tally_precision != RT_TALLY_FP64 && o->tally_precision != RT_TALLY_FP32)

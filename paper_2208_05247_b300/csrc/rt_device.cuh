@@ -99,7 +99,7 @@ __device__ __forceinline__ void turn(float &ux, float &uy, float &uz, float mu, 
     } else {
         nx = st * cp;
         ny = st * sp;
-        nz = copysignf(mu, uz);
+        nz = uz > 0.0f ? mu : -mu;
     }
     const float rn = rsqrtf(nx * nx + ny * ny + nz * nz);
     ux = nx * rn;

@@ -46,12 +46,15 @@ struct TraceArgs {
     unsigned long long id_begin, count, ncol;
     int nx, ny, nz, NX, NY, NZ, cx, cy, cz;
     float dx, dy, dz, inv_dx, inv_dy, inv_dz, Lx, Ly, H;
+    float cdx, cdy, cdz;              // coarse cell size [m] (the last cell may be smaller)
     float sx, sy, sz;                 // travel direction of the direct beam
     uint32_t key0, key1;
     double energy;                    // W per unit photon weight
     double scale2, scale3;            // energy / (dx dy), energy / (dx dy dz)
     uint32_t max_steps;
     uint32_t chunk;
+    int ready_threshold;              // lanes that must be ready before an interaction sweep
+    int max_inner;                    // bound on face-crossing sweeps per interaction sweep
 };
 
 // ---------------------------------------------------------------------------
@@ -143,13 +146,24 @@ __device__ __forceinline__ double warp_sum_f64(double v)
 // ---------------------------------------------------------------------------
 // a3-a11: persistent transport kernel.
 //
-// Every warp loops until the photon queue is empty. Each iteration: lanes
-// whose photon has ended take new photon ids (one atomicAdd per warp for a
-// chunk of ids, handed out by ballot rank), then every live lane makes ONE
-// step: either it crosses a face of its coarse cell (subtracting k_max * l from
-// its remaining optical depth) or it has an event inside it. Steps are short
-// and alike, so lanes stay busy even though photon lifetimes differ by orders
-// of magnitude.
+// Every warp loops until the photon queue is empty. One iteration has three
+// phases, each warp-synchronous:
+//
+//  1. refill: lanes whose photon ended take new photon ids (one atomicAdd per
+//     warp for a chunk of ids, handed out by ballot rank) and are born at the
+//     domain top along the sun beam;
+//  2. advance: lanes without a pending interaction cross faces of their coarse
+//     cell (subtracting k_max * l from the remaining optical depth) until the
+//     free path ends inside a cell (an event), the photon reaches the surface
+//     or leaves the top. The sweep repeats until `ready_threshold` lanes are
+//     ready (or none is left to advance, or `max_inner` sweeps), so the costly
+//     interaction code below runs with most lanes active;
+//  3. interact: ready lanes handle their event, surface hit or exit.
+//
+// The walk over the coarse grid is parametric: along a straight segment from
+// origin o with direction u, tn[a] is the distance to the next face on axis a;
+// a crossing updates only the crossed axis. x and y wrap periodically (the
+// origin shifts by the domain length).
 //
 // Events (Sec. 2.3, weights after Iwabuchi 2006): at every majorant event the
 // cell absorbs w k_abs/k_max (heating tally) and w shrinks by the same amount;
@@ -164,6 +178,15 @@ __device__ __forceinline__ double warp_sum_f64(double v)
 // the next block (choice, mu, phi, next free path) and slot 1 of the same
 // block for roulette.
 // ---------------------------------------------------------------------------
+enum : int { kNone = 0, kEvent = 1, kSurface = 2, kTop = 3, kCap = 4 };
+
+template <typename T>
+__device__ __forceinline__ void flush_partial(const TraceArgs<T> &A, int &pcell, bool pdir, float pacc)
+{
+    if (pcell >= 0) tally_add((pdir ? A.tal.abs_dir : A.tal.abs_dif) + pcell, pacc, A.scale3);
+    pcell = -1;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ TraceArgs<T> A)
 {
@@ -171,28 +194,53 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
     const unsigned lane = threadIdx.x & 31u;
     const unsigned below = (1u << lane) - 1u;
 
-    float px = 0.f, py = 0.f, pz = 0.f, ux = 0.f, uy = 0.f, uz = -1.f;
+    // rare counters and the energy ledger live in shared memory
+    __shared__ unsigned long long s_cnt[3];   // surface hits, roulette kills, capped
+    __shared__ double s_led[3];               // created, destroyed, capped energy
+    if (threadIdx.x < 3) { s_cnt[threadIdx.x] = 0; s_led[threadIdx.x] = 0.0; }
+    __syncthreads();
+
+    float ox = 0.f, oy = 0.f, oz = 0.f;       // origin of the current straight segment
+    float ux = 0.f, uy = 0.f, uz = -1.f;      // direction
+    float ivx = 0.f, ivy = 0.f, ivz = 0.f;    // 1/u per axis (used only on axes that move)
+    float tnx = 0.f, tny = 0.f, tnz = 0.f;    // distance from o to the next face per axis
+    float tcur = 0.f;                         // distance from o to the photon
     float w = 0.f, tau = 0.f, kmaj = 0.f;
     int I = 0, J = 0, K = 0;
     unsigned long long gid = 0;
     uint32_t blk = 0, steps = 0, nev = 0;
     bool alive = false, direct = false;
+    int ready = kNone;
     int pcell = -1;
     bool pdir = false;
     float pacc = 0.f;
 
-    uint32_t c_ph = 0, c_ev = 0, c_sc = 0, c_cr = 0, c_sf = 0, c_rk = 0, c_cap = 0, c_max = 0;
-    double e_cr = 0.0, e_de = 0.0, e_cap = 0.0;
+    uint32_t c_ph = 0, c_ev = 0, c_sc = 0, c_cr = 0, c_max = 0;
 
     unsigned long long pool_next = 0, pool_end = 0;
     bool exhausted = false;
 
     const uint32_t k0 = A.key0, k1 = A.key1;
 
+    // distances to the next coarse faces from origin o along u, for cell (I,J,K)
+    // An axis along which the photon does not move gets an infinite distance and
+    // is never crossed, so its reciprocal is never used.
+    auto start_segment = [&]() {
+        tcur = 0.f;
+        ivx = __frcp_rn(ux); ivy = __frcp_rn(uy); ivz = __frcp_rn(uz);
+        tnx = ux > 0.f ? (fminf((float)(I + 1) * A.cdx, A.Lx) - ox) * ivx
+            : ux < 0.f ? ((float)I * A.cdx - ox) * ivx : INFINITY;
+        tny = uy > 0.f ? (fminf((float)(J + 1) * A.cdy, A.Ly) - oy) * ivy
+            : uy < 0.f ? ((float)J * A.cdy - oy) * ivy : INFINITY;
+        tnz = uz > 0.f ? (fminf((float)(K + 1) * A.cdz, A.H) - oz) * ivz
+            : uz < 0.f ? ((float)K * A.cdz - oz) * ivz : INFINITY;
+        tnx = fmaxf(tnx, 0.f); tny = fmaxf(tny, 0.f); tnz = fmaxf(tnz, 0.f);
+    };
+
     for (;;) {
+        // ---------------- 1. refill ----------------
         const unsigned dead = __ballot_sync(kFull, !alive);
         if (dead) {
-            // ---- warp-level refill ----
             const unsigned ndead = __popc(dead);
             const unsigned rank = __popc(dead & below);
             const unsigned long long avail = pool_end - pool_next;
@@ -225,176 +273,201 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
                 const unsigned col = (unsigned)(gid % A.ncol);
                 const int ci = (int)(col % (unsigned)A.nx), cj = (int)(col / (unsigned)A.nx);
                 const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), 0u, 0u), k0, k1);
-                px = ((float)ci + u01(r.x)) * A.dx;
-                py = ((float)cj + u01(r.y)) * A.dy;
-                pz = A.H;
+                ox = ((float)ci + u01(r.x)) * A.dx;
+                oy = ((float)cj + u01(r.y)) * A.dy;
+                oz = A.H;
                 ux = A.sx; uy = A.sy; uz = A.sz;
                 tau = -__logf(u01(r.z));
                 w = 1.f;
                 direct = true;
                 alive = true;
+                ready = kNone;
                 I = ci / A.cx; J = cj / A.cy; K = A.NZ - 1;
                 kmaj = __ldg(A.kmax + ((size_t)K * A.NY + J) * A.NX + I);
+                start_segment();
                 blk = 1; steps = 0; nev = 0;
                 ++c_ph;
             }
             if (!__any_sync(kFull, alive)) break;
         }
-        if (!alive) continue;
 
-        bool end_photon = false;
-        if (++steps > A.max_steps) {
-            // step cap: record, stop the photon, never spin
-            ++c_cap;
-            e_cap += (double)w * A.energy;
-            atomicOr(&A.scr->status, kStatusBudget);
-            end_photon = true;
-        } else {
-            const int ilo = I * A.cx, ihi = min(ilo + A.cx, A.nx);
-            const int jlo = J * A.cy, jhi = min(jlo + A.cy, A.ny);
-            const int klo = K * A.cz, khi = min(klo + A.cz, A.nz);
-            const float bx = (float)(ux > 0.f ? ihi : ilo) * A.dx;
-            const float by = (float)(uy > 0.f ? jhi : jlo) * A.dy;
-            const float bz = (float)(uz > 0.f ? khi : klo) * A.dz;
-            const float tx = ux != 0.f ? fmaxf(0.f, __fdividef(bx - px, ux)) : INFINITY;
-            const float ty = uy != 0.f ? fmaxf(0.f, __fdividef(by - py, uy)) : INFINITY;
-            const float tz = uz != 0.f ? fmaxf(0.f, __fdividef(bz - pz, uz)) : INFINITY;
-            float smin = tx;
-            int axis = 0;
-            if (ty < smin) { smin = ty; axis = 1; }
-            if (tz < smin) { smin = tz; axis = 2; }
-
-            if (kmaj * smin > tau) {
-                // ---- a4/a5: majorant event inside this coarse cell ----
-                const float s = __fdividef(tau, kmaj);
-                px = fmaf(ux, s, px); py = fmaf(uy, s, py); pz = fmaf(uz, s, pz);
-                const int fi = min(max((int)(px * A.inv_dx), ilo), ihi - 1);
-                const int fj = min(max((int)(py * A.inv_dy), jlo), jhi - 1);
-                const int fk = min(max((int)(pz * A.inv_dz), klo), khi - 1);
-                const int cell = (fk * A.ny + fj) * A.nx + fi;
-                const float4 o = __ldg(A.rec + cell);
-                const float wn = w * (1.0f - __fdividef(o.x, kmaj));
-                const float dep = w - wn;
-                if (cell != pcell || direct != pdir) {
-                    if (pcell >= 0) tally_add((pdir ? A.tal.abs_dir : A.tal.abs_dif) + pcell, pacc, A.scale3);
-                    pcell = cell; pdir = direct; pacc = 0.f;
+        // ---------------- 2. advance (a4) ----------------
+        for (int it = 0; it < A.max_inner; ++it) {
+            const bool pend = alive && ready == kNone;
+            const unsigned pm = __ballot_sync(kFull, pend);
+            if (!pm) break;
+            if (it > 0 && __popc(__ballot_sync(kFull, ready != kNone)) >= A.ready_threshold) break;
+            if (!pend) continue;
+            if (++steps > A.max_steps) { ready = kCap; continue; }
+            float tm;
+            int ax;
+            if (tnx <= tny && tnx <= tnz) { tm = tnx; ax = 0; }
+            else if (tny <= tnz) { tm = tny; ax = 1; }
+            else { tm = tnz; ax = 2; }
+            const float dt = fmaxf(tm - tcur, 0.f);
+            if (kmaj * dt > tau) {
+                tcur += __fdividef(tau, kmaj);     // the free path ends in this coarse cell
+                ready = kEvent;
+                continue;
+            }
+            tau = fmaf(-kmaj, dt, tau);
+            tcur = tm;
+            ++c_cr;
+            if (ax == 0) {
+                if (ux > 0.f) {
+                    if (++I == A.NX) { I = 0; ox -= A.Lx; }
+                    tnx = (fminf((float)(I + 1) * A.cdx, A.Lx) - ox) * ivx;
+                } else {
+                    if (--I < 0) { I = A.NX - 1; ox += A.Lx; }
+                    tnx = ((float)I * A.cdx - ox) * ivx;
                 }
-                pacc += dep;
-                w = wn;
-                ++c_ev; ++nev;
-                const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk, 0u), k0, k1);
-                ++blk;
-                // ---- a6/a7: real scattering or null collision ----
-                const float den = kmaj - o.x;
-                if (den > 0.f) {
-                    const float rd = 1.0f / den;
-                    const float xi = u01(r.x);
-                    if (xi < o.y * rd) {
-                        const float mu = (xi < o.z * rd) ? hg_mu(o.w, u01(r.y)) : rayleigh_mu(u01(r.y));
-                        float sp, cp;
-                        azimuth(u01(r.z), sp, cp);
-                        turn(ux, uy, uz, mu, sp, cp);
-                        direct = false;
-                        ++c_sc;
-                    }
-                }
-                tau = -__logf(u01(r.w));
-                // ---- a8: roulette ----
-                if (w < 0.5f) {
-                    const uint4 q = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk - 1u, 1u), k0, k1);
-                    if (u01(q.x) > w) {
-                        e_de += (double)w * A.energy;
-                        ++c_rk;
-                        end_photon = true;
-                    } else {
-                        e_cr += (double)(1.0f - w) * A.energy;
-                        w = 1.f;
-                    }
+            } else if (ax == 1) {
+                if (uy > 0.f) {
+                    if (++J == A.NY) { J = 0; oy -= A.Ly; }
+                    tny = (fminf((float)(J + 1) * A.cdy, A.Ly) - oy) * ivy;
+                } else {
+                    if (--J < 0) { J = A.NY - 1; oy += A.Ly; }
+                    tny = ((float)J * A.cdy - oy) * ivy;
                 }
             } else {
-                // ---- a4: cross a face of the coarse cell ----
-                tau = fmaf(-kmaj, smin, tau);
-                ++c_cr;
-                if (axis == 0) {
-                    py = fmaf(uy, smin, py); pz = fmaf(uz, smin, pz);
-                    px = bx;
-                    if (ux > 0.f) { if (++I == A.NX) { I = 0; px = 0.f; } }
-                    else { if (--I < 0) { I = A.NX - 1; px = A.Lx; } }
-                } else if (axis == 1) {
-                    px = fmaf(ux, smin, px); pz = fmaf(uz, smin, pz);
-                    py = by;
-                    if (uy > 0.f) { if (++J == A.NY) { J = 0; py = 0.f; } }
-                    else { if (--J < 0) { J = A.NY - 1; py = A.Ly; } }
+                if (uz > 0.f) {
+                    if (++K == A.NZ) { ready = kTop; continue; }
+                    tnz = (fminf((float)(K + 1) * A.cdz, A.H) - oz) * ivz;
                 } else {
-                    px = fmaf(ux, smin, px); py = fmaf(uy, smin, py);
-                    pz = bz;
-                    K += (uz > 0.f) ? 1 : -1;
+                    if (--K < 0) { ready = kSurface; continue; }
+                    tnz = ((float)K * A.cdz - oz) * ivz;
                 }
-                if (K < 0) {
-                    // ---- a9: Lambertian surface ----
-                    K = 0; pz = 0.f;
-                    const int fi = min(max((int)(px * A.inv_dx), ilo), ihi - 1);
-                    const int fj = min(max((int)(py * A.inv_dy), jlo), jhi - 1);
-                    const int col = fj * A.nx + fi;
-                    tally_add((direct ? A.tal.sfc_dir : A.tal.sfc_dif) + col, w, A.scale2);
-                    ++c_sf;
-                    w *= __ldg(A.alb + col);
+            }
+            kmaj = __ldg(A.kmax + ((size_t)K * A.NY + J) * A.NX + I);
+        }
+
+        // ---------------- 3. interact ----------------
+        if (ready == kNone) continue;
+        bool end_photon = false;
+        const int ilo = I * A.cx, ihi = min(ilo + A.cx, A.nx);
+        const int jlo = J * A.cy, jhi = min(jlo + A.cy, A.ny);
+        const float px = fmaf(ux, tcur, ox), py = fmaf(uy, tcur, oy);
+        const int fi = min(max((int)(px * A.inv_dx), ilo), ihi - 1);
+        const int fj = min(max((int)(py * A.inv_dy), jlo), jhi - 1);
+        if (ready == kEvent) {
+            // ---- a5: majorant event: absorb a fraction of the weight ----
+            ++steps;
+            const float pz = fmaf(uz, tcur, oz);
+            const int klo = K * A.cz, khi = min(klo + A.cz, A.nz);
+            const int fk = min(max((int)(pz * A.inv_dz), klo), khi - 1);
+            const int cell = (fk * A.ny + fj) * A.nx + fi;
+            const float4 o = __ldg(A.rec + cell);
+            const float pabs = fminf(__fdividef(o.x, kmaj), 1.0f);
+            const float wn = w * (1.0f - pabs);
+            if (cell != pcell || direct != pdir) {
+                flush_partial(A, pcell, pdir, pacc);
+                pcell = cell; pdir = direct; pacc = 0.f;
+            }
+            pacc += w - wn;
+            w = wn;
+            ++c_ev; ++nev;
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk, 0u), k0, k1);
+            ++blk;
+            // ---- a6/a7: real scattering or null collision ----
+            ox = px; oy = py; oz = pz;
+            const float den = kmaj - o.x;
+            bool scattered = false;
+            if (den > 0.f) {
+                const float rd = 1.0f / den;
+                const float xi = u01(r.x);
+                if (xi < o.y * rd) {
+                    const float mu = (xi < o.z * rd) ? hg_mu(o.w, u01(r.y)) : rayleigh_mu(u01(r.y));
+                    float sp, cp;
+                    azimuth(u01(r.z), sp, cp);
+                    turn(ux, uy, uz, mu, sp, cp);
                     direct = false;
-                    const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk, 0u), k0, k1);
-                    ++blk;
-                    lambert_up(ux, uy, uz, u01(r.x), u01(r.y));
-                    tau = -__logf(u01(r.w));
-                    if (w < 0.5f) {
-                        if (u01(r.z) > w) {
-                            e_de += (double)w * A.energy;
-                            ++c_rk;
-                            end_photon = true;
-                        } else {
-                            e_cr += (double)(1.0f - w) * A.energy;
-                            w = 1.f;
-                        }
-                    }
-                } else if (K >= A.NZ) {
-                    // ---- a10: leaves through the domain top ----
-                    const int fi = min(max((int)(px * A.inv_dx), ilo), ihi - 1);
-                    const int fj = min(max((int)(py * A.inv_dy), jlo), jhi - 1);
-                    tally_add(A.tal.toa + (fj * A.nx + fi), w, A.scale2);
+                    scattered = true;
+                    ++c_sc;
+                }
+            }
+            if (scattered) {
+                start_segment();
+            } else {
+                tnx -= tcur; tny -= tcur; tnz -= tcur;
+                tcur = 0.f;
+            }
+            tau = -__logf(u01(r.w));
+            // ---- a8: roulette ----
+            if (w < 0.5f) {
+                const uint4 q = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk - 1u, 1u), k0, k1);
+                if (u01(q.x) > w) {
+                    atomicAdd(&s_led[1], (double)w * A.energy);
+                    atomicAdd(&s_cnt[1], 1ull);
                     end_photon = true;
                 } else {
-                    kmaj = __ldg(A.kmax + ((size_t)K * A.NY + J) * A.NX + I);
+                    atomicAdd(&s_led[0], (double)(1.0f - w) * A.energy);
+                    w = 1.f;
                 }
             }
-        }
-        if (end_photon) {
-            if (pcell >= 0) {
-                tally_add((pdir ? A.tal.abs_dir : A.tal.abs_dif) + pcell, pacc, A.scale3);
-                pcell = -1;
+        } else if (ready == kSurface) {
+            // ---- a9: Lambertian surface ----
+            ++steps;
+            const int col = fj * A.nx + fi;
+            tally_add((direct ? A.tal.sfc_dir : A.tal.sfc_dif) + col, w, A.scale2);
+            atomicAdd(&s_cnt[0], 1ull);
+            w *= __ldg(A.alb + col);
+            direct = false;
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk, 0u), k0, k1);
+            ++blk;
+            lambert_up(ux, uy, uz, u01(r.x), u01(r.y));
+            tau = -__logf(u01(r.w));
+            K = 0;
+            ox = px; oy = py; oz = 0.f;
+            start_segment();
+            if (w < 0.5f) {
+                if (u01(r.z) > w) {
+                    atomicAdd(&s_led[1], (double)w * A.energy);
+                    atomicAdd(&s_cnt[1], 1ull);
+                    end_photon = true;
+                } else {
+                    atomicAdd(&s_led[0], (double)(1.0f - w) * A.energy);
+                    w = 1.f;
+                }
             }
+        } else if (ready == kTop) {
+            // ---- a10: leaves through the domain top ----
+            tally_add(A.tal.toa + (fj * A.nx + fi), w, A.scale2);
+            end_photon = true;
+        } else {
+            // step cap: record, stop the photon, never spin
+            atomicAdd(&s_cnt[2], 1ull);
+            atomicAdd(&s_led[2], (double)w * A.energy);
+            atomicOr(&A.scr->status, kStatusBudget);
+            end_photon = true;
+        }
+        ready = kNone;
+        if (end_photon) {
+            flush_partial(A, pcell, pdir, pacc);
             alive = false;
             c_max = max(c_max, nev);
         }
     }
 
-    // ---- counters: warp reduction, one atomic per warp ----
+    // ---- counters: warp reduction, one atomic per warp; block totals once ----
     const unsigned long long s_ph = warp_sum_u32(c_ph), s_ev = warp_sum_u32(c_ev),
-                             s_sc = warp_sum_u32(c_sc), s_cr = warp_sum_u32(c_cr),
-                             s_sf = warp_sum_u32(c_sf), s_rk = warp_sum_u32(c_rk),
-                             s_cap = warp_sum_u32(c_cap);
+                             s_sc = warp_sum_u32(c_sc), s_cr = warp_sum_u32(c_cr);
     const unsigned m_ev = __reduce_max_sync(kFull, c_max);
-    const double d_cr = warp_sum_f64(e_cr), d_de = warp_sum_f64(e_de), d_cap = warp_sum_f64(e_cap);
+    Scratch *S = A.scr;
     if (lane == 0) {
-        Scratch *S = A.scr;
         if (s_ph) atomicAdd(&S->photons, s_ph);
         if (s_ev) atomicAdd(&S->events, s_ev);
         if (s_sc) atomicAdd(&S->scatters, s_sc);
         if (s_cr) atomicAdd(&S->crossings, s_cr);
-        if (s_sf) atomicAdd(&S->surface_hits, s_sf);
-        if (s_rk) atomicAdd(&S->roulette_kills, s_rk);
-        if (s_cap) atomicAdd(&S->capped, s_cap);
         if (m_ev) atomicMax(&S->max_events, (unsigned long long)m_ev);
-        if (d_cr != 0.0) atomicAdd(&S->created, d_cr);
-        if (d_de != 0.0) atomicAdd(&S->destroyed, d_de);
-        if (d_cap != 0.0) atomicAdd(&S->capped_energy, d_cap);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_cnt[0]) atomicAdd(&S->surface_hits, s_cnt[0]);
+        if (s_cnt[1]) atomicAdd(&S->roulette_kills, s_cnt[1]);
+        if (s_cnt[2]) atomicAdd(&S->capped, s_cnt[2]);
+        if (s_led[0] != 0.0) atomicAdd(&S->created, s_led[0]);
+        if (s_led[1] != 0.0) atomicAdd(&S->destroyed, s_led[1]);
+        if (s_led[2] != 0.0) atomicAdd(&S->capped_energy, s_led[2]);
     }
 }
 

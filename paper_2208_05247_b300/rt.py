@@ -32,7 +32,8 @@ class RtError(RuntimeError):
 class rt_options(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("refill_chunk", ctypes.c_int), ("max_steps", ctypes.c_uint32),
-                ("pcld_mode", ctypes.c_int), ("tally_precision", ctypes.c_int)]
+                ("pcld_mode", ctypes.c_int), ("tally_precision", ctypes.c_int),
+                ("ready_threshold", ctypes.c_int), ("max_inner", ctypes.c_int)]
 
 
 class rt_stats_t(ctypes.Structure):

@@ -158,29 +158,46 @@ def zscores(m1, se1, m2, se2):
     return z
 
 
-def parity_report(gpu_batches, orc_batches, z_limit=4.0):
+def parity_report(gpu_batches, orc_batches, z_limit=4.0, min_nonzero=0.9):
     """Cell-wise statistical parity of two sets of independent batch results.
 
-    gpu_batches, orc_batches: arrays [B, ...]. Per cell z = (m1 - m2) /
-    sqrt(se1^2 + se2^2) with batch standard errors. Returns the fraction of
-    cells with |z| > z_limit, the bound it is held to (the larger of 3 cells
-    and twice the Student-t tail with B-1 dof), the largest |z| and the
-    relative difference of the domain sums.
+    gpu_batches, orc_batches: arrays [B, ...] (3D fields [B, nz, ny, nx] or 2D
+    [B, ny, nx]). A cell is well sampled when both sides score in at least
+    `min_nonzero` of their batches; for those, z = (m1 - m2) / sqrt(se1^2 + se2^2)
+    with batch standard errors. Cells that a collision estimator scores only
+    rarely have no usable per-cell variance, so they are pooled (summed) per
+    layer of a 3D field, or all together for a 2D field, and the pooled sums get
+    the same z test. Returns the fraction of well-sampled cells with
+    |z| > z_limit and the bound it is held to (the larger of 3 cells and twice
+    the two-sided Student-t tail with B-1 dof), the largest pooled |z|, and the
+    relative difference of the domain sums with its standard error.
     """
     from scipy import stats as st
     g = np.asarray(gpu_batches, dtype=np.float64)
     o = np.asarray(orc_batches, dtype=np.float64)
     B1, B2 = g.shape[0], o.shape[0]
+    good = ((g != 0).mean(0) >= min_nonzero) & ((o != 0).mean(0) >= min_nonzero)
     mg, mo = g.mean(0), o.mean(0)
     sg, so = g.std(0, ddof=1) / np.sqrt(B1), o.std(0, ddof=1) / np.sqrt(B2)
-    z = zscores(mg, sg, mo, so).ravel()
+    z = zscores(mg, sg, mo, so)[good].ravel()
     n = z.size
-    frac = float(np.mean(np.abs(z) > z_limit))
+    frac = float(np.mean(np.abs(z) > z_limit)) if n else 0.0
     dof = min(B1, B2) - 1
-    bound = max(3.0 / n, 2.0 * 2.0 * st.t.sf(z_limit, dof))
+    bound = max(3.0 / max(n, 1), 2.0 * 2.0 * st.t.sf(z_limit, dof))
+    # pooled rare cells
+    rare = ~good
+    if g.ndim == 4:
+        pg = np.where(rare[None], g, 0).sum(axis=(2, 3))    # [B, nz]
+        po = np.where(rare[None], o, 0).sum(axis=(2, 3))
+    else:
+        pg = np.where(rare[None], g, 0).reshape(B1, -1).sum(1)[:, None]
+        po = np.where(rare[None], o, 0).reshape(B2, -1).sum(1)[:, None]
+    zp = zscores(pg.mean(0), pg.std(0, ddof=1) / np.sqrt(B1), po.mean(0), po.std(0, ddof=1) / np.sqrt(B2))
+    zp = zp[(pg != 0).any(0) | (po != 0).any(0)]
     tot_g, tot_o = g.reshape(B1, -1).sum(1), o.reshape(B2, -1).sum(1)
     rel = float((tot_g.mean() - tot_o.mean()) / tot_o.mean()) if tot_o.mean() != 0 else 0.0
     se_rel = float(np.sqrt(tot_g.var(ddof=1) / B1 + tot_o.var(ddof=1) / B2) / abs(tot_o.mean())) \
         if tot_o.mean() != 0 else 0.0
     return {"frac_over": frac, "bound": bound, "max_abs_z": float(np.max(np.abs(z))) if n else 0.0,
-            "n": n, "domain_rel": rel, "domain_rel_se": se_rel, "z": z}
+            "n": n, "n_total": int(good.size), "pooled_max_abs_z": float(np.max(np.abs(zp))) if zp.size else 0.0,
+            "domain_rel": rel, "domain_rel_se": se_rel, "z": z}

@@ -168,9 +168,9 @@ def test_gpu_thin_slab_single_scattering_oblique(phase):
 @pytest.fixture(scope="module")
 def c0_parity():
     sc = scenes.ellipsoid_scene(seed=0)
-    B, N = 24, 2 ** 18
-    g, st = gpu_batches(sc, 30.0, 0.0, 1000.0, N, range(100, 100 + B))
-    o = oracle_batches(sc, 30.0, 0.0, 1000.0, N, range(500, 500 + B))
+    B = 24
+    g, st = gpu_batches(sc, 30.0, 0.0, 1000.0, 2 ** 22, range(100, 100 + B))
+    o = oracle_batches(sc, 30.0, 0.0, 1000.0, 2 ** 18, range(500, 500 + B))
     return sc, g, o, st
 
 
@@ -179,6 +179,8 @@ def test_parity_cellwise_with_oracle(c0_parity, field):
     _, g, o, _ = c0_parity
     rep = refs.parity_report(g[field], o[field])
     assert rep["frac_over"] <= rep["bound"], (field, rep["frac_over"], rep["bound"], rep["max_abs_z"])
+    assert rep["n"] >= 0.8 * rep["n_total"], (field, rep["n"], rep["n_total"])
+    assert rep["pooled_max_abs_z"] < 4.5, (field, rep["pooled_max_abs_z"])
     # the standardised differences look like noise (KS against the normal law)
     z = rep["z"][np.isfinite(rep["z"])]
     assert stats.kstest(z, "norm").pvalue > 1e-4 or np.std(z) < 1.15, (field, np.std(z))
@@ -199,7 +201,7 @@ def test_energy_ledger_closes(c0_parity):
         rhs = s["energy_toa_up"] + s["energy_atm_abs"] + s["energy_sfc_abs"]
         assert abs(lhs - rhs) < 2e-6 * s["energy_in"], (lhs, rhs)
         assert s["status"] == 0 and s["capped"] == 0
-        assert s["photons"] == 2 ** 18
+        assert s["photons"] == 2 ** 22
 
 
 # --- reproducibility, launch-geometry and partition invariance -----------------------
@@ -390,8 +392,10 @@ def test_fullsize_cumulus_direct_beam_and_closure(c1_scene):
     arr = g["sfc_dir"].reshape(B, -1)[:, cols]
     m = arr.mean(0)
     se = arr.std(0, ddof=1) / np.sqrt(B)
-    # per-column binomial SE floor for columns whose batches happen to agree
-    se = np.maximum(se, want / np.sqrt(64 * B) * 0.05)
+    # Shadowed columns may see no direct photon in any batch; bound the standard
+    # error from below by that of the direct-arrival fraction (weights <= 1).
+    Tm = np.clip(T, 0.0, 1.0)
+    se = np.maximum(se, F0 * np.cos(np.deg2rad(sza)) * np.sqrt(Tm * (1 - Tm) / (64 * B)) + 1e-9)
     z = (m - want) / se
     assert np.mean(np.abs(z) > 4.5) <= 0.02, np.sort(np.abs(z))[-5:]
     assert abs(m.mean() / want.mean() - 1) < 0.005

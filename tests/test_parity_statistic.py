@@ -22,6 +22,7 @@ def test_criterion_passes_for_independent_oracle_runs(small_scene):
     for f in oracle.FIELDS:
         rep = refs.parity_report(a[f], b[f])
         assert rep["frac_over"] <= rep["bound"], (f, rep["frac_over"], rep["bound"])
+        assert rep["pooled_max_abs_z"] < 4.5, (f, rep["pooled_max_abs_z"])
         assert abs(rep["domain_rel"]) < 4 * rep["domain_rel_se"] + 1e-12
 
 
