@@ -158,12 +158,16 @@ def zscores(m1, se1, m2, se2):
     return z
 
 
-def parity_report(gpu_batches, orc_batches, z_limit=4.0, min_nonzero=0.9):
+def parity_report(gpu_batches, orc_batches, z_limit=4.0, min_nonzero=0.9, pilot=None):
     """Cell-wise statistical parity of two sets of independent batch results.
 
     gpu_batches, orc_batches: arrays [B, ...] (3D fields [B, nz, ny, nx] or 2D
     [B, ny, nx]). A cell is well sampled when both sides score in at least
-    `min_nonzero` of their batches; for those, z = (m1 - m2) / sqrt(se1^2 + se2^2)
+    `min_nonzero` of their batches of `pilot` = (gpu_pilot, orc_pilot), which
+    must be independent of the batches under test: choosing cells from the
+    tested batches themselves would select cells where one side happened to
+    score low and bias the pooled sums. For well-sampled cells,
+    z = (m1 - m2) / sqrt(se1^2 + se2^2)
     with batch standard errors. Cells that a collision estimator scores only
     rarely have no usable per-cell variance, so they are pooled (summed) per
     layer of a 3D field, or all together for a 2D field, and the pooled sums get
@@ -176,7 +180,10 @@ def parity_report(gpu_batches, orc_batches, z_limit=4.0, min_nonzero=0.9):
     g = np.asarray(gpu_batches, dtype=np.float64)
     o = np.asarray(orc_batches, dtype=np.float64)
     B1, B2 = g.shape[0], o.shape[0]
-    good = ((g != 0).mean(0) >= min_nonzero) & ((o != 0).mean(0) >= min_nonzero)
+    if pilot is None:
+        raise ValueError("parity_report needs independent pilot batches for cell selection")
+    pg_, po_ = (np.asarray(x, dtype=np.float64) for x in pilot)
+    good = ((pg_ != 0).mean(0) >= min_nonzero) & ((po_ != 0).mean(0) >= min_nonzero)
     mg, mo = g.mean(0), o.mean(0)
     sg, so = g.std(0, ddof=1) / np.sqrt(B1), o.std(0, ddof=1) / np.sqrt(B2)
     z = zscores(mg, sg, mo, so)[good].ravel()
@@ -201,3 +208,15 @@ def parity_report(gpu_batches, orc_batches, z_limit=4.0, min_nonzero=0.9):
     return {"frac_over": frac, "bound": bound, "max_abs_z": float(np.max(np.abs(z))) if n else 0.0,
             "n": n, "n_total": int(good.size), "pooled_max_abs_z": float(np.max(np.abs(zp))) if zp.size else 0.0,
             "domain_rel": rel, "domain_rel_se": se_rel, "z": z}
+
+
+def domain_compare(gpu_batches, orc_batches):
+    """Relative difference of the domain sums of two batch sets and its SE."""
+    g = np.asarray(gpu_batches, dtype=np.float64)
+    o = np.asarray(orc_batches, dtype=np.float64)
+    tg, to = g.reshape(g.shape[0], -1).sum(1), o.reshape(o.shape[0], -1).sum(1)
+    m = to.mean()
+    if m == 0:
+        return 0.0, 0.0
+    se = np.sqrt(tg.var(ddof=1) / tg.size + to.var(ddof=1) / to.size) / abs(m)
+    return float((tg.mean() - m) / m), float(se)

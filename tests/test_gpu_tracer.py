@@ -171,13 +171,16 @@ def c0_parity():
     B = 24
     g, st = gpu_batches(sc, 30.0, 0.0, 1000.0, 2 ** 22, range(100, 100 + B))
     o = oracle_batches(sc, 30.0, 0.0, 1000.0, 2 ** 18, range(500, 500 + B))
-    return sc, g, o, st
+    # independent pilot batches decide which cells are sampled well enough to test alone
+    gp, _ = gpu_batches(sc, 30.0, 0.0, 1000.0, 2 ** 22, range(200, 208))
+    op = oracle_batches(sc, 30.0, 0.0, 1000.0, 2 ** 18, range(600, 608))
+    return sc, g, o, st, (gp, op)
 
 
 @pytest.mark.parametrize("field", FIELDS)
 def test_parity_cellwise_with_oracle(c0_parity, field):
-    _, g, o, _ = c0_parity
-    rep = refs.parity_report(g[field], o[field])
+    _, g, o, _, (gp, op) = c0_parity
+    rep = refs.parity_report(g[field], o[field], pilot=(gp[field], op[field]))
     assert rep["frac_over"] <= rep["bound"], (field, rep["frac_over"], rep["bound"], rep["max_abs_z"])
     assert rep["n"] >= 0.8 * rep["n_total"], (field, rep["n"], rep["n_total"])
     assert rep["pooled_max_abs_z"] < 4.5, (field, rep["pooled_max_abs_z"])
@@ -188,14 +191,14 @@ def test_parity_cellwise_with_oracle(c0_parity, field):
 
 @pytest.mark.parametrize("field", FIELDS)
 def test_parity_domain_means_within_half_percent(c0_parity, field):
-    _, g, o, _ = c0_parity
-    rep = refs.parity_report(g[field], o[field])
+    _, g, o, _, (gp, op) = c0_parity
+    rep = refs.parity_report(g[field], o[field], pilot=(gp[field], op[field]))
     assert abs(rep["domain_rel"]) < 0.005, (field, rep["domain_rel"], rep["domain_rel_se"])
     assert abs(rep["domain_rel"]) < 4 * rep["domain_rel_se"] + 1e-9
 
 
 def test_energy_ledger_closes(c0_parity):
-    _, _, _, st = c0_parity
+    _, _, _, st, _ = c0_parity
     for s in st:
         lhs = s["energy_in"] + s["energy_created"] - s["energy_destroyed"] - s["energy_capped"]
         rhs = s["energy_toa_up"] + s["energy_atm_abs"] + s["energy_sfc_abs"]
@@ -247,8 +250,8 @@ def test_coarse_factors_do_not_change_the_expectation(small_scene):
     base = res[(4, 4, 4)]
     for c, g in res.items():
         for f in ("sfc_dif", "toa_up", "abs_dif"):
-            rep = refs.parity_report(g[f], base[f])
-            assert abs(rep["domain_rel"]) < 4 * rep["domain_rel_se"] + 1e-12, (c, f, rep["domain_rel"])
+            rel, se = refs.domain_compare(g[f], base[f])
+            assert abs(rel) < 4 * se + 1e-12, (c, f, rel, se)
 
 
 # --- precision, modes and buffers ----------------------------------------------------
@@ -407,5 +410,5 @@ def test_fullsize_cumulus_domain_means_match_oracle(c1_scene):
     g, _ = gpu_batches(sc, 30.0, 0.0, 1000.0, 4 * N, range(8))
     o = oracle_batches(sc, 30.0, 0.0, 1000.0, N, range(900, 916))
     for f in FIELDS:
-        rep = refs.parity_report(g[f], o[f])
-        assert abs(rep["domain_rel"]) < max(0.005, 4 * rep["domain_rel_se"]), (f, rep["domain_rel"], rep["domain_rel_se"])
+        rel, se = refs.domain_compare(g[f], o[f])
+        assert abs(rel) < max(0.005, 4 * se), (f, rel, se)

@@ -19,8 +19,10 @@ def _batches(scene, seeds, n):
 def test_criterion_passes_for_independent_oracle_runs(small_scene):
     a = _batches(small_scene, range(1000, 1016), 2 ** 15)
     b = _batches(small_scene, range(2000, 2016), 2 ** 15)
+    pa = _batches(small_scene, range(1100, 1108), 2 ** 15)
+    pb = _batches(small_scene, range(2100, 2108), 2 ** 15)
     for f in oracle.FIELDS:
-        rep = refs.parity_report(a[f], b[f])
+        rep = refs.parity_report(a[f], b[f], pilot=(pa[f], pb[f]))
         assert rep["frac_over"] <= rep["bound"], (f, rep["frac_over"], rep["bound"])
         assert rep["pooled_max_abs_z"] < 4.5, (f, rep["pooled_max_abs_z"])
         assert abs(rep["domain_rel"]) < 4 * rep["domain_rel_se"] + 1e-12
@@ -33,5 +35,7 @@ def test_criterion_catches_a_planted_error(small_scene):
     wrong.ssa_cld[cloudy] = np.float32(0.97)          # planted: 3 % cloud absorption
     a = _batches(small_scene, range(3000, 3016), 2 ** 15)
     b = _batches(wrong, range(4000, 4016), 2 ** 15)
-    rep = refs.parity_report(a["sfc_dif"], b["sfc_dif"])
+    pa = _batches(small_scene, range(3100, 3104), 2 ** 15)
+    pb = _batches(wrong, range(4100, 4104), 2 ** 15)
+    rep = refs.parity_report(a["sfc_dif"], b["sfc_dif"], pilot=(pa["sfc_dif"], pb["sfc_dif"]))
     assert rep["frac_over"] > rep["bound"] or abs(rep["domain_rel"]) > 4 * rep["domain_rel_se"]
