@@ -195,6 +195,46 @@ const char *rt_last_error(void);
  * way to learn why rt_create returned NULL. */
 int rt_last_error_code(void);
 
+/* ---- tracing without any allocation ---- */
+
+/* The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory -- for example an atmospheric model that reserves all
+ * of its GPU memory in one pool at start-up and may not allocate inside its
+ * time loop, or a host framework whose own allocator must own every buffer.
+ * rt_create allocates, so such callers cannot hold a handle.
+ *
+ * Traces `photons` photons exactly as rt_trace does (Sec. 2.3; same random
+ * streams for the same seed, scatterer choice RT_PCLD_SCATTERING) and ADDS
+ * their contribution to the caller's output buffers, in the units of
+ * rt_fields / rt_fields_split. Every pointer is device memory of the current
+ * device and is owned by the caller:
+ *   inputs  k_gas, ssa_gas, k_cld, ssa_cld, g_cld: nx*ny*nz floats [nz][ny][nx];
+ *           albedo: nx*ny floats
+ *   outputs abs_dir, abs_dif: nx*ny*nz doubles [W m^-3]; sfc_dir, sfc_dif,
+ *           toa_up: nx*ny doubles [W m^-2]; zero them before the first call.
+ * cx, cy, cz are the coarsening factors of the majorant grid (0,0,0 = 4,4,4
+ * clipped). `stream` orders the work (NULL = default stream); the call waits
+ * for it to finish, then returns. events_out (host, may be NULL) receives the
+ * number of majorant events.
+ *
+ * Memory: the call allocates nothing. The photon queue head, an event counter,
+ * a status word and the majorant grid live in one fixed device array of
+ * 4 MiB + 256 B inside the library, which every GPU that loads the library
+ * holds until the process exits. The majorant grid must fit in it: at most
+ * 1,048,576 coarse cells, otherwise RT_E_INVAL. The first call on a device
+ * looks the array's device address up once (cudaGetSymbolAddress); make that
+ * first call before any stream capture. All calls on a device share the array
+ * and it keeps the last call's contents (each call clears what must start at
+ * zero), so calls whose work overlaps on the GPU race: serialise them.
+ * Errors: RT_E_INVAL (sizes, pointers, angles, too many coarse cells, invalid
+ * optical property -- outputs then unchanged), RT_E_BUDGET (a photon hit the
+ * step cap), RT_E_CUDA. */
+int rt_trace_noalloc(int nx, int ny, int nz, double dx, double dy, double dz, const float *k_gas,
+                     const float *ssa_gas, const float *k_cld, const float *ssa_cld, const float *g_cld,
+                     const float *albedo, int cx, int cy, int cz, double sza_deg, double azimuth_deg,
+                     double toa_flux, uint64_t photons, uint64_t seed, double *abs_dir, double *abs_dif,
+                     double *sfc_dir, double *sfc_dif, double *toa_up, void *stream, uint64_t *events_out);
+
 /* ---- test entry points: the device RNG and samplers, on host buffers ---- */
 
 /* n Philox4x32-10 blocks computed on the GPU: ctr[4n], key[2n] in, out[4n]. */

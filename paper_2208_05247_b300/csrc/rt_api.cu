@@ -58,6 +58,12 @@ int grid_for(size_t n, int block = 256)
 
 }  // namespace
 
+namespace rt {
+// Records an error for rt_last_error()/rt_last_error_code() from other files of
+// the library.
+int record_error(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace rt
+
 struct rt_scene {
     int nx, ny, nz;
     double dx, dy, dz;

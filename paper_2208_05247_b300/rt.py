@@ -77,6 +77,8 @@ def library() -> ctypes.CDLL:
             "rt_synchronize": ([H], i32),
             "rt_last_error": ([], ctypes.c_char_p),
             "rt_last_error_code": ([], i32),
+            "rt_trace_noalloc": ([i32, i32, i32, f64, f64, f64] + [P] * 6 + [i32, i32, i32, f64, f64, f64,
+                                                                            u64, u64] + [P] * 5 + [P, P], i32),
             "rt_debug_philox": ([P, P, P, i32], i32),
             "rt_debug_sample": ([i32, ctypes.c_float, u64, u64, P], i32),
             "rt_debug_turn": ([P, P, P, P, i32], i32),
@@ -231,6 +233,33 @@ def rt_stats(h) -> dict:
 
 def rt_synchronize(h):
     return _check(library().rt_synchronize(h))
+
+
+def rt_trace_noalloc(nx, ny, nz, dx, dy, dz, k_gas, ssa_gas, k_cld, ssa_cld, g_cld, albedo, sza_deg,
+                     azimuth_deg, toa_flux, photons, seed, abs_dir, abs_dif, sfc_dir, sfc_dif, toa_up,
+                     coarse=(0, 0, 0), stream=None) -> int:
+    """Trace without any allocation into caller-owned CUDA tensors; returns the event count.
+
+    For callers that may not allocate device memory (see include/rt.h). All
+    buffers must be CUDA tensors; outputs are accumulated.
+    """
+    ncell, ncol = int(nx) * int(ny) * int(nz), int(nx) * int(ny)
+    ins = [_buf(a, ncell, np.float32, n) for a, n in
+           zip((k_gas, ssa_gas, k_cld, ssa_cld, g_cld), ("k_gas", "ssa_gas", "k_cld", "ssa_cld", "g_cld"))]
+    ins.append(_buf(albedo, ncol, np.float32, "albedo"))
+    outs = [_buf(abs_dir, ncell, np.float64, "abs_dir", True), _buf(abs_dif, ncell, np.float64, "abs_dif", True)]
+    outs += [_buf(a, ncol, np.float64, n, True) for a, n in
+             zip((sfc_dir, sfc_dif, toa_up), ("sfc_dir", "sfc_dif", "toa_up"))]
+    if _same_mem(*ins, *outs) != RT_DEVICE:
+        raise ValueError("rt_trace_noalloc takes device buffers only")
+    sptr = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    ev = ctypes.c_uint64(0)
+    _check(library().rt_trace_noalloc(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz),
+                                      *[p for p, _ in ins], int(coarse[0]), int(coarse[1]), int(coarse[2]),
+                                      float(sza_deg), float(azimuth_deg), float(toa_flux), int(photons),
+                                      int(seed) & 0xFFFFFFFFFFFFFFFF, *[p for p, _ in outs], sptr,
+                                      ctypes.byref(ev)))
+    return ev.value
 
 
 def rt_debug_philox(ctr, key) -> np.ndarray:
