@@ -51,7 +51,7 @@ PROFILE = os.path.join(ROOT, "profiles", "trace_kernel_cumulus256.md")
 def parse():
     p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--ppc", type=int, default=256, help="photons per column per step")
@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-ppc", type=int, default=16)
+    p.add_argument("--no-autotune", action="store_true",
+                   help="use the default launch parameters and a 4x4x4 coarse grid")
     return p.parse_args()
 
 
@@ -67,10 +69,10 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", 0))
 
 
-def workload_config(args, world):
+def workload_config(args, world, coarse=COARSE):
     return {"workload": f"cumulus 256x256x128 (dx=dy=50 m, dz=25 m, 400 blobs, 20% cloud), "
                         f"sza {args.sza:g}, {args.ppc} photons/column, {args.ppc * 65536} photons per GPU "
-                        f"per step, coarse grid {COARSE[0]}x{COARSE[1]}x{COARSE[2]}",
+                        f"per step, coarse grid {coarse[0]}x{coarse[1]}x{coarse[2]}",
             "photons_per_step": args.ppc * 65536 * world,
             "l2": "inputs larger than L2: 168 MB optics + 134 MB derived records + 135 MB FP64 tallies",
             "parallelism": f"photon ranges, {world} rank(s), no data-path collective"}
@@ -226,13 +228,22 @@ def run_ours(args):
     begin, N, total = shard.photon_range(rank, world, args.ppc * ncol)
 
     t = rt.Tracer(scene.nx, scene.ny, scene.nz, scene.dx, scene.dy, scene.dz, stream=stream)
+    t.set_optics(*d_in)
+    t.set_surface(d_alb)
+    coarse = COARSE
+    tuned = None
+    if not args.no_autotune:
+        # untimed: pick coarse factors and launch parameters by photons/s
+        from paper_2208_05247_b300 import autotune
+        tuned, _ = autotune.autotune(t, args.sza, AZ, F0, N, seed=SEED + 1000)
+        coarse = tuned["coarse"]
 
     def step(seed, ev=None, inputs=None, outputs=None):
         src = inputs if inputs is not None else (d_in, d_alb)
         out = outputs if outputs is not None else d_out
         t.set_optics(*src[0])
         t.set_surface(src[1])
-        t.build_accel(*COARSE)
+        t.build_accel(*coarse)
         t.reset()
         if ev is not None:
             ev[0].record(stream)
@@ -326,8 +337,9 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(args, world),
+            "config": dict(workload_config(args, world, coarse), launch=tuned or "defaults"),
             "photons_per_s": N * world * args.steps / (ms_max / 1e3),
+            "real_scatters_per_s": st["scatters"] * world * args.steps / (ms_max / 1e3),
             "events_per_step": events_all, "real_scatter_fraction": st["scatters"] / max(1, events),
             "trace_kernel_ms": 1e3 * tk, "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps}

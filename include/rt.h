@@ -83,8 +83,11 @@ typedef struct {
     int pcld_mode;               /* RT_PCLD_*; applies from the next rt_set_optics */
     int tally_precision;         /* RT_TALLY_*; applies from the next rt_reset_tallies */
     int ready_threshold;         /* lanes of a warp that must have an event, surface hit or exit
-                                    pending before the warp handles them together; 0 = 24 */
+                                    pending before the warp handles them together; 0 = 16 */
     int max_inner;               /* bound on face-crossing sweeps between two such passes; 0 = 16 */
+    int batch_optics;            /* 1: rt_set_optics also keeps gas and cloud apart and
+                                    rt_build_accel builds the factored majorant, as
+                                    rt_trace_batch needs (+20 B per cell); 0 (default): not */
 } rt_options;
 
 typedef struct {
@@ -161,6 +164,33 @@ int rt_trace(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux,
 int rt_trace_range(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux,
                    uint64_t photon_begin, uint64_t photon_count, uint64_t photons_total,
                    uint64_t seed);
+
+/* One traced (scene, quadrature point) pair of a batched launch. */
+typedef struct {
+    rt_handle scene;       /* optics, surface and grid set with batch_optics = 1; tallies add here */
+    double sza_deg;        /* solar zenith angle of this job [deg, 0..90) */
+    double azimuth_deg;
+    double toa_flux;       /* flux of this quadrature point normal to the beam [W m^-2] */
+    double gas_scale;      /* factor on the scene's gas extinction (absorption and scattering) */
+    uint64_t photons;      /* photons of this job when total_photons is 0 */
+} rt_job;
+
+/* Trace all jobs -- every spectral quadrature point of several scenes of
+ * different sizes -- in one persistent launch (Sec. 2.3 traces each quadrature
+ * point independently; the tallies of a scene sum over its jobs as they would
+ * over separate rt_trace calls). With total_photons > 0 the photons are split in
+ * proportion to the energy each job brings into its domain (toa_flux cos(sza)
+ * times the domain area), the largest remainders taking the leftovers;
+ * otherwise each job traces its own `photons`. Job j uses Philox key
+ * (seed lo, seed hi + j * 0x9E3779B9), so job 0 with gas_scale 1 draws the same
+ * streams as rt_trace(seed). Per cell, k_abs = s k_abs,gas + k_abs,cloud and
+ * k_sca = s k_sca,gas + k_sca,cloud with s = gas_scale; the majorant is
+ * s max k_ext,gas + max k_ext,cloud per coarse cell. Up to 16 distinct scenes;
+ * jobs are launched 512 at a time. Ordered on the first job's scene's stream;
+ * other scenes' streams must not overlap with it. Counters and the energy
+ * ledger are added to each job's own scene. Asynchronous. Errors: RT_E_INVAL,
+ * RT_E_STATE (a scene without batch_optics or grid), RT_E_CUDA, RT_E_OOM. */
+int rt_trace_batch(const rt_job *jobs, int njobs, uint64_t total_photons, uint64_t seed);
 
 /* Copy the accumulated fields out, normalised (Sec. 2.3 fluxes from mean
  * weights; absorption per cell volume). abs3d: nx*ny*nz doubles [W m^-3], the

@@ -54,7 +54,7 @@ def autotune(tracer, sza, az, flux, photons, seed=1, repeats=2, verbose=False):
     measurement as dicts (photons/s, events/s, ms).
     """
     table = []
-    cur = {"coarse": (4, 4, 4), "ready_threshold": 24, "max_inner": 16, "refill_chunk": 32,
+    cur = {"coarse": (4, 4, 4), "ready_threshold": 16, "max_inner": 16, "refill_chunk": 32,
            "block_size": 256, "blocks_per_sm": 0}
 
     def measure(cfg):

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -38,7 +39,7 @@ int fail(int code, const char *fmt, ...)
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr uint32_t kDefaultMaxSteps = 10000000u;
-constexpr int kDefaultReadyThreshold = 24;
+constexpr int kDefaultReadyThreshold = 16;
 constexpr int kDefaultMaxInner = 16;
 
 template <typename T>
@@ -72,6 +73,17 @@ struct rt_scene {
     int num_sms = 148;
     cudaStream_t stream = nullptr;
     rt_options opt{};
+
+    // split gas/cloud record, cloud asymmetry and factored majorant for rt_trace_batch
+    float4 *rec2 = nullptr;
+    float *gcl = nullptr;
+    float2 *kmax2 = nullptr;
+    size_t kmax2_cap = 0;
+    bool split_ok = false, accel2_ok = false;
+
+    // batch descriptors (on the first job's scene)
+    unsigned char *desc = nullptr;
+    size_t desc_cap = 0;
 
     // derived optics, surface, majorant grid
     float4 *rec = nullptr;
@@ -230,51 +242,135 @@ int device_status(rt_handle h)
 }
 
 template <typename T>
-int launch_trace(rt_handle h, T *base, double sza, double az, double toa_flux, uint64_t begin,
-                 uint64_t count, uint64_t total, uint64_t seed)
+rt::SceneDev<T> scene_desc(rt_handle h, T *base, bool batch)
 {
-    rt::TraceArgs<T> A{};
-    A.rec = h->rec;
-    A.kmax = h->kmax;
-    A.alb = h->alb;
-    A.tal = tallies_of(base, h->ncell, h->ncol);
-    A.scr = h->scr;
-    A.id_begin = begin;
-    A.count = count;
-    A.ncol = h->ncol;
-    A.nx = h->nx; A.ny = h->ny; A.nz = h->nz;
-    A.NX = h->NX; A.NY = h->NY; A.NZ = h->NZ;
-    A.cx = h->cx; A.cy = h->cy; A.cz = h->cz;
-    A.dx = (float)h->dx; A.dy = (float)h->dy; A.dz = (float)h->dz;
-    A.inv_dx = (float)(1.0 / h->dx); A.inv_dy = (float)(1.0 / h->dy); A.inv_dz = (float)(1.0 / h->dz);
-    A.Lx = (float)(h->nx * h->dx); A.Ly = (float)(h->ny * h->dy); A.H = (float)(h->nz * h->dz);
-    A.cdx = (float)(h->cx * h->dx); A.cdy = (float)(h->cy * h->dy); A.cdz = (float)(h->cz * h->dz);
+    rt::SceneDev<T> S{};
+    S.rec = batch ? h->rec2 : h->rec;
+    S.gcl = h->gcl;
+    S.kmax = h->kmax;
+    S.kmax2 = h->kmax2;
+    S.alb = h->alb;
+    S.tal = tallies_of(base, h->ncell, h->ncol);
+    S.scr = h->scr;
+    S.nx = h->nx; S.ny = h->ny; S.nz = h->nz;
+    S.NX = h->NX; S.NY = h->NY; S.NZ = h->NZ;
+    S.cx = h->cx; S.cy = h->cy; S.cz = h->cz;
+    S.pcld_mode = h->opt.pcld_mode;
+    S.dx = (float)h->dx; S.dy = (float)h->dy; S.dz = (float)h->dz;
+    S.inv_dx = (float)(1.0 / h->dx); S.inv_dy = (float)(1.0 / h->dy); S.inv_dz = (float)(1.0 / h->dz);
+    S.Lx = (float)(h->nx * h->dx); S.Ly = (float)(h->ny * h->dy); S.H = (float)(h->nz * h->dz);
+    S.cdx = (float)(h->cx * h->dx); S.cdy = (float)(h->cy * h->dy); S.cdz = (float)(h->cz * h->dz);
+    return S;
+}
+
+// Job descriptor: sun direction, Philox key and energy per photon of `total` photons.
+rt::JobDev job_desc(rt_handle h, double sza, double az, double toa_flux, double gas_scale, uint64_t total,
+                    uint64_t seed, uint32_t key_offset)
+{
+    rt::JobDev J{};
     const double t = sza * kPi / 180.0, p = az * kPi / 180.0;
-    A.sx = (float)(-std::sin(t) * std::sin(p));
-    A.sy = (float)(-std::sin(t) * std::cos(p));
-    A.sz = (float)(-std::cos(t));
-    A.key0 = (uint32_t)seed;
-    A.key1 = (uint32_t)(seed >> 32);
-    const double mu0 = std::cos(t);
+    J.sx = (float)(-std::sin(t) * std::sin(p));
+    J.sy = (float)(-std::sin(t) * std::cos(p));
+    J.sz = (float)(-std::cos(t));
+    J.gas_scale = (float)gas_scale;
+    J.key0 = (uint32_t)seed;
+    J.key1 = (uint32_t)(seed >> 32) + key_offset * 0x9E3779B9u;
+    J.ncol = h->ncol;
     const double area = h->nx * h->dx * h->ny * h->dy;
-    A.energy = toa_flux * mu0 * area / (double)total;
-    A.scale2 = A.energy / (h->dx * h->dy);
-    A.scale3 = A.energy / (h->dx * h->dy * h->dz);
+    J.energy = toa_flux * std::cos(t) * area / (double)total;
+    J.scale2 = J.energy / (h->dx * h->dy);
+    J.scale3 = J.energy / (h->dx * h->dy * h->dz);
+    return J;
+}
+
+template <typename T>
+void fill_launch(rt_handle h, rt::TraceArgs<T> &A)
+{
     A.max_steps = h->opt.max_steps ? h->opt.max_steps : kDefaultMaxSteps;
     A.chunk = (uint32_t)(h->opt.refill_chunk > 0 ? h->opt.refill_chunk : 32);
     A.ready_threshold = h->opt.ready_threshold > 0 ? h->opt.ready_threshold : kDefaultReadyThreshold;
     A.max_inner = h->opt.max_inner > 0 ? h->opt.max_inner : kDefaultMaxInner;
+}
+
+template <typename T>
+int launch_trace(rt_handle h, T *base, double sza, double az, double toa_flux, uint64_t begin,
+                 uint64_t count, uint64_t total, uint64_t seed)
+{
+    rt::TraceArgs<T> A{};
+    A.scene = scene_desc<T>(h, base, false);
+    A.job = job_desc(h, sza, az, toa_flux, 1.0, total, seed, 0);
+    A.job.start = 0;
+    A.job.id_begin = begin;
+    A.count = count;
+    A.scr = h->scr;
+    fill_launch(h, A);
 
     const int block = h->opt.block_size > 0 ? h->opt.block_size : 256;
     int bps = h->opt.blocks_per_sm;
     if (bps <= 0) {
-        RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rt::trace_kernel<T>, block, 0));
+        RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rt::trace_kernel<T, false>, block, 0));
         bps = std::max(1, bps);
     }
     RT_CUDA(cudaMemsetAsync(&h->scr->queue_head, 0, sizeof(unsigned long long), h->stream));
-    rt::trace_kernel<T><<<h->num_sms * bps, block, 0, h->stream>>>(A);
+    rt::trace_kernel<T, false><<<h->num_sms * bps, block, 0, h->stream>>>(A);
     RT_CUDA(cudaGetLastError());
-    h->energy_in += toa_flux * mu0 * area * ((double)count / (double)total);
+    const double mu0 = std::cos(sza * kPi / 180.0);
+    h->energy_in += toa_flux * mu0 * h->nx * h->dx * h->ny * h->dy * ((double)count / (double)total);
+    return RT_OK;
+}
+
+// One batched launch: scene and job descriptors go to the home scene's
+// descriptor buffer, the photon queue head to its scratch; `count` photons in
+// total, job j owning queue indices [jobs[j].start, jobs[j+1].start).
+template <typename T>
+int launch_batch(rt_handle home, const std::vector<rt_handle> &scenes, const std::vector<rt::JobDev> &jobs,
+                 unsigned long long count)
+{
+    std::vector<rt::SceneDev<T>> sd(scenes.size());
+    for (size_t q = 0; q < scenes.size(); ++q) {
+        rt_handle h = scenes[q];
+        T *base = std::is_same<T, double>::value ? reinterpret_cast<T *>(h->t64) : reinterpret_cast<T *>(h->t32);
+        sd[q] = scene_desc<T>(h, base, true);
+    }
+    const size_t bytes_s = sd.size() * sizeof(rt::SceneDev<T>), bytes_j = jobs.size() * sizeof(rt::JobDev);
+    if (home->desc_cap < bytes_s + bytes_j) {
+        cudaFree(home->desc);
+        home->desc = nullptr;
+        home->desc_cap = 0;
+        int rc = dev_alloc(&home->desc, bytes_s + bytes_j);
+        if (rc) return rc;
+        home->desc_cap = bytes_s + bytes_j;
+    }
+    // pageable source: the call returns once the bytes are staged, so the
+    // vector may go out of scope afterwards
+    std::vector<unsigned char> host(bytes_s + bytes_j);
+    std::memcpy(host.data(), sd.data(), bytes_s);
+    std::memcpy(host.data() + bytes_s, jobs.data(), bytes_j);
+    RT_CUDA(cudaMemcpyAsync(home->desc, host.data(), host.size(), cudaMemcpyHostToDevice, home->stream));
+
+    rt::TraceArgs<T> A{};
+    A.scenes = reinterpret_cast<const rt::SceneDev<T> *>(home->desc);
+    A.jobs = reinterpret_cast<const rt::JobDev *>(home->desc + bytes_s);
+    A.nscenes = (int)sd.size();
+    A.njobs = (int)jobs.size();
+    A.count = count;
+    A.scr = home->scr;
+    fill_launch(home, A);
+
+    const int block = home->opt.block_size > 0 ? home->opt.block_size : 256;
+    const size_t smem = bytes_s + bytes_j;
+    if (smem > 48 * 1024)
+        RT_CUDA(cudaFuncSetAttribute(rt::trace_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    int bps = home->opt.blocks_per_sm;
+    int fit = 0;
+    RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, rt::trace_kernel<T, true>, block, smem));
+    if (fit <= 0) return fail(RT_E_INVAL, "rt_trace_batch: descriptors of %d jobs do not fit in shared memory",
+                              (int)jobs.size());
+    if (bps <= 0 || bps > fit) bps = fit;
+    RT_CUDA(cudaMemsetAsync(&home->scr->queue_head, 0, sizeof(unsigned long long), home->stream));
+    rt::trace_kernel<T, true><<<home->num_sms * bps, block, smem, home->stream>>>(A);
+    RT_CUDA(cudaGetLastError());
     return RT_OK;
 }
 
@@ -355,6 +451,10 @@ int rt_destroy(rt_handle h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     cudaFree(h->rec);
+    cudaFree(h->rec2);
+    cudaFree(h->gcl);
+    cudaFree(h->kmax2);
+    cudaFree(h->desc);
     cudaFree(h->alb);
     cudaFree(h->kmax);
     cudaFree(h->stage);
@@ -394,12 +494,14 @@ int rt_set_options(rt_handle h, const rt_options *o)
         return fail(RT_E_INVAL, "rt_set_options: max_inner must be in [0, 4096]");
     if (o->pcld_mode != RT_PCLD_SCATTERING && o->pcld_mode != RT_PCLD_EXTINCTION)
         return fail(RT_E_INVAL, "rt_set_options: unknown pcld_mode");
+    if (o->batch_optics != 0 && o->batch_optics != 1)
+        return fail(RT_E_INVAL, "rt_set_options: batch_optics must be 0 or 1");
     if (o->tally_precision != RT_TALLY_FP64 && o->tally_precision != RT_TALLY_FP32)
         return fail(RT_E_INVAL, "rt_set_options: unknown tally_precision");
     if (o->blocks_per_sm > 0) {
         int fit = 0;
         const int block = o->block_size > 0 ? o->block_size : 256;
-        RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, rt::trace_kernel<double>, block, 0));
+        RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, rt::trace_kernel<double, false>, block, 0));
         if (o->blocks_per_sm > fit)
             return fail(RT_E_INVAL, "rt_set_options: %d blocks/SM do not fit (max %d)", o->blocks_per_sm, fit);
     }
@@ -438,6 +540,15 @@ int rt_set_optics(rt_handle h, const float *k_gas, const float *ssa_gas, const f
     rt::derive_optics<<<grid_for(n), 256, 0, h->stream>>>(src[0], src[1], src[2], src[3], src[4], h->rec, n,
                                                           h->opt.pcld_mode, h->bad);
     RT_CUDA(cudaGetLastError());
+    h->split_ok = false;
+    h->accel2_ok = false;
+    if (h->opt.batch_optics) {
+        if (!h->rec2 && (rc = dev_alloc(&h->rec2, n))) return rc;
+        if (!h->gcl && (rc = dev_alloc(&h->gcl, n))) return rc;
+        rt::derive_split<<<grid_for(n), 256, 0, h->stream>>>(src[0], src[1], src[2], src[3], src[4], h->rec2,
+                                                             h->gcl, n);
+        RT_CUDA(cudaGetLastError());
+    }
     int bad = 0;
     if ((rc = read_bad(h, &bad))) return rc;
     h->accel_ok = false;
@@ -447,6 +558,7 @@ int rt_set_optics(rt_handle h, const float *k_gas, const float *ssa_gas, const f
                                 "albedo outside [0,1] or |g| >= 1)");
     }
     h->optics_ok = true;
+    h->split_ok = h->opt.batch_optics != 0;
     return RT_OK;
 }
 
@@ -496,6 +608,20 @@ int rt_build_accel(rt_handle h, int cx, int cy, int cz)
     rt::build_majorant<<<grid_for(nc), 256, 0, h->stream>>>(h->rec, h->kmax, h->nx, h->ny, h->nz, cx, cy, cz,
                                                             NX, NY, NZ);
     RT_CUDA(cudaGetLastError());
+    h->accel2_ok = false;
+    if (h->split_ok) {
+        if (nc > h->kmax2_cap) {
+            cudaFree(h->kmax2);
+            h->kmax2 = nullptr;
+            h->kmax2_cap = 0;
+            if ((rc = dev_alloc(&h->kmax2, nc))) return rc;
+            h->kmax2_cap = nc;
+        }
+        rt::build_majorant_split<<<grid_for(nc), 256, 0, h->stream>>>(h->rec2, h->kmax2, h->nx, h->ny, h->nz, cx,
+                                                                      cy, cz, NX, NY, NZ);
+        RT_CUDA(cudaGetLastError());
+        h->accel2_ok = true;
+    }
     h->accel_ok = true;
     return RT_OK;
 }
@@ -526,6 +652,90 @@ int rt_trace(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux, u
 {
     if (photons == 0) return check(h);
     return rt_trace_range(h, sza_deg, azimuth_deg, toa_flux, 0, photons, photons, seed);
+}
+
+int rt_trace_batch(const rt_job *jobs, int njobs, uint64_t total_photons, uint64_t seed)
+{
+    if (!jobs || njobs <= 0) return fail(RT_E_INVAL, "rt_trace_batch: need at least one job");
+    rt_handle home = jobs[0].scene;
+    int rc = check(home);
+    if (rc) return rc;
+    std::vector<rt_handle> scenes;
+    std::vector<int> sidx(njobs);
+    std::vector<double> energy(njobs);
+    for (int j = 0; j < njobs; ++j) {
+        const rt_job &jb = jobs[j];
+        rt_handle h = jb.scene;
+        if (!h) return fail(RT_E_INVAL, "rt_trace_batch: job %d has no scene", j);
+        if (h->device != home->device) return fail(RT_E_INVAL, "rt_trace_batch: all scenes must be on one device");
+        if (!h->optics_ok || !h->surface_ok || !h->accel_ok)
+            return fail(RT_E_STATE, "rt_trace_batch: job %d: set optics and surface and build the "
+                                    "acceleration grid first", j);
+        if (!h->split_ok || !h->accel2_ok)
+            return fail(RT_E_STATE, "rt_trace_batch: job %d: set rt_options.batch_optics = 1 before "
+                                    "rt_set_optics, then build the acceleration grid", j);
+        if (h->tally_prec != home->tally_prec)
+            return fail(RT_E_INVAL, "rt_trace_batch: all scenes must use the same tally precision");
+        if (!(jb.sza_deg >= 0.0 && jb.sza_deg < 90.0) || !std::isfinite(jb.azimuth_deg) ||
+            !(jb.toa_flux >= 0.0) || !std::isfinite(jb.toa_flux) || !(jb.gas_scale >= 0.0) ||
+            !std::isfinite(jb.gas_scale) || jb.gas_scale > 1e30)
+            return fail(RT_E_INVAL, "rt_trace_batch: job %d: bad sza, azimuth, toa_flux or gas_scale", j);
+        int q = -1;
+        for (size_t k = 0; k < scenes.size(); ++k)
+            if (scenes[k] == h) q = (int)k;
+        if (q < 0) {
+            if ((int)scenes.size() == rt::kMaxBatchScenes)
+                return fail(RT_E_INVAL, "rt_trace_batch: at most %d distinct scenes per call", rt::kMaxBatchScenes);
+            q = (int)scenes.size();
+            scenes.push_back(h);
+        }
+        sidx[j] = q;
+        energy[j] = jb.toa_flux * std::cos(jb.sza_deg * kPi / 180.0) * h->nx * h->dx * h->ny * h->dy;
+    }
+    // photon budgets: given per job, or total_photons split in proportion to
+    // the energy each job brings in (largest remainders get the leftovers)
+    std::vector<uint64_t> n(njobs, 0);
+    if (total_photons > 0) {
+        double etot = 0.0;
+        for (double e : energy) etot += e;
+        if (!(etot > 0.0)) return fail(RT_E_INVAL, "rt_trace_batch: no job brings in any energy");
+        std::vector<std::pair<double, int>> frac(njobs);
+        uint64_t used = 0;
+        for (int j = 0; j < njobs; ++j) {
+            const double x = (double)total_photons * energy[j] / etot;
+            n[j] = (uint64_t)std::floor(x);
+            used += n[j];
+            frac[j] = {x - std::floor(x), j};
+        }
+        std::sort(frac.begin(), frac.end(), [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+            return a.first > b.first || (a.first == b.first && a.second < b.second);
+        });
+        for (uint64_t k = 0; used < total_photons; ++k, ++used) ++n[frac[k % njobs].second];
+    } else {
+        for (int j = 0; j < njobs; ++j) n[j] = jobs[j].photons;
+    }
+    for (int c0 = 0; c0 < njobs; c0 += rt::kMaxBatchJobs) {
+        const int c1 = std::min(njobs, c0 + rt::kMaxBatchJobs);
+        std::vector<rt::JobDev> jd;
+        unsigned long long start = 0;
+        for (int j = c0; j < c1; ++j) {
+            rt_handle h = jobs[j].scene;
+            rt::JobDev J = job_desc(h, jobs[j].sza_deg, jobs[j].azimuth_deg, jobs[j].toa_flux, jobs[j].gas_scale,
+                                    n[j] ? n[j] : 1, seed, (uint32_t)j);
+            J.start = start;
+            J.id_begin = 0;
+            J.scene = sidx[j];
+            jd.push_back(J);
+            start += n[j];
+        }
+        if (start == 0) continue;
+        rc = home->tally_prec == RT_TALLY_FP64 ? launch_batch<double>(home, scenes, jd, start)
+                                               : launch_batch<float>(home, scenes, jd, start);
+        if (rc) return rc;
+    }
+    for (int j = 0; j < njobs; ++j)
+        if (n[j]) jobs[j].scene->energy_in += energy[j];
+    return RT_OK;
 }
 
 int rt_reset_tallies(rt_handle h)

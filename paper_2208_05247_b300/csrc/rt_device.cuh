@@ -59,7 +59,7 @@ __device__ __forceinline__ float rayleigh_mu(float xi)
     const float a = 4.0f * xi - 2.0f;
     const float t = fabsf(a);
     const float c = cbrtf(t + sqrtf(fmaf(t, t, 1.0f)));
-    return copysignf(c - 1.0f / c, a);
+    return copysignf(c - __frcp_rn(c), a);
 }
 
 // Henyey-Greenstein: with s = 2 xi - 1 the inverse CDF
@@ -72,7 +72,7 @@ __device__ __forceinline__ float hg_mu(float g, float xi)
     const float s2 = s * s;
     const float num = s + g * (0.5f * (3.0f + s2) + g * (s + 0.5f * g * (s2 - 1.0f)));
     const float d = fmaf(g, s, 1.0f);
-    const float mu = num / (d * d);
+    const float mu = __fdividef(num, d * d);
     return fminf(1.0f, fmaxf(-1.0f, mu));
 }
 

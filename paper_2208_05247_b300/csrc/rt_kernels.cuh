@@ -36,25 +36,56 @@ struct Tallies {
     T *sfc_dir, *sfc_dif, *toa;     // [ncol]
 };
 
+constexpr int kMaxBatchScenes = 16;
+constexpr int kMaxBatchJobs = 512;
+
+// One scene as the transport kernel sees it.
 template <typename T>
-struct TraceArgs {
-    const float4 *__restrict__ rec;   // [nz][ny][nx] {k_abs, k_sca, k_sca*P(cloud), g}
-    const float *__restrict__ kmax;   // [NZ][NY][NX]
-    const float *__restrict__ alb;    // [ny][nx]
+struct SceneDev {
+    const float4 *rec;     // single-scene launches: {k_abs, k_sca, k_sca*P(cloud), g} per cell;
+                           // batched launches: {k_abs,gas, k_sca,gas, k_abs,cloud, k_sca,cloud}
+    const float *gcl;      // batched launches: cloud asymmetry per cell
+    const float *kmax;     // single-scene: max k_ext per coarse cell
+    const float2 *kmax2;   // batched: {max gas k_ext, max cloud k_ext} per coarse cell
+    const float *alb;      // [ny][nx]
     Tallies<T> tal;
     Scratch *scr;
-    unsigned long long id_begin, count, ncol;
-    int nx, ny, nz, NX, NY, NZ, cx, cy, cz;
+    int nx, ny, nz, NX, NY, NZ, cx, cy, cz, pcld_mode;
     float dx, dy, dz, inv_dx, inv_dy, inv_dz, Lx, Ly, H;
-    float cdx, cdy, cdz;              // coarse cell size [m] (the last cell may be smaller)
-    float sx, sy, sz;                 // travel direction of the direct beam
-    uint32_t key0, key1;
-    double energy;                    // W per unit photon weight
-    double scale2, scale3;            // energy / (dx dy), energy / (dx dy dz)
+    float cdx, cdy, cdz;   // coarse cell size [m] (the last cell may be smaller)
+};
+
+// One traced job: a scene, a sun position, an energy per photon and a range of
+// photon ids; in a batched launch one job per (scene, g-point).
+struct JobDev {
+    unsigned long long start;      // first queue index of the job
+    unsigned long long id_begin;   // photon id of that queue index
+    unsigned long long ncol;
+    float sx, sy, sz;              // travel direction of the direct beam
+    float gas_scale;               // multiplies the gas extinction (batched launches)
+    uint32_t key0, key1;           // Philox key
+    int scene, pad_;
+    double energy;                 // W per unit photon weight
+    double scale2, scale3;         // energy / (dx dy), energy / (dx dy dz)
+};
+
+static_assert(sizeof(SceneDev<double>) % 16 == 0 && sizeof(SceneDev<float>) % 16 == 0,
+              "scene descriptors are copied to shared memory in 16-byte words");
+static_assert(sizeof(JobDev) % 16 == 0, "job descriptors are copied in 16-byte words");
+
+template <typename T>
+struct TraceArgs {
+    SceneDev<T> scene;             // single-scene launches
+    JobDev job;
+    const SceneDev<T> *scenes;     // batched launches (copied into shared memory)
+    const JobDev *jobs;
+    int nscenes, njobs;
+    unsigned long long count;      // photons of the launch
+    Scratch *scr;                  // queue head; counters of single-scene launches
     uint32_t max_steps;
     uint32_t chunk;
-    int ready_threshold;              // lanes that must be ready before an interaction sweep
-    int max_inner;                    // bound on face-crossing sweeps per interaction sweep
+    int ready_threshold;           // lanes that must be ready before an interaction sweep
+    int max_inner;                 // bound on face-crossing sweeps per interaction sweep
 };
 
 // ---------------------------------------------------------------------------
@@ -119,12 +150,57 @@ __global__ void build_majorant(const float4 *__restrict__ rec, float *__restrict
 }
 
 // ---------------------------------------------------------------------------
+// Batched launches scale the gas extinction per g-point, so they keep gas and
+// cloud apart: {k_abs,gas, k_sca,gas, k_abs,cloud, k_sca,cloud} and g per cell,
+// and a factored majorant s * max(k_ext,gas) + max(k_ext,cloud) per coarse
+// cell, which bounds s k_ext,gas + k_ext,cloud of every fine cell for any gas
+// scale s >= 0. Both maxima are raised by 2^-20 relative so the bound still
+// holds after the FP32 rounding of the per-cell sums.
+// ---------------------------------------------------------------------------
+__global__ void derive_split(const float *__restrict__ kg, const float *__restrict__ wg,
+                             const float *__restrict__ kc, const float *__restrict__ wc,
+                             const float *__restrict__ gc, float4 *__restrict__ rec2, float *__restrict__ gcl,
+                             size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float a = kg[i], b = wg[i], c = kc[i], d = wc[i];
+        rec2[i] = make_float4(a * (1.0f - b), a * b, c * (1.0f - d), c * d);
+        gcl[i] = gc[i];
+    }
+}
+
+__global__ void build_majorant_split(const float4 *__restrict__ rec2, float2 *__restrict__ kmax2, int nx,
+                                     int ny, int nz, int cx, int cy, int cz, int NX, int NY, int NZ)
+{
+    const int n = NX * NY * NZ;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const int I = q % NX, J = (q / NX) % NY, K = q / (NX * NY);
+        const int i1 = min(I * cx + cx, nx), j1 = min(J * cy + cy, ny), k1 = min(K * cz + cz, nz);
+        float mg = 0.0f, mc = 0.0f;
+        for (int k = K * cz; k < k1; ++k)
+            for (int j = J * cy; j < j1; ++j) {
+                const float4 *row = rec2 + ((size_t)k * ny + j) * nx;
+                for (int i = I * cx; i < i1; ++i) {
+                    const float4 o = __ldg(row + i);
+                    mg = fmaxf(mg, o.x + o.y);
+                    mc = fmaxf(mc, o.z + o.w);
+                }
+            }
+        const float up = 1.0f + 9.5367431640625e-7f;   // 1 + 2^-20
+        kmax2[q] = make_float2(mg * up, mc * up);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Tally accumulation: FP32 partial times the per-call energy, added into the
 // FP64 (or, for the precision study, FP32) global accumulator.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void tally_add(double *p, float v, double scale)
 {
-    atomicAdd(p, (double)v * scale);
+    // the partial is FP32 already; scaling it in FP32 keeps the thin FP64 pipe
+    // to the one conversion the FP64 accumulator needs
+    atomicAdd(p, (double)(v * (float)scale));
 }
 __device__ __forceinline__ void tally_add(float *p, float v, double scale)
 {
@@ -180,26 +256,41 @@ __device__ __forceinline__ double warp_sum_f64(double v)
 // ---------------------------------------------------------------------------
 enum : int { kNone = 0, kEvent = 1, kSurface = 2, kTop = 3, kCap = 4 };
 
-template <typename T>
-__device__ __forceinline__ void flush_partial(const TraceArgs<T> &A, int &pcell, bool pdir, float pacc)
-{
-    if (pcell >= 0) tally_add((pdir ? A.tal.abs_dir : A.tal.abs_dif) + pcell, pacc, A.scale3);
-    pcell = -1;
-}
+// Scene and job fields of the lane's photon: kernel parameters in single-scene
+// launches, shared memory in batched ones (folded at compile time).
+#define RT_SC(f) (BATCH ? s_scenes[sid].f : A.scene.f)
+#define RT_JB(f) (BATCH ? s_jobs[jid].f : A.job.f)
 
-template <typename T>
+template <typename T, bool BATCH>
 __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ TraceArgs<T> A)
 {
     constexpr unsigned kFull = 0xffffffffu;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned below = (1u << lane) - 1u;
 
-    // rare counters and the energy ledger live in shared memory
-    __shared__ unsigned long long s_cnt[3];   // surface hits, roulette kills, capped
-    __shared__ double s_led[3];               // created, destroyed, capped energy
-    if (threadIdx.x < 3) { s_cnt[threadIdx.x] = 0; s_led[threadIdx.x] = 0.0; }
+    // batched launches: scene and job descriptors in dynamic shared memory
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    SceneDev<T> *s_scenes = reinterpret_cast<SceneDev<T> *>(s_dyn);
+    JobDev *s_jobs = reinterpret_cast<JobDev *>(s_dyn + (BATCH ? A.nscenes : 0) * sizeof(SceneDev<T>));
+    // rare counters and the energy ledger per scene: surface hits, roulette
+    // kills, capped | created, destroyed, capped energy; batched launches also
+    // keep photons, events, scatters and crossings per scene here
+    constexpr int NS = BATCH ? kMaxBatchScenes : 1;
+    __shared__ unsigned long long s_cnt[NS][7];
+    __shared__ double s_led[NS][3];
+    for (int q = threadIdx.x; q < NS * 7; q += blockDim.x) s_cnt[q / 7][q % 7] = 0;
+    for (int q = threadIdx.x; q < NS * 3; q += blockDim.x) s_led[q / 3][q % 3] = 0.0;
+    if (BATCH) {
+        const int4 *src = reinterpret_cast<const int4 *>(A.scenes);
+        int4 *dst = reinterpret_cast<int4 *>(s_scenes);
+        for (int q = threadIdx.x; q < (int)(A.nscenes * sizeof(SceneDev<T>) / 16); q += blockDim.x) dst[q] = src[q];
+        const int4 *js = reinterpret_cast<const int4 *>(A.jobs);
+        int4 *jd = reinterpret_cast<int4 *>(s_jobs);
+        for (int q = threadIdx.x; q < (int)(A.njobs * sizeof(JobDev) / 16); q += blockDim.x) jd[q] = js[q];
+    }
     __syncthreads();
 
+    int sid = 0, jid = 0;                     // scene and job of the lane's photon
     float ox = 0.f, oy = 0.f, oz = 0.f;       // origin of the current straight segment
     float ux = 0.f, uy = 0.f, uz = -1.f;      // direction
     float ivx = 0.f, ivy = 0.f, ivz = 0.f;    // 1/u per axis (used only on axes that move)
@@ -208,7 +299,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
     float w = 0.f, tau = 0.f, kmaj = 0.f;
     int I = 0, J = 0, K = 0;
     unsigned long long gid = 0;
-    uint32_t blk = 0, steps = 0, nev = 0;
+    uint32_t blk = 0, steps = 0, nev = 0, nsc = 0, ncr = 0;
     bool alive = false, direct = false;
     int ready = kNone;
     int pcell = -1;
@@ -220,20 +311,33 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
     unsigned long long pool_next = 0, pool_end = 0;
     bool exhausted = false;
 
-    const uint32_t k0 = A.key0, k1 = A.key1;
+    auto load_kmaj = [&]() -> float {
+        const size_t q = ((size_t)K * RT_SC(NY) + J) * RT_SC(NX) + I;
+        if constexpr (BATCH) {
+            const float2 m = __ldg(RT_SC(kmax2) + q);
+            return fmaf(RT_JB(gas_scale), m.x, m.y);
+        } else {
+            return __ldg(RT_SC(kmax) + q);
+        }
+    };
+    auto flush = [&]() {
+        if (pcell >= 0)
+            tally_add((pdir ? RT_SC(tal.abs_dir) : RT_SC(tal.abs_dif)) + pcell, pacc, RT_JB(scale3));
+        pcell = -1;
+    };
 
-    // distances to the next coarse faces from origin o along u, for cell (I,J,K)
+    // distances to the next coarse faces from origin o along u, for cell (I,J,K).
     // An axis along which the photon does not move gets an infinite distance and
     // is never crossed, so its reciprocal is never used.
     auto start_segment = [&]() {
         tcur = 0.f;
         ivx = __frcp_rn(ux); ivy = __frcp_rn(uy); ivz = __frcp_rn(uz);
-        tnx = ux > 0.f ? (fminf((float)(I + 1) * A.cdx, A.Lx) - ox) * ivx
-            : ux < 0.f ? ((float)I * A.cdx - ox) * ivx : INFINITY;
-        tny = uy > 0.f ? (fminf((float)(J + 1) * A.cdy, A.Ly) - oy) * ivy
-            : uy < 0.f ? ((float)J * A.cdy - oy) * ivy : INFINITY;
-        tnz = uz > 0.f ? (fminf((float)(K + 1) * A.cdz, A.H) - oz) * ivz
-            : uz < 0.f ? ((float)K * A.cdz - oz) * ivz : INFINITY;
+        tnx = ux > 0.f ? (fminf((float)(I + 1) * RT_SC(cdx), RT_SC(Lx)) - ox) * ivx
+            : ux < 0.f ? ((float)I * RT_SC(cdx) - ox) * ivx : INFINITY;
+        tny = uy > 0.f ? (fminf((float)(J + 1) * RT_SC(cdy), RT_SC(Ly)) - oy) * ivy
+            : uy < 0.f ? ((float)J * RT_SC(cdy) - oy) * ivy : INFINITY;
+        tnz = uz > 0.f ? (fminf((float)(K + 1) * RT_SC(cdz), RT_SC(H)) - oz) * ivz
+            : uz < 0.f ? ((float)K * RT_SC(cdz) - oz) * ivz : INFINITY;
         tnx = fmaxf(tnx, 0.f); tny = fmaxf(tny, 0.f); tnz = fmaxf(tnz, 0.f);
     };
 
@@ -268,24 +372,36 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
                 }
             }
             if (mine != ~0ull) {
+                // ---- a11: which job (batched launches: binary search of job starts) ----
+                if constexpr (BATCH) {
+                    int lo = 0, hi = A.njobs - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_jobs[mid].start <= mine) lo = mid; else hi = mid - 1;
+                    }
+                    jid = lo;
+                    sid = s_jobs[jid].scene;
+                }
                 // ---- a3: birth at the domain top, along the sun beam ----
-                gid = A.id_begin + mine;
-                const unsigned col = (unsigned)(gid % A.ncol);
-                const int ci = (int)(col % (unsigned)A.nx), cj = (int)(col / (unsigned)A.nx);
-                const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), 0u, 0u), k0, k1);
-                ox = ((float)ci + u01(r.x)) * A.dx;
-                oy = ((float)cj + u01(r.y)) * A.dy;
-                oz = A.H;
-                ux = A.sx; uy = A.sy; uz = A.sz;
+                gid = RT_JB(id_begin) + (mine - RT_JB(start));
+                const unsigned long long ncol = RT_JB(ncol);
+                const unsigned col = (gid >> 32) ? (unsigned)(gid % ncol) : (uint32_t)gid % (uint32_t)ncol;
+                const int ci = (int)(col % (unsigned)RT_SC(nx)), cj = (int)(col / (unsigned)RT_SC(nx));
+                const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), 0u, 0u),
+                                              RT_JB(key0), RT_JB(key1));
+                ox = ((float)ci + u01(r.x)) * RT_SC(dx);
+                oy = ((float)cj + u01(r.y)) * RT_SC(dy);
+                oz = RT_SC(H);
+                ux = RT_JB(sx); uy = RT_JB(sy); uz = RT_JB(sz);
                 tau = -__logf(u01(r.z));
                 w = 1.f;
                 direct = true;
                 alive = true;
                 ready = kNone;
-                I = ci / A.cx; J = cj / A.cy; K = A.NZ - 1;
-                kmaj = __ldg(A.kmax + ((size_t)K * A.NY + J) * A.NX + I);
+                I = ci / RT_SC(cx); J = cj / RT_SC(cy); K = RT_SC(NZ) - 1;
+                kmaj = load_kmaj();
                 start_segment();
-                blk = 1; steps = 0; nev = 0;
+                blk = 1; steps = 0; nev = 0; nsc = 0; ncr = 0;
                 ++c_ph;
             }
             if (!__any_sync(kFull, alive)) break;
@@ -313,76 +429,101 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
             tau = fmaf(-kmaj, dt, tau);
             tcur = tm;
             ++c_cr;
+            if (BATCH) ++ncr;
             if (ax == 0) {
                 if (ux > 0.f) {
-                    if (++I == A.NX) { I = 0; ox -= A.Lx; }
-                    tnx = (fminf((float)(I + 1) * A.cdx, A.Lx) - ox) * ivx;
+                    if (++I == RT_SC(NX)) { I = 0; ox -= RT_SC(Lx); }
+                    tnx = (fminf((float)(I + 1) * RT_SC(cdx), RT_SC(Lx)) - ox) * ivx;
                 } else {
-                    if (--I < 0) { I = A.NX - 1; ox += A.Lx; }
-                    tnx = ((float)I * A.cdx - ox) * ivx;
+                    if (--I < 0) { I = RT_SC(NX) - 1; ox += RT_SC(Lx); }
+                    tnx = ((float)I * RT_SC(cdx) - ox) * ivx;
                 }
             } else if (ax == 1) {
                 if (uy > 0.f) {
-                    if (++J == A.NY) { J = 0; oy -= A.Ly; }
-                    tny = (fminf((float)(J + 1) * A.cdy, A.Ly) - oy) * ivy;
+                    if (++J == RT_SC(NY)) { J = 0; oy -= RT_SC(Ly); }
+                    tny = (fminf((float)(J + 1) * RT_SC(cdy), RT_SC(Ly)) - oy) * ivy;
                 } else {
-                    if (--J < 0) { J = A.NY - 1; oy += A.Ly; }
-                    tny = ((float)J * A.cdy - oy) * ivy;
+                    if (--J < 0) { J = RT_SC(NY) - 1; oy += RT_SC(Ly); }
+                    tny = ((float)J * RT_SC(cdy) - oy) * ivy;
                 }
             } else {
                 if (uz > 0.f) {
-                    if (++K == A.NZ) { ready = kTop; continue; }
-                    tnz = (fminf((float)(K + 1) * A.cdz, A.H) - oz) * ivz;
+                    if (++K == RT_SC(NZ)) { ready = kTop; continue; }
+                    tnz = (fminf((float)(K + 1) * RT_SC(cdz), RT_SC(H)) - oz) * ivz;
                 } else {
                     if (--K < 0) { ready = kSurface; continue; }
-                    tnz = ((float)K * A.cdz - oz) * ivz;
+                    tnz = ((float)K * RT_SC(cdz) - oz) * ivz;
                 }
             }
-            kmaj = __ldg(A.kmax + ((size_t)K * A.NY + J) * A.NX + I);
+            kmaj = load_kmaj();
         }
 
         // ---------------- 3. interact ----------------
         if (ready == kNone) continue;
         bool end_photon = false;
-        const int ilo = I * A.cx, ihi = min(ilo + A.cx, A.nx);
-        const int jlo = J * A.cy, jhi = min(jlo + A.cy, A.ny);
+        const int ilo = I * RT_SC(cx), ihi = min(ilo + RT_SC(cx), RT_SC(nx));
+        const int jlo = J * RT_SC(cy), jhi = min(jlo + RT_SC(cy), RT_SC(ny));
         const float px = fmaf(ux, tcur, ox), py = fmaf(uy, tcur, oy);
-        const int fi = min(max((int)(px * A.inv_dx), ilo), ihi - 1);
-        const int fj = min(max((int)(py * A.inv_dy), jlo), jhi - 1);
+        const int fi = min(max((int)(px * RT_SC(inv_dx)), ilo), ihi - 1);
+        const int fj = min(max((int)(py * RT_SC(inv_dy)), jlo), jhi - 1);
         if (ready == kEvent) {
             // ---- a5: majorant event: absorb a fraction of the weight ----
             ++steps;
             const float pz = fmaf(uz, tcur, oz);
-            const int klo = K * A.cz, khi = min(klo + A.cz, A.nz);
-            const int fk = min(max((int)(pz * A.inv_dz), klo), khi - 1);
-            const int cell = (fk * A.ny + fj) * A.nx + fi;
-            const float4 o = __ldg(A.rec + cell);
-            const float pabs = fminf(__fdividef(o.x, kmaj), 1.0f);
+            const int klo = K * RT_SC(cz), khi = min(klo + RT_SC(cz), RT_SC(nz));
+            const int fk = min(max((int)(pz * RT_SC(inv_dz)), klo), khi - 1);
+            const int cell = (fk * RT_SC(ny) + fj) * RT_SC(nx) + fi;
+            float kabs, ksca, kscl;   // absorption, scattering, scattering times P(cloud)
+            const float4 o = __ldg(RT_SC(rec) + cell);
+            if constexpr (BATCH) {
+                const float s = RT_JB(gas_scale);
+                kabs = fmaf(s, o.x, o.z);
+                ksca = fmaf(s, o.y, o.w);
+                if (RT_SC(pcld_mode) == 1) {
+                    const float kc = o.z + o.w, kext = fmaf(s, o.x + o.y, kc);
+                    kscl = kext > 0.f ? ksca * (kc / kext) : 0.f;
+                } else {
+                    kscl = o.w;
+                }
+            } else {
+                kabs = o.x; ksca = o.y; kscl = o.z;
+            }
+            const float pabs = fminf(__fdividef(kabs, kmaj), 1.0f);
             const float wn = w * (1.0f - pabs);
             if (cell != pcell || direct != pdir) {
-                flush_partial(A, pcell, pdir, pacc);
+                flush();
                 pcell = cell; pdir = direct; pacc = 0.f;
             }
             pacc += w - wn;
             w = wn;
             ++c_ev; ++nev;
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk, 0u), k0, k1);
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk, 0u),
+                                          RT_JB(key0), RT_JB(key1));
             ++blk;
             // ---- a6/a7: real scattering or null collision ----
+            // scatter if xi < k_sca/(k_max - k_abs), by cloud if xi < k_sca,cloud/(k_max - k_abs)
             ox = px; oy = py; oz = pz;
-            const float den = kmaj - o.x;
+            const float den = kmaj - kabs;
             bool scattered = false;
             if (den > 0.f) {
-                const float rd = 1.0f / den;
-                const float xi = u01(r.x);
-                if (xi < o.y * rd) {
-                    const float mu = (xi < o.z * rd) ? hg_mu(o.w, u01(r.y)) : rayleigh_mu(u01(r.y));
+                const float xd = u01(r.x) * den;
+                if (xd < ksca) {
+                    float mu;
+                    if (xd < kscl) {
+                        float g;
+                        if constexpr (BATCH) g = __ldg(RT_SC(gcl) + cell);
+                        else g = o.w;
+                        mu = hg_mu(g, u01(r.y));
+                    } else {
+                        mu = rayleigh_mu(u01(r.y));
+                    }
                     float sp, cp;
                     azimuth(u01(r.z), sp, cp);
                     turn(ux, uy, uz, mu, sp, cp);
                     direct = false;
                     scattered = true;
                     ++c_sc;
+                    if (BATCH) ++nsc;
                 }
             }
             if (scattered) {
@@ -394,25 +535,27 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
             tau = -__logf(u01(r.w));
             // ---- a8: roulette ----
             if (w < 0.5f) {
-                const uint4 q = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk - 1u, 1u), k0, k1);
+                const uint4 q = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk - 1u, 1u),
+                                              RT_JB(key0), RT_JB(key1));
                 if (u01(q.x) > w) {
-                    atomicAdd(&s_led[1], (double)w * A.energy);
-                    atomicAdd(&s_cnt[1], 1ull);
+                    atomicAdd(&s_led[sid][1], (double)w * RT_JB(energy));
+                    atomicAdd(&s_cnt[sid][1], 1ull);
                     end_photon = true;
                 } else {
-                    atomicAdd(&s_led[0], (double)(1.0f - w) * A.energy);
+                    atomicAdd(&s_led[sid][0], (double)(1.0f - w) * RT_JB(energy));
                     w = 1.f;
                 }
             }
         } else if (ready == kSurface) {
             // ---- a9: Lambertian surface ----
             ++steps;
-            const int col = fj * A.nx + fi;
-            tally_add((direct ? A.tal.sfc_dir : A.tal.sfc_dif) + col, w, A.scale2);
-            atomicAdd(&s_cnt[0], 1ull);
-            w *= __ldg(A.alb + col);
+            const int col = fj * RT_SC(nx) + fi;
+            tally_add((direct ? RT_SC(tal.sfc_dir) : RT_SC(tal.sfc_dif)) + col, w, RT_JB(scale2));
+            atomicAdd(&s_cnt[sid][0], 1ull);
+            w *= __ldg(RT_SC(alb) + col);
             direct = false;
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk, 0u), k0, k1);
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk, 0u),
+                                          RT_JB(key0), RT_JB(key1));
             ++blk;
             lambert_up(ux, uy, uz, u01(r.x), u01(r.y));
             tau = -__logf(u01(r.w));
@@ -421,55 +564,75 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
             start_segment();
             if (w < 0.5f) {
                 if (u01(r.z) > w) {
-                    atomicAdd(&s_led[1], (double)w * A.energy);
-                    atomicAdd(&s_cnt[1], 1ull);
+                    atomicAdd(&s_led[sid][1], (double)w * RT_JB(energy));
+                    atomicAdd(&s_cnt[sid][1], 1ull);
                     end_photon = true;
                 } else {
-                    atomicAdd(&s_led[0], (double)(1.0f - w) * A.energy);
+                    atomicAdd(&s_led[sid][0], (double)(1.0f - w) * RT_JB(energy));
                     w = 1.f;
                 }
             }
         } else if (ready == kTop) {
             // ---- a10: leaves through the domain top ----
-            tally_add(A.tal.toa + (fj * A.nx + fi), w, A.scale2);
+            tally_add(RT_SC(tal.toa) + (fj * RT_SC(nx) + fi), w, RT_JB(scale2));
             end_photon = true;
         } else {
             // step cap: record, stop the photon, never spin
-            atomicAdd(&s_cnt[2], 1ull);
-            atomicAdd(&s_led[2], (double)w * A.energy);
-            atomicOr(&A.scr->status, kStatusBudget);
+            atomicAdd(&s_cnt[sid][2], 1ull);
+            atomicAdd(&s_led[sid][2], (double)w * RT_JB(energy));
+            atomicOr(&RT_SC(scr)->status, kStatusBudget);
             end_photon = true;
         }
         ready = kNone;
         if (end_photon) {
-            flush_partial(A, pcell, pdir, pacc);
+            flush();
             alive = false;
             c_max = max(c_max, nev);
+            if (BATCH) {
+                atomicAdd(&s_cnt[sid][3], 1ull);
+                atomicAdd(&s_cnt[sid][4], (unsigned long long)nev);
+                atomicAdd(&s_cnt[sid][5], (unsigned long long)nsc);
+                atomicAdd(&s_cnt[sid][6], (unsigned long long)ncr);
+                atomicMax(&RT_SC(scr)->max_events, (unsigned long long)nev);
+            }
         }
     }
 
     // ---- counters: warp reduction, one atomic per warp; block totals once ----
-    const unsigned long long s_ph = warp_sum_u32(c_ph), s_ev = warp_sum_u32(c_ev),
-                             s_sc = warp_sum_u32(c_sc), s_cr = warp_sum_u32(c_cr);
-    const unsigned m_ev = __reduce_max_sync(kFull, c_max);
-    Scratch *S = A.scr;
-    if (lane == 0) {
-        if (s_ph) atomicAdd(&S->photons, s_ph);
-        if (s_ev) atomicAdd(&S->events, s_ev);
-        if (s_sc) atomicAdd(&S->scatters, s_sc);
-        if (s_cr) atomicAdd(&S->crossings, s_cr);
-        if (m_ev) atomicMax(&S->max_events, (unsigned long long)m_ev);
+    if (!BATCH) {
+        const unsigned long long s_ph = warp_sum_u32(c_ph), s_ev = warp_sum_u32(c_ev),
+                                 s_sc = warp_sum_u32(c_sc), s_cr = warp_sum_u32(c_cr);
+        const unsigned m_ev = __reduce_max_sync(kFull, c_max);
+        Scratch *S = A.scene.scr;
+        if (lane == 0) {
+            if (s_ph) atomicAdd(&S->photons, s_ph);
+            if (s_ev) atomicAdd(&S->events, s_ev);
+            if (s_sc) atomicAdd(&S->scatters, s_sc);
+            if (s_cr) atomicAdd(&S->crossings, s_cr);
+            if (m_ev) atomicMax(&S->max_events, (unsigned long long)m_ev);
+        }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (s_cnt[0]) atomicAdd(&S->surface_hits, s_cnt[0]);
-        if (s_cnt[1]) atomicAdd(&S->roulette_kills, s_cnt[1]);
-        if (s_cnt[2]) atomicAdd(&S->capped, s_cnt[2]);
-        if (s_led[0] != 0.0) atomicAdd(&S->created, s_led[0]);
-        if (s_led[1] != 0.0) atomicAdd(&S->destroyed, s_led[1]);
-        if (s_led[2] != 0.0) atomicAdd(&S->capped_energy, s_led[2]);
+    const int nsc_blk = BATCH ? A.nscenes : 1;
+    for (int q = threadIdx.x; q < nsc_blk; q += blockDim.x) {
+        Scratch *S = BATCH ? s_scenes[q].scr : A.scene.scr;
+        if (s_cnt[q][0]) atomicAdd(&S->surface_hits, s_cnt[q][0]);
+        if (s_cnt[q][1]) atomicAdd(&S->roulette_kills, s_cnt[q][1]);
+        if (s_cnt[q][2]) atomicAdd(&S->capped, s_cnt[q][2]);
+        if (BATCH) {
+            if (s_cnt[q][3]) atomicAdd(&S->photons, s_cnt[q][3]);
+            if (s_cnt[q][4]) atomicAdd(&S->events, s_cnt[q][4]);
+            if (s_cnt[q][5]) atomicAdd(&S->scatters, s_cnt[q][5]);
+            if (s_cnt[q][6]) atomicAdd(&S->crossings, s_cnt[q][6]);
+        }
+        if (s_led[q][0] != 0.0) atomicAdd(&S->created, s_led[q][0]);
+        if (s_led[q][1] != 0.0) atomicAdd(&S->destroyed, s_led[q][1]);
+        if (s_led[q][2] != 0.0) atomicAdd(&S->capped_energy, s_led[q][2]);
     }
 }
+
+#undef RT_SC
+#undef RT_JB
 
 // ---------------------------------------------------------------------------
 // a12: FP64 normalisation and output fields. Tallies already hold W m^-3 and

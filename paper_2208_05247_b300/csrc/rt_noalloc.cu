@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) trace_fields(const __grid_constant__ Args
         const unsigned long long gid = atomicAdd(&A.hdr->queue_head, 1ull);
         if (gid >= A.count) break;
         // birth at the domain top along the sun beam
-        const unsigned col0 = (unsigned)(gid % A.ncol);
+        const unsigned col0 = (gid >> 32) ? (unsigned)(gid % A.ncol) : (uint32_t)gid % (uint32_t)A.ncol;
         const int ci = (int)(col0 % (unsigned)A.nx), cj = (int)(col0 / (unsigned)A.nx);
         const uint4 r0 = rt::philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), 0u, 0u), k0, k1);
         float ox = ((float)ci + rt::u01(r0.x)) * A.dx;
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) trace_fields(const __grid_constant__ Args
                 const float pabs = fminf(__fdividef(kabs, kmaj), 1.0f);
                 const float wn = w * (1.0f - pabs);
                 if (cell != pcell || direct != pdir) {
-                    if (pcell >= 0) atomicAdd((pdir ? A.abs_dir : A.abs_dif) + pcell, (double)pacc * A.scale3);
+                    if (pcell >= 0) atomicAdd((pdir ? A.abs_dir : A.abs_dif) + pcell, (double)(pacc * (float)A.scale3));
                     pcell = cell; pdir = direct; pacc = 0.f;
                 }
                 pacc += w - wn;
@@ -215,11 +215,10 @@ __global__ void __launch_bounds__(256) trace_fields(const __grid_constant__ Args
                 const float den = kmaj - kabs;
                 bool scattered = false;
                 if (den > 0.f) {
-                    const float rd = 1.0f / den;
-                    const float xi = rt::u01(r.x);
-                    if (xi < ksca * rd) {
-                        const float mu = (xi < ksc * rd) ? rt::hg_mu(A.gc[cell], rt::u01(r.y))
-                                                         : rt::rayleigh_mu(rt::u01(r.y));
+                    const float xd = rt::u01(r.x) * den;
+                    if (xd < ksca) {
+                        const float mu = (xd < ksc) ? rt::hg_mu(A.gc[cell], rt::u01(r.y))
+                                                    : rt::rayleigh_mu(rt::u01(r.y));
                         float sp, cp;
                         rt::azimuth(rt::u01(r.z), sp, cp);
                         rt::turn(ux, uy, uz, mu, sp, cp);
@@ -242,7 +241,7 @@ __global__ void __launch_bounds__(256) trace_fields(const __grid_constant__ Args
             } else if (what == 2) {
                 ++steps;
                 const int col = fj * A.nx + fi;
-                atomicAdd((direct ? A.sfc_dir : A.sfc_dif) + col, (double)w * A.scale2);
+                atomicAdd((direct ? A.sfc_dir : A.sfc_dif) + col, (double)(w * (float)A.scale2));
                 w *= A.alb[col];
                 direct = false;
                 const uint4 r = rt::philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk, 0u), k0, k1);
@@ -257,14 +256,14 @@ __global__ void __launch_bounds__(256) trace_fields(const __grid_constant__ Args
                     else w = 1.f;
                 }
             } else if (what == 3) {
-                atomicAdd(A.toa + (fj * A.nx + fi), (double)w * A.scale2);
+                atomicAdd(A.toa + (fj * A.nx + fi), (double)(w * (float)A.scale2));
                 end_photon = true;
             } else {
                 atomicOr(&A.hdr->status, kBudget);
                 end_photon = true;
             }
             if (end_photon) {
-                if (pcell >= 0) atomicAdd((pdir ? A.abs_dir : A.abs_dif) + pcell, (double)pacc * A.scale3);
+                if (pcell >= 0) atomicAdd((pdir ? A.abs_dir : A.abs_dif) + pcell, (double)(pacc * (float)A.scale3));
                 alive = false;
             }
         }

@@ -33,7 +33,13 @@ class rt_options(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("refill_chunk", ctypes.c_int), ("max_steps", ctypes.c_uint32),
                 ("pcld_mode", ctypes.c_int), ("tally_precision", ctypes.c_int),
-                ("ready_threshold", ctypes.c_int), ("max_inner", ctypes.c_int)]
+                ("ready_threshold", ctypes.c_int), ("max_inner", ctypes.c_int),
+                ("batch_optics", ctypes.c_int)]
+
+
+class rt_job(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_void_p), ("sza_deg", ctypes.c_double), ("azimuth_deg", ctypes.c_double),
+                ("toa_flux", ctypes.c_double), ("gas_scale", ctypes.c_double), ("photons", ctypes.c_uint64)]
 
 
 class rt_stats_t(ctypes.Structure):
@@ -72,6 +78,7 @@ def library() -> ctypes.CDLL:
             "rt_fields": ([H, P, P, P, P, i32], i32),
             "rt_fields_split": ([H, P, P, P, i32], i32),
             "rt_heating_rate": ([H, P, i32, i32], i32),
+            "rt_trace_batch": ([ctypes.POINTER(rt_job), i32, u64, u64], i32),
             "rt_reset_tallies": ([H], i32),
             "rt_stats": ([H, ctypes.POINTER(rt_stats_t)], i32),
             "rt_synchronize": ([H], i32),
@@ -200,6 +207,21 @@ def rt_trace_range(h, sza_deg, azimuth_deg, toa_flux, photon_begin, photon_count
     return _check(library().rt_trace_range(h, float(sza_deg), float(azimuth_deg), float(toa_flux),
                                            int(photon_begin), int(photon_count), int(photons_total),
                                            int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+
+def rt_trace_batch(jobs, total_photons=0, seed=1):
+    """jobs: sequence of dicts with scene (handle or Tracer), sza_deg, azimuth_deg,
+    toa_flux, gas_scale and photons (used when total_photons is 0)."""
+    arr = (rt_job * len(jobs))()
+    for a, j in zip(arr, jobs):
+        sc = j["scene"]
+        a.scene = sc.h if hasattr(sc, "h") else sc
+        a.sza_deg = float(j.get("sza_deg", 0.0))
+        a.azimuth_deg = float(j.get("azimuth_deg", 0.0))
+        a.toa_flux = float(j.get("toa_flux", 0.0))
+        a.gas_scale = float(j.get("gas_scale", 1.0))
+        a.photons = int(j.get("photons", 0))
+    return _check(library().rt_trace_batch(arr, len(jobs), int(total_photons), int(seed) & 0xFFFFFFFFFFFFFFFF))
 
 
 def rt_fields(h, ncell, ncol, abs3d=None, sfc_dir=None, sfc_dif=None, toa_up=None):

@@ -1,0 +1,206 @@
+"""GPU tests of rt_trace_batch: all spectral quadrature points of several scenes
+in one persistent launch (each quadrature point is traced independently,
+Sec. 2.3), with per-g-point gas scaling and energy-proportional budgets."""
+import copy
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_05247_b300 import rt, scenes
+from tests import refs
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("abs_dir", "abs_dif", "sfc_dir", "sfc_dif", "toa_up")
+
+
+def batch_tracer(scene, coarse=(4, 4, 4)):
+    t = rt.Tracer(scene.nx, scene.ny, scene.nz, scene.dx, scene.dy, scene.dz)
+    t.set_options(batch_optics=1)
+    t.set_optics(*scene.fields())
+    t.set_surface(scene.albedo)
+    t.build_accel(*coarse)
+    return t
+
+
+def scaled_gas(scene, s):
+    sc = copy.deepcopy(scene)
+    sc.k_gas = (sc.k_gas * np.float32(s)).astype(np.float32)
+    return sc
+
+
+def budgets(energies, total):
+    """The split rule of rt_trace_batch: proportional to energy, largest remainders first."""
+    e = np.asarray(energies, dtype=np.float64)
+    x = total * e / e.sum()
+    n = np.floor(x).astype(np.int64)
+    order = sorted(range(len(e)), key=lambda j: (-(x[j] - np.floor(x[j])), j))
+    for k in range(int(total - n.sum())):
+        n[order[k % len(e)]] += 1
+    return n
+
+
+def energy_of(scene, job):
+    return job["toa_flux"] * np.cos(np.deg2rad(job["sza_deg"])) * scene.nx * scene.dx * scene.ny * scene.dy
+
+
+def closes(st, tol=2e-6):
+    lhs = st["energy_in"] + st["energy_created"] - st["energy_destroyed"] - st["energy_capped"]
+    rhs = st["energy_toa_up"] + st["energy_atm_abs"] + st["energy_sfc_abs"]
+    return abs(lhs - rhs) < tol * st["energy_in"]
+
+
+def test_single_job_batch_matches_rt_trace_statistically(small_scene):
+    B, N = 12, 2 ** 18
+    g_b, g_t = {f: [] for f in FIELDS}, {f: [] for f in FIELDS}
+    tb = batch_tracer(small_scene)
+    with rt.Tracer.from_scene(small_scene, 4, 4, 4) as tt:
+        for s in range(B):
+            tb.reset()
+            rt.rt_trace_batch([dict(scene=tb, sza_deg=30.0, azimuth_deg=0.0, toa_flux=1000.0, gas_scale=1.0,
+                                    photons=N)], seed=100 + s)
+            fb, st = tb.fields(split=True), tb.stats()
+            assert st["photons"] == N and closes(st)
+            tt.reset()
+            tt.trace(30.0, 0.0, 1000.0, N, 300 + s)
+            ft = tt.fields(split=True)
+            for f in FIELDS:
+                g_b[f].append(fb[f])
+                g_t[f].append(ft[f])
+    tb.close()
+    for f in FIELDS:
+        rel, se = refs.domain_compare(np.stack(g_b[f]), np.stack(g_t[f]))
+        assert abs(rel) < 4 * se + 1e-12, (f, rel, se)
+
+
+@pytest.mark.parametrize("s", [1e-3, 0.37, 10.0])
+def test_gas_scale_equals_scaled_gas_fields(small_scene, s):
+    """A job with gas_scale s has the expectation of the scene with s * k_gas."""
+    B, N = 12, 2 ** 18
+    sc2 = scaled_gas(small_scene, s)
+    tb = batch_tracer(small_scene)
+    res_b = {f: [] for f in FIELDS}
+    for k in range(B):
+        tb.reset()
+        rt.rt_trace_batch([dict(scene=tb, sza_deg=50.0, azimuth_deg=70.0, toa_flux=500.0, gas_scale=s,
+                                photons=N)], seed=10 + k)
+        fb = tb.fields(split=True)
+        for f in FIELDS:
+            res_b[f].append(fb[f])
+        assert closes(tb.stats())
+    tb.close()
+    res_o = {f: [] for f in FIELDS}
+    for k in range(B):
+        r = oracle.trace(sc2, 50.0, 70.0, 500.0, N, 700 + k)
+        for f in FIELDS:
+            res_o[f].append(getattr(r, f))
+    for f in FIELDS:
+        rel, se = refs.domain_compare(np.stack(res_b[f]), np.stack(res_o[f]))
+        assert abs(rel) < 4 * se + 1e-12, (s, f, rel, se)
+
+
+def test_multi_scene_batch_parity_with_oracle():
+    """Two scenes of different sizes, four g-points each (gas scale, flux and
+    sun differ), one launch with an energy-proportional budget: each scene's
+    tallies match the oracle's sum over the same jobs."""
+    scA = scenes.ellipsoid_scene(seed=0)
+    scB = scenes.cumulus_scene(seed=5, nx=48, ny=40, nz=32)
+    gp = [(0.01, 180.0), (0.3, 300.0), (1.0, 350.0), (6.0, 170.0)]
+    jobsA = [dict(sza_deg=30.0, azimuth_deg=20.0, toa_flux=f, gas_scale=s) for s, f in gp]
+    jobsB = [dict(sza_deg=55.0, azimuth_deg=228.1, toa_flux=f, gas_scale=s) for s, f in gp]
+    total = 2 ** 21
+    n = budgets([energy_of(scA, j) for j in jobsA] + [energy_of(scB, j) for j in jobsB], total)
+    tA, tB = batch_tracer(scA), batch_tracer(scB)
+    B = 10
+    gpu = {"A": {f: [] for f in FIELDS}, "B": {f: [] for f in FIELDS}}
+    for k in range(B):
+        tA.reset()
+        tB.reset()
+        jobs = [dict(j, scene=tA) for j in jobsA] + [dict(j, scene=tB) for j in jobsB]
+        rt.rt_trace_batch(jobs, total_photons=total, seed=1000 + k)
+        for name, t in (("A", tA), ("B", tB)):
+            st = t.stats()
+            assert closes(st), name
+            want = int(n[:4].sum() if name == "A" else n[4:].sum())
+            assert st["photons"] == want, (name, st["photons"], want)
+            fb = t.fields(split=True)
+            for f in FIELDS:
+                gpu[name][f].append(fb[f])
+    tA.close()
+    tB.close()
+    orc = {"A": {f: [] for f in FIELDS}, "B": {f: [] for f in FIELDS}}
+    for k in range(B):
+        for name, sc, jobs, nn in (("A", scA, jobsA, n[:4]), ("B", scB, jobsB, n[4:])):
+            acc = {f: 0.0 for f in FIELDS}
+            for q, (j, nj) in enumerate(zip(jobs, nn)):
+                r = oracle.trace(scaled_gas(sc, j["gas_scale"]), j["sza_deg"], j["azimuth_deg"], j["toa_flux"],
+                                 int(nj), 5000 + 100 * k + 10 * (name == "B") + q)
+                for f in FIELDS:
+                    acc[f] = acc[f] + getattr(r, f)
+            for f in FIELDS:
+                orc[name][f].append(acc[f])
+    for name in ("A", "B"):
+        for f in FIELDS:
+            rel, se = refs.domain_compare(np.stack(gpu[name][f]), np.stack(orc[name][f]))
+            assert abs(rel) < max(0.005, 4 * se), (name, f, rel, se)
+
+
+def test_zero_flux_jobs_and_more_than_512_jobs(small_scene):
+    t = batch_tracer(small_scene)
+    jobs = [dict(scene=t, sza_deg=30.0, azimuth_deg=0.0, toa_flux=(0.0 if j % 7 == 0 else 1.0 + j % 5),
+                 gas_scale=0.5 + 0.01 * j) for j in range(600)]
+    total = 600_000
+    n = budgets([energy_of(small_scene, j) for j in jobs], total)
+    assert n[0] == 0 and n.sum() == total
+    rt.rt_trace_batch(jobs, total_photons=total, seed=3)
+    st = t.stats()
+    assert st["photons"] == total and closes(st)
+    assert np.isclose(st["energy_in"], sum(energy_of(small_scene, j) for j in jobs), rtol=1e-12)
+    t.close()
+
+
+def test_batch_errors(small_scene):
+    with rt.Tracer.from_scene(small_scene) as plain:
+        with pytest.raises(rt.RtError) as e:
+            rt.rt_trace_batch([dict(scene=plain, sza_deg=30.0, toa_flux=1.0, photons=10)])
+        assert e.value.code == rt.RT_E_STATE
+    t = batch_tracer(small_scene)
+    for bad in (dict(sza_deg=95.0), dict(gas_scale=-1.0), dict(toa_flux=float("nan"))):
+        j = dict(scene=t, sza_deg=30.0, toa_flux=1.0, gas_scale=1.0, photons=10)
+        j.update(bad)
+        with pytest.raises(rt.RtError) as e:
+            rt.rt_trace_batch([j])
+        assert e.value.code == rt.RT_E_INVAL
+    with pytest.raises(rt.RtError):
+        rt.rt_trace_batch([dict(scene=t, sza_deg=30.0, toa_flux=0.0, photons=0)], total_photons=100)
+    tiny = scenes.layered_scene(2, 2, 2, 10.0, 10.0, 10.0, k_gas=1e-3, ssa_gas=0.5)
+    many = [batch_tracer(tiny, (1, 1, 1)) for _ in range(17)]
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_trace_batch([dict(scene=m, sza_deg=10.0, toa_flux=1.0, photons=5) for m in many])
+    assert e.value.code == rt.RT_E_INVAL
+    for m in many:
+        m.close()
+    t.close()
+
+
+def test_full_batched_workload_closes_and_splits_budgets():
+    """The batched workload at full size: 4 scenes of uneven size x 112
+    g-points, 2^26 photons in one call (launched in 512-job chunks)."""
+    scs = scenes.batch_scenes()
+    scale, flux = scenes.gpoint_table()
+    tr = [batch_tracer(sc) for sc in scs]
+    jobs = [dict(scene=t, sza_deg=30.0, azimuth_deg=0.0, toa_flux=float(f), gas_scale=float(s))
+            for t in tr for s, f in zip(scale, flux)]
+    total = 2 ** 26
+    n = budgets([energy_of(sc, dict(toa_flux=float(f), sza_deg=30.0)) for sc in scs for f in flux], total)
+    rt.rt_trace_batch(jobs, total_photons=total, seed=11)
+    for q, (t, sc) in enumerate(zip(tr, scs)):
+        st = t.stats()
+        assert st["status"] == 0 and st["capped"] == 0
+        assert st["photons"] == int(n[q * 112:(q + 1) * 112].sum())
+        assert closes(st)
+        # every scene receives 1000 W m^-2 * cos(30) through its top in total
+        area = sc.nx * sc.dx * sc.ny * sc.dy
+        assert np.isclose(st["energy_in"], 1000.0 * np.cos(np.deg2rad(30.0)) * area, rtol=1e-9)
+        t.close()
