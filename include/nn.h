@@ -1,0 +1,106 @@
+/*
+ * nn.h -- C ABI of the BF16 tensor-core kernels behind the learned denoiser.
+ *
+ * The paper traces every field at 256 samples per pixel and reports that the
+ * error falls only as N^-1/2 while the cost grows as N (Sec. 3.2). The denoiser
+ * built on these kernels (a 3D U-Net) maps a field traced with few photons,
+ * plus the optics, to the field a high photon count would give. The paper has
+ * no denoiser; these kernels are its training and inference path.
+ *
+ * Conventions
+ *   - Activations and activation gradients: BF16, channels last,
+ *     [N][D][H][W][C] (C fastest), device memory. Convolutions need C_in a
+ *     multiple of 16.
+ *   - Master weights and weight gradients: FP32 [taps][C_in][C_out] with
+ *     taps = 27 (3x3x3, tap t = 9 (dz+1) + 3 (dy+1) + (dx+1)) or 1 (1x1x1).
+ *     The convolution kernel reads BF16 weights in [taps][C_out][C_in]
+ *     ("wt") and, for the input gradient, [taps][C_in][C_out] with the taps
+ *     reversed ("wd"); nn_weights_bf16 writes both.
+ *   - Padding is "same" with zeros outside the volume.
+ *   - All products are accumulated in FP32 by mma.sync (BF16 inputs).
+ *   - Every call is ordered on `stream` (NULL = default stream) and returns
+ *     NN_OK or a negative NN_E_* code; nn_last_error() gives the message.
+ */
+#ifndef NN_B300_H
+#define NN_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { NN_OK = 0, NN_E_INVAL = -1, NN_E_CUDA = -3 };
+
+const char *nn_last_error(void);
+
+/* out[p][o] = act(bias[o] + sum_t sum_i in[p + off(t)][i] W[t][i][o]) with
+ * act = ReLU if relu != 0. wt: BF16 [taps][Cout][Cin]. bias may be NULL.
+ * Writes out_bf16 (BF16 [vox][Cout], Cout even) and/or out_f32 (FP32). With
+ * the input gradient of a convolution as `in` and its "wd" weights, this is
+ * the gradient with respect to that convolution's input (Cin, Cout swapped). */
+int nn_conv3d_fwd(const void *in, const void *wt, const float *bias, void *out_bf16, float *out_f32, int N, int D,
+                  int H, int W, int Cin, int Cout, int ksize, int relu, void *stream);
+
+/* gw[t][i][o] += sum_p in[p + off(t)][i] gout[p][o]; gb[o] += sum_p gout[p][o]
+ * (gb may be NULL). FP32 atomics: zero gw and gb first. Channels multiples of 8. */
+int nn_conv3d_wgrad(const void *in, const void *gout, float *gw, float *gb, int N, int D, int H, int W, int Cin,
+                    int Cout, int ksize, void *stream);
+
+/* g[i] = 0 where y[i] <= 0 (gradient through ReLU, y the ReLU output). */
+int nn_relu_bwd(const void *y, void *g, long long n, void *stream);
+
+/* 2x2x2 average pooling [N][D][H][W][C] -> [N][D/2][H/2][W/2][C] and its gradient. */
+int nn_pool2_fwd(const void *in, void *out, int N, int D, int H, int W, int C, void *stream);
+int nn_pool2_bwd(const void *gout, void *gin, int N, int D, int H, int W, int C, void *stream);
+
+/* Nearest 2x upsampling of [N][d][h][w][C] into channels [c0, c0+C) of a
+ * [N][2d][2h][2w][Cdst] tensor, and its gradient (sum over the 8 children). */
+int nn_up2_fwd(const void *in, void *out, int N, int d, int h, int w, int C, int Cdst, int c0, void *stream);
+int nn_up2_bwd(const void *gout, void *gin, int N, int d, int h, int w, int C, int Csrc, int c0, void *stream);
+
+/* dst[v][d0 + c] (+)= src[v][s0 + c] for c < C over vox voxels (concatenation
+ * and its gradient). */
+int nn_copy_channels(const void *src, int Csrc, int s0, void *dst, int Cdst, int d0, long long vox, int C,
+                     int accumulate, void *stream);
+
+/* Mean weighted squared error of FP32 pred [vox][Cp] (channels < Cuse) against
+ * FP32 target [vox][Cuse], channel weights chw (NULL = 1); writes the BF16
+ * gradient [vox][Cp] and ADDS the loss to *loss (device double). */
+int nn_mse(const float *pred, int Cp, const float *target, int Cuse, const float *chw, void *grad, long long vox,
+           double *loss, void *stream);
+
+/* One Adam step (bias-corrected, optional decoupled-style L2 term) on FP32
+ * master parameters; step counts from 1. */
+int nn_adam(float *W, float *m, float *v, const float *grad, long long n, float lr, float b1, float b2, float eps,
+            int step, float weight_decay, void *stream);
+
+/* BF16 copies of FP32 W [taps][Cin][Cout]: wt [taps][Cout][Cin] for the
+ * forward pass and wd [taps][Cin][Cout] with reversed taps for the input
+ * gradient (either may be NULL). */
+int nn_weights_bf16(const float *W, void *wt, void *wd, int ksize, int Cin, int Cout, void *stream);
+
+/* Denoiser inputs from a traced field (FP64 [D][H][W] absorption [W m^-3],
+ * [H][W] surface direct/diffuse [W m^-2]) and the optics (FP32 [D][H][W]):
+ * BF16 [D][H][W][16] with channels 0: 100 A dz / F, 1: direct / F, 2: diffuse
+ * / F (surface values repeated in every layer), 3: log(tau_cell + 1e-4) / 5,
+ * 4: k_sca / k_ext, 5: cloud g, 6..15: 0. F = toa_flux cos(sza) [W m^-2]. */
+int nn_pack_inputs(const double *abs3d, const double *sfc_dir, const double *sfc_dif, const float *k_gas,
+                   const float *ssa_gas, const float *k_cld, const float *ssa_cld, const float *g_cld, void *out,
+                   int D, int H, int W, double dz, double flux, void *stream);
+
+/* Training targets FP32 [D][H][W][3]: channels 0..2 of the high-photon field
+ * minus those of the low-photon field (as BF16-rounded inputs hold them). */
+int nn_pack_targets(const double *abs_hi, const double *sdir_hi, const double *sdif_hi, const double *abs_lo,
+                    const double *sdir_lo, const double *sdif_lo, float *out, int D, int H, int W, double dz,
+                    double flux, void *stream);
+
+/* Denoised fields: input channel + predicted correction (pred FP32 [vox][Cp]),
+ * back to W m^-3 and W m^-2; surface fields from the bottom layer. */
+int nn_unpack(const void *in, const float *pred, int Cp, double *abs3d, double *sfc_dir, double *sfc_dif, int D,
+              int H, int W, double dz, double flux, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NN_B300_H */

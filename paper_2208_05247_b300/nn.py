@@ -1,0 +1,127 @@
+"""Python binding of the denoiser kernels declared in include/nn.h.
+
+Argument marshalling only: tensors are CUDA torch tensors (device memory and
+streams come from torch); every computation runs in librt_b300.so.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from .rt import library
+
+NN_OK = 0
+
+_sig_done = False
+
+
+def _lib():
+    global _sig_done
+    lib = library()
+    if not _sig_done:
+        P, i32, i64, f32, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_float, ctypes.c_double
+        sig = {
+            "nn_last_error": ([], ctypes.c_char_p),
+            "nn_conv3d_fwd": ([P, P, P, P, P] + [i32] * 8 + [P], i32),
+            "nn_conv3d_wgrad": ([P, P, P, P] + [i32] * 7 + [P], i32),
+            "nn_relu_bwd": ([P, P, i64, P], i32),
+            "nn_pool2_fwd": ([P, P] + [i32] * 5 + [P], i32),
+            "nn_pool2_bwd": ([P, P] + [i32] * 5 + [P], i32),
+            "nn_up2_fwd": ([P, P] + [i32] * 7 + [P], i32),
+            "nn_up2_bwd": ([P, P] + [i32] * 7 + [P], i32),
+            "nn_copy_channels": ([P, i32, i32, P, i32, i32, i64, i32, i32, P], i32),
+            "nn_mse": ([P, i32, P, i32, P, P, i64, P, P], i32),
+            "nn_adam": ([P, P, P, P, i64, f32, f32, f32, f32, i32, f32, P], i32),
+            "nn_weights_bf16": ([P, P, P, i32, i32, i32, P], i32),
+            "nn_pack_inputs": ([P] * 9 + [i32] * 3 + [f64, f64, P], i32),
+            "nn_pack_targets": ([P] * 7 + [i32] * 3 + [f64, f64, P], i32),
+            "nn_unpack": ([P, P, i32, P, P, P] + [i32] * 3 + [f64, f64, P], i32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _sig_done = True
+    return lib
+
+
+class NnError(RuntimeError):
+    pass
+
+
+def _check(rc):
+    if rc != NN_OK:
+        raise NnError(_lib().nn_last_error().decode())
+
+
+def _p(t):
+    return None if t is None else t.data_ptr()
+
+
+def _s(stream):
+    return None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+
+
+def nn_conv3d_fwd(x, wt, bias, out_bf16, out_f32, N, D, H, W, Cin, Cout, ksize, relu, stream=None):
+    _check(_lib().nn_conv3d_fwd(_p(x), _p(wt), _p(bias), _p(out_bf16), _p(out_f32), N, D, H, W, Cin, Cout, ksize,
+                                int(relu), _s(stream)))
+
+
+def nn_conv3d_wgrad(x, gout, gw, gb, N, D, H, W, Cin, Cout, ksize, stream=None):
+    _check(_lib().nn_conv3d_wgrad(_p(x), _p(gout), _p(gw), _p(gb), N, D, H, W, Cin, Cout, ksize, _s(stream)))
+
+
+def nn_relu_bwd(y, g, stream=None):
+    _check(_lib().nn_relu_bwd(_p(y), _p(g), g.numel(), _s(stream)))
+
+
+def nn_pool2_fwd(x, out, N, D, H, W, C, stream=None):
+    _check(_lib().nn_pool2_fwd(_p(x), _p(out), N, D, H, W, C, _s(stream)))
+
+
+def nn_pool2_bwd(gout, gin, N, D, H, W, C, stream=None):
+    _check(_lib().nn_pool2_bwd(_p(gout), _p(gin), N, D, H, W, C, _s(stream)))
+
+
+def nn_up2_fwd(x, out, N, d, h, w, C, Cdst, c0, stream=None):
+    _check(_lib().nn_up2_fwd(_p(x), _p(out), N, d, h, w, C, Cdst, c0, _s(stream)))
+
+
+def nn_up2_bwd(gout, gin, N, d, h, w, C, Csrc, c0, stream=None):
+    _check(_lib().nn_up2_bwd(_p(gout), _p(gin), N, d, h, w, C, Csrc, c0, _s(stream)))
+
+
+def nn_copy_channels(src, Csrc, s0, dst, Cdst, d0, vox, C, accumulate=False, stream=None):
+    _check(_lib().nn_copy_channels(_p(src), Csrc, s0, _p(dst), Cdst, d0, vox, C, int(accumulate), _s(stream)))
+
+
+def nn_mse(pred, Cp, target, Cuse, chw, grad, vox, loss, stream=None):
+    _check(_lib().nn_mse(_p(pred), Cp, _p(target), Cuse, _p(chw), _p(grad), vox, _p(loss), _s(stream)))
+
+
+def nn_adam(W, m, v, grad, lr, step, b1=0.9, b2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
+    _check(_lib().nn_adam(_p(W), _p(m), _p(v), _p(grad), W.numel(), lr, b1, b2, eps, step, weight_decay,
+                          _s(stream)))
+
+
+def nn_weights_bf16(W, wt, wd, ksize, Cin, Cout, stream=None):
+    _check(_lib().nn_weights_bf16(_p(W), _p(wt), _p(wd), ksize, Cin, Cout, _s(stream)))
+
+
+def nn_pack_inputs(abs3d, sfc_dir, sfc_dif, k_gas, ssa_gas, k_cld, ssa_cld, g_cld, out, D, H, W, dz, flux,
+                   stream=None):
+    _check(_lib().nn_pack_inputs(*[_p(t) for t in (abs3d, sfc_dir, sfc_dif, k_gas, ssa_gas, k_cld, ssa_cld, g_cld,
+                                                    out)], D, H, W, float(dz), float(flux), _s(stream)))
+
+
+def nn_pack_targets(abs_hi, sdir_hi, sdif_hi, abs_lo, sdir_lo, sdif_lo, out, D, H, W, dz, flux, stream=None):
+    _check(_lib().nn_pack_targets(*[_p(t) for t in (abs_hi, sdir_hi, sdif_hi, abs_lo, sdir_lo, sdif_lo, out)],
+                                  D, H, W, float(dz), float(flux), _s(stream)))
+
+
+def nn_unpack(x, pred, Cp, abs3d, sfc_dir, sfc_dif, D, H, W, dz, flux, stream=None):
+    _check(_lib().nn_unpack(_p(x), _p(pred), Cp, _p(abs3d), _p(sfc_dir), _p(sfc_dif), D, H, W, float(dz),
+                            float(flux), _s(stream)))
+
+
+def nn_last_error() -> str:
+    return _lib().nn_last_error().decode()

@@ -1,0 +1,147 @@
+"""GPU tests of the denoiser's BF16 tensor-core kernels against the FP64 numpy
+reference (oracle/nn_ref.py). Inputs are rounded to BF16 on both sides, so the
+remaining difference is FP32 accumulation (and BF16 rounding of BF16 outputs)."""
+import numpy as np
+import pytest
+
+from oracle import nn_ref
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2208_05247_b300 import build, nn  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def bf(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to("cuda").to(torch.bfloat16)
+
+
+def f32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to("cuda")
+
+
+def host(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def weights_dev(W, ksize):
+    taps, Cin, Cout = W.shape
+    Wd = f32(W)
+    wt = torch.empty(taps * Cin * Cout, dtype=torch.bfloat16, device="cuda")
+    wd = torch.empty_like(wt)
+    nn.nn_weights_bf16(Wd, wt, wd, ksize, Cin, Cout)
+    return wt, wd
+
+
+def _tol(x, W, b=None):
+    """FP32 accumulation bound: a few ulps of the sum of |terms| per output."""
+    mag = nn_ref.conv3d(np.abs(x), np.abs(W), None if b is None else np.abs(b), ksize=3 if W.shape[0] == 27 else 1)
+    return 1e-5 * mag + 1e-6
+
+
+@pytest.mark.parametrize("ksize,shape,Cin,Cout,relu", [
+    (3, (2, 3, 5, 7), 16, 24, True),
+    (3, (1, 8, 8, 8), 32, 64, False),
+    (1, (1, 4, 6, 9), 32, 16, False),
+    (3, (1, 5, 3, 130), 48, 40, True),
+])
+def test_conv_forward(ksize, shape, Cin, Cout, relu):
+    rng = np.random.default_rng(Cin + Cout)
+    taps = 27 if ksize == 3 else 1
+    x = nn_ref.bf16_round(rng.normal(size=shape + (Cin,)))
+    W = nn_ref.bf16_round(rng.normal(size=(taps, Cin, Cout)) / np.sqrt(taps * Cin))
+    b = rng.normal(size=Cout).astype(np.float32)
+    ref = nn_ref.conv3d(x, W, b, ksize, relu)
+    wt, _ = weights_dev(W, ksize)
+    out = torch.empty(int(np.prod(shape)) * Cout, dtype=torch.float32, device="cuda")
+    outb = torch.empty(int(np.prod(shape)) * Cout, dtype=torch.bfloat16, device="cuda")
+    nn.nn_conv3d_fwd(bf(x), wt, f32(b), outb, out, *shape, Cin, Cout, ksize, relu)
+    torch.cuda.synchronize()
+    got = host(out).reshape(ref.shape)
+    assert np.all(np.abs(got - ref) <= _tol(x, W, b)), np.abs(got - ref).max()
+    gotb = host(outb).reshape(ref.shape)
+    assert np.all(np.abs(gotb - ref) <= 2 ** -8 * np.abs(ref) + _tol(x, W, b))
+
+
+@pytest.mark.parametrize("ksize,shape,Cin,Cout", [(3, (2, 3, 4, 5), 16, 32), (3, (1, 6, 5, 4), 32, 48),
+                                                  (1, (1, 4, 4, 4), 32, 16)])
+def test_conv_input_and_weight_gradients(ksize, shape, Cin, Cout):
+    rng = np.random.default_rng(7 + Cin)
+    taps = 27 if ksize == 3 else 1
+    x = nn_ref.bf16_round(rng.normal(size=shape + (Cin,)))
+    W = nn_ref.bf16_round(rng.normal(size=(taps, Cin, Cout)) / np.sqrt(taps * Cin))
+    g = nn_ref.bf16_round(rng.normal(size=shape + (Cout,)))
+    gx_ref, gW_ref, gb_ref = nn_ref.conv3d_backward(x, W, g, ksize)
+    _, wd = weights_dev(W, ksize)
+    vox = int(np.prod(shape))
+    gx = torch.empty(vox * Cin, dtype=torch.float32, device="cuda")
+    nn.nn_conv3d_fwd(bf(g), wd, None, None, gx, *shape, Cout, Cin, ksize, False)
+    gw = torch.zeros(taps * Cin * Cout, dtype=torch.float32, device="cuda")
+    gb = torch.zeros(Cout, dtype=torch.float32, device="cuda")
+    nn.nn_conv3d_wgrad(bf(x), bf(g), gw, gb, *shape, Cin, Cout, ksize)
+    torch.cuda.synchronize()
+    mag_x = np.abs(nn_ref.conv3d_backward(np.abs(x), np.abs(W), np.abs(g), ksize)[0])
+    assert np.all(np.abs(host(gx).reshape(gx_ref.shape) - gx_ref) <= 1e-5 * mag_x + 1e-6)
+    mag_w = np.abs(nn_ref.conv3d_backward(np.abs(x), np.abs(W), np.abs(g), ksize)[1])
+    assert np.all(np.abs(host(gw).reshape(gW_ref.shape) - gW_ref) <= 1e-5 * mag_w + 1e-5)
+    assert np.allclose(host(gb), gb_ref, rtol=1e-5, atol=1e-4)
+
+
+def test_pool_upsample_concat_relu_and_loss():
+    rng = np.random.default_rng(3)
+    x = nn_ref.bf16_round(rng.normal(size=(1, 4, 6, 8, 16)))
+    N, D, H, W, C = x.shape
+    p = torch.empty(N * 2 * 3 * 4 * C, dtype=torch.bfloat16, device="cuda")
+    nn.nn_pool2_fwd(bf(x), p, N, D, H, W, C)
+    assert np.allclose(host(p).reshape(1, 2, 3, 4, C), nn_ref.pool2(x), rtol=2 ** -8, atol=1e-3)
+    gp = nn_ref.bf16_round(rng.normal(size=(1, 2, 3, 4, C)))
+    gx = torch.empty(x.size, dtype=torch.bfloat16, device="cuda")
+    nn.nn_pool2_bwd(bf(gp), gx, N, D, H, W, C)
+    assert np.allclose(host(gx).reshape(x.shape), nn_ref.pool2_backward(gp), rtol=2 ** -8, atol=1e-4)
+    # upsample into the first 16 of 48 channels; the other 32 from a skip tensor
+    y = nn_ref.bf16_round(rng.normal(size=(1, 2, 3, 4, 16)))
+    skip = nn_ref.bf16_round(rng.normal(size=(1, 4, 6, 8, 32)))
+    cat = torch.zeros(x.size // 16 * 48, dtype=torch.bfloat16, device="cuda")
+    nn.nn_up2_fwd(bf(y), cat, 1, 2, 3, 4, 16, 48, 0)
+    nn.nn_copy_channels(bf(skip), 32, 0, cat, 48, 16, x.size // 16, 32)
+    want = np.concatenate([nn_ref.up2(y), skip], axis=-1)
+    assert np.array_equal(host(cat).reshape(want.shape), want)
+    gcat = nn_ref.bf16_round(rng.normal(size=want.shape))
+    gy = torch.empty(y.size, dtype=torch.bfloat16, device="cuda")
+    nn.nn_up2_bwd(bf(gcat), gy, 1, 2, 3, 4, 16, 48, 0)
+    assert np.allclose(host(gy).reshape(y.shape), nn_ref.up2_backward(gcat[..., :16]), rtol=2 ** -7, atol=1e-2)
+    # ReLU gradient mask
+    yr = bf(np.maximum(x, 0))
+    g = bf(np.ones_like(x))
+    nn.nn_relu_bwd(yr, g)
+    assert np.array_equal(host(g).ravel(), (x > 0).astype(np.float64).ravel())
+    # loss and its gradient
+    pred = rng.normal(size=(500, 16)).astype(np.float32)
+    tgt = rng.normal(size=(500, 3)).astype(np.float32)
+    w = np.array([1.0, 2.0, 0.5], np.float32)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    grad = torch.empty(500 * 16, dtype=torch.bfloat16, device="cuda")
+    nn.nn_mse(f32(pred), 16, f32(tgt), 3, f32(w), grad, 500, loss)
+    l_ref, g_ref = nn_ref.mse(pred, tgt, w)
+    assert np.isclose(loss.item(), l_ref, rtol=1e-6)
+    assert np.allclose(host(grad).reshape(500, 16), g_ref, rtol=2 ** -8, atol=1e-9)
+
+
+def test_adam_step():
+    rng = np.random.default_rng(5)
+    W = rng.normal(size=1000).astype(np.float32)
+    g = rng.normal(size=1000).astype(np.float32)
+    m = np.zeros(1000, np.float32)
+    v = np.zeros(1000, np.float32)
+    Wd, md, vd, gd = f32(W), f32(m), f32(v), f32(g)
+    for step in (1, 2, 3):
+        nn.nn_adam(Wd, md, vd, gd, 1e-3, step)
+        m = 0.9 * m + 0.1 * g
+        v = 0.999 * v + 0.001 * g * g
+        W = W - 1e-3 * (m / (1 - 0.9 ** step)) / (np.sqrt(v / (1 - 0.999 ** step)) + 1e-8)
+    assert np.allclose(Wd.cpu().numpy(), W, rtol=1e-5, atol=1e-6)
