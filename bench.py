@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-ppc", type=int, default=16)
+    p.add_argument("--no-denoise", action="store_true", help="skip the denoised-vs-plain time-to-RMSE leg")
+    p.add_argument("--denoise-train", type=int, default=64, help="training scenes of the denoiser leg")
     p.add_argument("--no-autotune", action="store_true",
                    help="use the default launch parameters and a 4x4x4 coarse grid")
     return p.parse_args()
@@ -195,6 +197,33 @@ def run_reference(args):
                              "photons_per_s": photons / secs},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---- denoised vs plain: wall time to a target RMS error ----------------------------------
+
+def denoise_leg(args):
+    """Train the 3D U-Net on tracer pairs (4 vs 1024 photons/column, 128^3
+    cumulus scenes) and time denoised 4-photon runs against the plain tracer at
+    matched RMS error of GHI and heating rate on held-out scenes."""
+    from paper_2208_05247_b300 import denoise
+    shape = (128, 128, 128)
+    t0 = time.time()
+    pairs = denoise.make_pairs(list(range(1000, 1000 + args.denoise_train)), shape, workers=os.cpu_count() or 8)
+    t_pairs = time.time() - t0
+    net = denoise.UNet(seed=0)
+    t0 = time.time()
+    losses = denoise.train(net, pairs, epochs=4, lr=1e-3)
+    t_train = time.time() - t0
+    del pairs
+    res = denoise.evaluate(net, list(range(1512, 1520)), shape, truth_ppc=4096, workers=os.cpu_count() or 8)
+    return {"workload": "cumulus 128x128x128 (dx=dy=50 m, dz=25 m), sza 0/30/60, held-out seeds 1512-1519, "
+                        "truth 4096 photons/column",
+            "training": {"scenes": args.denoise_train, "epochs": 4, "pairs_s": t_pairs, "train_s": t_train,
+                         "loss_first": losses[0][1], "loss_last": losses[-1][1]},
+            "plain": res["plain"], "denoised": res["denoised"], "noisy_input": res["noisy_input"],
+            "plain_ppc_to_match": {"ghi": res["plain_ppc_to_match_ghi"], "hr": res["plain_ppc_to_match_hr"]},
+            "speedup": {"ghi": res["speedup_ghi"], "hr": res["speedup_hr"]},
+            "network": {"params": net.n_params(), "forward_gflop": net.flops(shape) / 1e9}}
 
 
 # ---- our CUDA path --------------------------------------------------------------------
@@ -334,6 +363,9 @@ def run_ours(args):
                "sample": f"{args.cpu_sample_ppc} photons/column ({tot['photons']} photons) of the benchmark "
                          f"scene, {dt:.1f} s wall; oracle collisions are all real (analog tracer)",
                "photons_per_s": tot["photons"] / dt}
+    dn = None
+    if world == 1 and not args.no_denoise:
+        dn = denoise_leg(args)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -342,7 +374,7 @@ def run_ours(args):
             "real_scatters_per_s": st["scatters"] * world * args.steps / (ms_max / 1e3),
             "events_per_step": events_all, "real_scatter_fraction": st["scatters"] / max(1, events),
             "trace_kernel_ms": 1e3 * tk, "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": KERNELS_PER_STEP * args.steps}
+            "gpu_launches": KERNELS_PER_STEP * args.steps, "time_to_rmse": dn}
     print(json.dumps(line), flush=True)
     t.close()
     if dist is not None:
