@@ -62,7 +62,9 @@ def parse():
     p.add_argument("--no-denoise", action="store_true", help="skip the denoised-vs-plain time-to-RMSE leg")
     p.add_argument("--denoise-train", type=int, default=64, help="training scenes of the denoiser leg")
     p.add_argument("--no-autotune", action="store_true",
-                   help="use the default launch parameters and a 4x4x4 coarse grid")
+                   help="use the default launch parameters and the --coarse grid")
+    p.add_argument("--coarse", type=int, nargs=3, default=None,
+                   help="coarse grid factors; implies --no-autotune")
     return p.parse_args()
 
 
@@ -259,9 +261,9 @@ def run_ours(args):
     t = rt.Tracer(scene.nx, scene.ny, scene.nz, scene.dx, scene.dy, scene.dz, stream=stream)
     t.set_optics(*d_in)
     t.set_surface(d_alb)
-    coarse = COARSE
+    coarse = tuple(args.coarse) if args.coarse else COARSE
     tuned = None
-    if not args.no_autotune:
+    if not args.no_autotune and not args.coarse:
         # untimed: pick coarse factors and launch parameters by photons/s
         from paper_2208_05247_b300 import autotune
         tuned, _ = autotune.autotune(t, args.sza, AZ, F0, N, seed=SEED + 1000)

@@ -137,6 +137,16 @@ int rt_get_options(rt_handle h, rt_options *opt);
 int rt_set_optics(rt_handle h, const float *k_gas, const float *ssa_gas, const float *k_cld,
                   const float *ssa_cld, const float *g_cld, int mem);
 
+/* The paper's own optics inputs (Sec. 2.3: total extinction, cloud extinction,
+ * single-scattering albedo and asymmetry): four float arrays [nz][ny][nx] of
+ * total k_ext [m^-1], cloud k_ext,cloud (<= k_ext), albedo and cloud g. A
+ * scattering is by cloud with probability k_ext,cloud / k_ext, the paper's
+ * ratio. Equivalent to rt_set_optics with k_gas = k_ext - k_ext,cloud and both
+ * albedos equal. Not usable with rt_trace_batch (no gas/cloud split of the
+ * albedo). Errors and state as rt_set_optics. */
+int rt_set_optics_total(rt_handle h, const float *k_ext, const float *k_ext_cld, const float *ssa,
+                        const float *g_cld, int mem);
+
 /* Lambertian surface albedo per column (Sec. 2.3), nx*ny floats in [0,1]. */
 int rt_set_surface(rt_handle h, const float *albedo, int mem);
 
@@ -173,6 +183,7 @@ typedef struct {
     double toa_flux;       /* flux of this quadrature point normal to the beam [W m^-2] */
     double gas_scale;      /* factor on the scene's gas extinction (absorption and scattering) */
     uint64_t photons;      /* photons of this job when total_photons is 0 */
+    double diffuse_fraction; /* share of the top flux entering diffuse (as rt_trace_ex) */
 } rt_job;
 
 /* Trace all jobs -- every spectral quadrature point of several scenes of
@@ -191,6 +202,14 @@ typedef struct {
  * ledger are added to each job's own scene. Asynchronous. Errors: RT_E_INVAL,
  * RT_E_STATE (a scene without batch_optics or grid), RT_E_CUDA, RT_E_OOM. */
 int rt_trace_batch(const rt_job *jobs, int njobs, uint64_t total_photons, uint64_t seed);
+
+/* As rt_trace_range, with a fraction `diffuse_fraction` in [0,1] of the
+ * photons starting diffuse (Sec. 2.3: the diffuse part of the top-of-domain
+ * flux enters as isotropic downwelling radiance, so those photons start with
+ * cosine-weighted downward directions and count as scattered). Photon p is
+ * diffuse when the fourth uniform of its birth block is below the fraction. */
+int rt_trace_ex(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux, double diffuse_fraction,
+                uint64_t photon_begin, uint64_t photon_count, uint64_t photons_total, uint64_t seed);
 
 /* Copy the accumulated fields out, normalised (Sec. 2.3 fluxes from mean
  * weights; absorption per cell volume). abs3d: nx*ny*nz doubles [W m^-3], the

@@ -62,7 +62,7 @@ def _load():
         lib.or_sample_mu.restype = i32
         lib.or_turn.argtypes = [P, u64, P, P, P]
         lib.or_trace.argtypes = ([i32, i32, i32, f64, f64, f64] + [P] * 6 +
-                                 [f64, f64, u64, u64, u64, u64, i32, i32, u64] + [P] * 9)
+                                 [f64, f64, u64, u64, u64, u64, i32, i32, u64, f64] + [P] * 9)
         lib.or_trace.restype = i32
         lib.or_direct_beam.argtypes = [i32, i32, i32, f64, f64, f64, P, P, f64, f64, i32, i32, P]
         lib.or_direct_beam.restype = i32
@@ -148,11 +148,14 @@ class OracleResult:
 
 def trace(scene, sza_deg: float, az_deg: float, toa_flux: float, photons: int, seed: int,
           id_begin: int = 0, photons_total: int | None = None, col_offset: int = 0,
-          pcld_mode: int = 0, nthreads: int = 0, max_steps: int = 10**9) -> OracleResult:
+          pcld_mode: int = 0, nthreads: int = 0, max_steps: int = 10**9,
+          diffuse_fraction: float = 0.0) -> OracleResult:
     """Analog FP64 Monte Carlo estimate (Sec. 2.3) for photon ids [id_begin, id_begin+photons).
 
     `photons_total` (default `photons`) sets the energy per photon, so that
-    disjoint id ranges traced separately add up to one run.
+    disjoint id ranges traced separately add up to one run. A share
+    `diffuse_fraction` of the photons starts diffuse (isotropic downwelling
+    radiance at the domain top, Sec. 2.3).
     """
     lib = _load()
     nx, ny, nz = scene.nx, scene.ny, scene.nz
@@ -167,6 +170,7 @@ def trace(scene, sza_deg: float, az_deg: float, toa_flux: float, photons: int, s
     st = lib.or_trace(nx, ny, nz, scene.dx, scene.dy, scene.dz, *[_ptr(a) for a in arrs],
                       float(sza_deg), float(az_deg), int(id_begin), int(id_begin + photons),
                       int(col_offset), int(seed), int(pcld_mode), int(nthreads), int(max_steps),
+                      float(diffuse_fraction),
                       _ptr(tl_dir), _ptr(tl_dif), _ptr(n_adir), _ptr(n_adif), _ptr(n_sdir),
                       _ptr(n_sdif), _ptr(n_sabs), _ptr(n_toa), _ptr(tot))
     if st != 0:

@@ -244,7 +244,7 @@ typedef struct {
 
 /* One analog photon history; returns 0 or OR_ESTEPS. */
 static int trace_photon(const scene_t *S, const double sun[3], uint64_t seed, uint64_t id,
-                        uint64_t col_offset, uint64_t max_steps, tally_t *T, uint64_t loc[8])
+                        uint64_t col_offset, double diffuse_frac, uint64_t max_steps, tally_t *T, uint64_t loc[8])
 {
     stream_t rs;
     stream_init(&rs, seed, id);
@@ -256,6 +256,15 @@ static int trace_photon(const scene_t *S, const double sun[3], uint64_t seed, ui
     p[1] = (j + stream_uniform(&rs)) * S->dy;
     p[2] = S->H;
     int direct = 1;
+    /* Sec. 2.3: a share of the top flux enters as isotropic downwelling
+     * radiance; its photons start diffuse with cosine-law downward directions */
+    if (diffuse_frac > 0.0 && stream_uniform(&rs) < diffuse_frac) {
+        double mu = sample_lambert(&rs);
+        double phi = 2.0 * M_PI * stream_uniform(&rs);
+        double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+        d[0] = st * cos(phi); d[1] = st * sin(phi); d[2] = -mu;
+        direct = 0;
+    }
     loc[0] += 1;
     uint64_t steps = 0;
     double tau = -log(stream_uniform(&rs));
@@ -343,7 +352,7 @@ int or_trace(int nx, int ny, int nz, double dx, double dy, double dz,
              const float *ssa_cld, const float *g_cld, const float *albedo,
              double sza_deg, double az_deg, uint64_t id_begin, uint64_t id_end,
              uint64_t col_offset, uint64_t seed, int pcld_mode, int nthreads,
-             uint64_t max_steps,
+             uint64_t max_steps, double diffuse_frac,
              double *tl_dir, double *tl_dif, uint64_t *n_abs_dir, uint64_t *n_abs_dif,
              uint64_t *n_sfc_dir, uint64_t *n_sfc_dif, uint64_t *n_sfc_abs, uint64_t *n_toa,
              uint64_t *totals)
@@ -351,7 +360,7 @@ int or_trace(int nx, int ny, int nz, double dx, double dy, double dz,
     scene_t S = {nx, ny, nz, dx, dy, dz, nx * dx, ny * dy, nz * dz,
                  k_gas, ssa_gas, k_cld, ssa_cld, g_cld, albedo, pcld_mode};
     if (scene_check(&S) != OR_OK || !(sza_deg >= 0.0 && sza_deg < 90.0)) return OR_EINVAL;
-    if (id_end < id_begin) return OR_EINVAL;
+    if (id_end < id_begin || !(diffuse_frac >= 0.0 && diffuse_frac <= 1.0)) return OR_EINVAL;
     tally_t T = {tl_dir, tl_dif, n_abs_dir, n_abs_dif, n_sfc_dir, n_sfc_dif, n_sfc_abs, n_toa, {0}};
     double sun[3];
     sun_direction(sza_deg, az_deg, sun);
@@ -365,7 +374,7 @@ int or_trace(int nx, int ny, int nz, double dx, double dy, double dz,
         int st = OR_OK;
 #pragma omp for schedule(dynamic, 1024)
         for (int64_t p = (int64_t)id_begin; p < (int64_t)id_end; ++p) {
-            if (trace_photon(&S, sun, seed, (uint64_t)p, col_offset, max_steps, &T, loc) != OR_OK)
+            if (trace_photon(&S, sun, seed, (uint64_t)p, col_offset, diffuse_frac, max_steps, &T, loc) != OR_OK)
                 st = OR_ESTEPS;
         }
 #pragma omp critical

@@ -293,12 +293,13 @@ void fill_launch(rt_handle h, rt::TraceArgs<T> &A)
 }
 
 template <typename T>
-int launch_trace(rt_handle h, T *base, double sza, double az, double toa_flux, uint64_t begin,
+int launch_trace(rt_handle h, T *base, double sza, double az, double toa_flux, double diffuse, uint64_t begin,
                  uint64_t count, uint64_t total, uint64_t seed)
 {
     rt::TraceArgs<T> A{};
     A.scene = scene_desc<T>(h, base, false);
     A.job = job_desc(h, sza, az, toa_flux, 1.0, total, seed, 0);
+    A.job.diffuse = (float)diffuse;
     A.job.start = 0;
     A.job.id_begin = begin;
     A.count = count;
@@ -562,6 +563,38 @@ int rt_set_optics(rt_handle h, const float *k_gas, const float *ssa_gas, const f
     return RT_OK;
 }
 
+int rt_set_optics_total(rt_handle h, const float *k_ext, const float *k_ext_cld, const float *ssa,
+                        const float *g_cld, int mem)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    if (!k_ext || !k_ext_cld || !ssa || !g_cld) return fail(RT_E_INVAL, "rt_set_optics_total: null field pointer");
+    if (mem != RT_HOST && mem != RT_DEVICE) return fail(RT_E_INVAL, "rt_set_optics_total: bad mem flag");
+    const size_t n = h->ncell;
+    const float *src[4] = {k_ext, k_ext_cld, ssa, g_cld};
+    if (mem == RT_HOST) {
+        if (!h->stage && (rc = dev_alloc(&h->stage, 5 * n))) return rc;
+        for (int q = 0; q < 4; ++q)
+            if ((rc = copy_in(h, h->stage + q * n, src[q], n, RT_HOST))) return rc;
+        for (int q = 0; q < 4; ++q) src[q] = h->stage + q * n;
+    }
+    RT_CUDA(cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
+    rt::derive_optics_total<<<grid_for(n), 256, 0, h->stream>>>(src[0], src[1], src[2], src[3], h->rec, n, h->bad);
+    RT_CUDA(cudaGetLastError());
+    h->split_ok = false;
+    h->accel2_ok = false;
+    h->accel_ok = false;
+    int bad = 0;
+    if ((rc = read_bad(h, &bad))) return rc;
+    if (bad) {
+        h->optics_ok = false;
+        return fail(RT_E_INVAL, "rt_set_optics_total: invalid optical property (NaN, negative extinction, cloud "
+                                "extinction above total, albedo outside [0,1] or |g| >= 1)");
+    }
+    h->optics_ok = true;
+    return RT_OK;
+}
+
 int rt_set_surface(rt_handle h, const float *albedo, int mem)
 {
     int rc = check(h);
@@ -626,8 +659,8 @@ int rt_build_accel(rt_handle h, int cx, int cy, int cz)
     return RT_OK;
 }
 
-int rt_trace_range(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux, uint64_t photon_begin,
-                   uint64_t photon_count, uint64_t photons_total, uint64_t seed)
+int rt_trace_ex(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux, double diffuse_fraction,
+                uint64_t photon_begin, uint64_t photon_count, uint64_t photons_total, uint64_t seed)
 {
     int rc = check(h);
     if (rc) return rc;
@@ -636,16 +669,24 @@ int rt_trace_range(rt_handle h, double sza_deg, double azimuth_deg, double toa_f
     if (!(sza_deg >= 0.0 && sza_deg < 90.0)) return fail(RT_E_INVAL, "rt_trace: sza must be in [0, 90)");
     if (!std::isfinite(azimuth_deg)) return fail(RT_E_INVAL, "rt_trace: azimuth must be finite");
     if (!(toa_flux >= 0.0) || !std::isfinite(toa_flux)) return fail(RT_E_INVAL, "rt_trace: toa_flux must be >= 0");
+    if (!(diffuse_fraction >= 0.0 && diffuse_fraction <= 1.0))
+        return fail(RT_E_INVAL, "rt_trace: diffuse_fraction must be in [0, 1]");
     if (photons_total == 0) return fail(RT_E_INVAL, "rt_trace: photons_total must be positive");
     if (photon_begin > photons_total || photon_count > photons_total - photon_begin)
         return fail(RT_E_INVAL, "rt_trace: photon range exceeds photons_total");
     if (photon_count == 0) return RT_OK;
     if ((rc = ensure_tallies(h))) return rc;
     if (h->tally_prec == RT_TALLY_FP64)
-        return launch_trace<double>(h, h->t64, sza_deg, azimuth_deg, toa_flux, photon_begin, photon_count,
+        return launch_trace<double>(h, h->t64, sza_deg, azimuth_deg, toa_flux, diffuse_fraction, photon_begin, photon_count,
                                     photons_total, seed);
-    return launch_trace<float>(h, h->t32, sza_deg, azimuth_deg, toa_flux, photon_begin, photon_count,
+    return launch_trace<float>(h, h->t32, sza_deg, azimuth_deg, toa_flux, diffuse_fraction, photon_begin, photon_count,
                                photons_total, seed);
+}
+
+int rt_trace_range(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux, uint64_t photon_begin,
+                   uint64_t photon_count, uint64_t photons_total, uint64_t seed)
+{
+    return rt_trace_ex(h, sza_deg, azimuth_deg, toa_flux, 0.0, photon_begin, photon_count, photons_total, seed);
 }
 
 int rt_trace(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux, uint64_t photons, uint64_t seed)
@@ -678,7 +719,8 @@ int rt_trace_batch(const rt_job *jobs, int njobs, uint64_t total_photons, uint64
             return fail(RT_E_INVAL, "rt_trace_batch: all scenes must use the same tally precision");
         if (!(jb.sza_deg >= 0.0 && jb.sza_deg < 90.0) || !std::isfinite(jb.azimuth_deg) ||
             !(jb.toa_flux >= 0.0) || !std::isfinite(jb.toa_flux) || !(jb.gas_scale >= 0.0) ||
-            !std::isfinite(jb.gas_scale) || jb.gas_scale > 1e30)
+            !std::isfinite(jb.gas_scale) || jb.gas_scale > 1e30 ||
+            !(jb.diffuse_fraction >= 0.0 && jb.diffuse_fraction <= 1.0))
             return fail(RT_E_INVAL, "rt_trace_batch: job %d: bad sza, azimuth, toa_flux or gas_scale", j);
         int q = -1;
         for (size_t k = 0; k < scenes.size(); ++k)
@@ -725,6 +767,7 @@ int rt_trace_batch(const rt_job *jobs, int njobs, uint64_t total_photons, uint64
             J.start = start;
             J.id_begin = 0;
             J.scene = sidx[j];
+            J.diffuse = (float)jobs[j].diffuse_fraction;
             jd.push_back(J);
             start += n[j];
         }

@@ -64,7 +64,8 @@ struct JobDev {
     float sx, sy, sz;              // travel direction of the direct beam
     float gas_scale;               // multiplies the gas extinction (batched launches)
     uint32_t key0, key1;           // Philox key
-    int scene, pad_;
+    int scene;
+    float diffuse;                 // fraction of photons that start diffuse (isotropic downwelling)
     double energy;                 // W per unit photon weight
     double scale2, scale3;         // energy / (dx dy), energy / (dx dy dz)
 };
@@ -111,6 +112,26 @@ __global__ void derive_optics(const float *__restrict__ kg, const float *__restr
         const float kabs = fmaf(a, 1.0f - b, c * (1.0f - d));
         float zc = ksc;
         if (pcld_mode == 1) zc = (a + c > 0.0f) ? ksca * (c / (a + c)) : 0.0f;
+        rec[i] = make_float4(kabs, ksca, zc, g);
+    }
+}
+
+// The paper's own inputs (Sec. 2.3): total extinction, cloud extinction, one
+// single-scattering albedo and g. The record follows: k_sca = w k_ext,
+// k_abs = k_ext - k_sca, and the cloud share of scattering is k_ext,cloud/k_ext.
+__global__ void derive_optics_total(const float *__restrict__ ke, const float *__restrict__ kc,
+                                    const float *__restrict__ w, const float *__restrict__ gc,
+                                    float4 *__restrict__ rec, size_t n, int *bad)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float e = ke[i], c = kc[i], a = w[i], g = gc[i];
+        const bool ok = (e >= 0.0f) && (e <= 3.0e38f) && (c >= 0.0f) && (c <= e) && (a >= 0.0f) && (a <= 1.0f) &&
+                        (fabsf(g) < 1.0f);
+        if (!ok) atomicOr(bad, 1);
+        const float ksca = e * a;
+        const float kabs = e * (1.0f - a);
+        const float zc = e > 0.0f ? ksca * (c / e) : 0.0f;
         rec[i] = make_float4(kabs, ksca, zc, g);
     }
 }
@@ -393,9 +414,18 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
                 oy = ((float)cj + u01(r.y)) * RT_SC(dy);
                 oz = RT_SC(H);
                 ux = RT_JB(sx); uy = RT_JB(sy); uz = RT_JB(sz);
+                direct = true;
+                if (RT_JB(diffuse) > 0.f && u01(r.w) < RT_JB(diffuse)) {
+                    // diffuse share of the top boundary: isotropic downwelling
+                    // radiance, i.e. cosine-weighted downward directions (Sec. 2.3)
+                    const uint4 d = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), 0u, 1u),
+                                                  RT_JB(key0), RT_JB(key1));
+                    lambert_up(ux, uy, uz, u01(d.x), u01(d.y));
+                    uz = -uz;
+                    direct = false;
+                }
                 tau = -__logf(u01(r.z));
                 w = 1.f;
-                direct = true;
                 alive = true;
                 ready = kNone;
                 I = ci / RT_SC(cx); J = cj / RT_SC(cy); K = RT_SC(NZ) - 1;

@@ -39,7 +39,8 @@ class rt_options(ctypes.Structure):
 
 class rt_job(ctypes.Structure):
     _fields_ = [("scene", ctypes.c_void_p), ("sza_deg", ctypes.c_double), ("azimuth_deg", ctypes.c_double),
-                ("toa_flux", ctypes.c_double), ("gas_scale", ctypes.c_double), ("photons", ctypes.c_uint64)]
+                ("toa_flux", ctypes.c_double), ("gas_scale", ctypes.c_double), ("photons", ctypes.c_uint64),
+                ("diffuse_fraction", ctypes.c_double)]
 
 
 class rt_stats_t(ctypes.Structure):
@@ -75,6 +76,8 @@ def library() -> ctypes.CDLL:
             "rt_build_accel": ([H, i32, i32, i32], i32),
             "rt_trace": ([H, f64, f64, f64, u64, u64], i32),
             "rt_trace_range": ([H, f64, f64, f64, u64, u64, u64, u64], i32),
+            "rt_trace_ex": ([H, f64, f64, f64, f64, u64, u64, u64, u64], i32),
+            "rt_set_optics_total": ([H, P, P, P, P, i32], i32),
             "rt_fields": ([H, P, P, P, P, i32], i32),
             "rt_fields_split": ([H, P, P, P, i32], i32),
             "rt_heating_rate": ([H, P, i32, i32], i32),
@@ -189,6 +192,20 @@ def rt_set_optics(h, ncell, k_gas, ssa_gas, k_cld, ssa_cld, g_cld):
     return _check(library().rt_set_optics(h, *[p for p, _ in bufs], mem))
 
 
+def rt_set_optics_total(h, ncell, k_ext, k_ext_cld, ssa, g_cld):
+    bufs = [_buf(a, ncell, np.float32, n) for a, n in
+            zip((k_ext, k_ext_cld, ssa, g_cld), ("k_ext", "k_ext_cld", "ssa", "g_cld"))]
+    mem = _same_mem(*bufs)
+    return _check(library().rt_set_optics_total(h, *[p for p, _ in bufs], mem))
+
+
+def rt_trace_ex(h, sza_deg, azimuth_deg, toa_flux, diffuse_fraction, photon_begin, photon_count, photons_total,
+                seed):
+    return _check(library().rt_trace_ex(h, float(sza_deg), float(azimuth_deg), float(toa_flux),
+                                        float(diffuse_fraction), int(photon_begin), int(photon_count),
+                                        int(photons_total), int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+
 def rt_set_surface(h, ncol, albedo):
     p, mem = _buf(albedo, ncol, np.float32, "albedo")
     return _check(library().rt_set_surface(h, p, mem))
@@ -221,6 +238,7 @@ def rt_trace_batch(jobs, total_photons=0, seed=1):
         a.toa_flux = float(j.get("toa_flux", 0.0))
         a.gas_scale = float(j.get("gas_scale", 1.0))
         a.photons = int(j.get("photons", 0))
+        a.diffuse_fraction = float(j.get("diffuse_fraction", 0.0))
     return _check(library().rt_trace_batch(arr, len(jobs), int(total_photons), int(seed) & 0xFFFFFFFFFFFFFFFF))
 
 
@@ -369,8 +387,11 @@ class Tracer:
     def build_accel(self, cx=0, cy=0, cz=0):
         rt_build_accel(self.h, cx, cy, cz)
 
-    def trace(self, sza_deg, azimuth_deg, toa_flux, photons, seed):
-        rt_trace(self.h, sza_deg, azimuth_deg, toa_flux, photons, seed)
+    def trace(self, sza_deg, azimuth_deg, toa_flux, photons, seed, diffuse_fraction=0.0):
+        if diffuse_fraction:
+            rt_trace_ex(self.h, sza_deg, azimuth_deg, toa_flux, diffuse_fraction, 0, photons, photons, seed)
+        else:
+            rt_trace(self.h, sza_deg, azimuth_deg, toa_flux, photons, seed)
 
     def trace_range(self, sza_deg, azimuth_deg, toa_flux, begin, count, total, seed):
         rt_trace_range(self.h, sza_deg, azimuth_deg, toa_flux, begin, count, total, seed)

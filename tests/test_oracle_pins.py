@@ -308,3 +308,31 @@ def test_track_length_matches_analog_counts(small_scene):
     m = np.array(means)
     d = m[:, 0] - m[:, 1]
     assert abs(d.mean()) < 4 * d.std(ddof=1) / np.sqrt(len(d)) + 1e-12
+
+
+# --- diffuse share of the top boundary (Sec. 2.3) --------------------------------------
+
+def test_mc_diffuse_fraction_in_an_empty_atmosphere():
+    """No atmosphere, black surface: the surface receives (1-f) F mu0 direct and
+    f F mu0 diffuse, exactly in expectation (binomial in the photon counts)."""
+    sc = scenes.layered_scene(4, 4, 3, 50.0, 50.0, 100.0, k_gas=0.0, ssa_gas=0.0)
+    N, f = 400_000, 0.3
+    r = oracle.trace(sc, 40.0, 0.0, 1000.0, N, seed=3, nthreads=NT, diffuse_fraction=f)
+    nd = r.counts["sfc_dif"].sum()
+    assert abs(nd - f * N) < 4 * np.sqrt(N * f * (1 - f))
+    assert r.counts["sfc_dir"].sum() + nd == N
+
+
+def test_mc_diffuse_fraction_through_an_absorbing_slab():
+    """Isotropic downwelling radiance crosses a purely absorbing slab of optical
+    depth tau with flux transmittance 2 E3(tau)."""
+    k = np.array([1e-3, 3e-3], dtype=np.float32)
+    dz = 150.0
+    sc = scenes.layered_scene(3, 3, 2, 100.0, 100.0, dz, k_gas=k, ssa_gas=0.0)
+    N = 1_000_000
+    r = oracle.trace(sc, 20.0, 0.0, 1.0, N, seed=9, nthreads=NT, diffuse_fraction=1.0)
+    tau = float(np.sum(k.astype(np.float64)) * dz)
+    p = 2 * refs.e3(tau)
+    n = r.counts["sfc_dif"].sum()
+    assert r.counts["sfc_dir"].sum() == 0
+    assert abs(n - p * N) < 4 * np.sqrt(N * p * (1 - p))
