@@ -25,7 +25,7 @@
 
 namespace {
 
-constexpr int kBM = 128, kBN = 32, kChunk = 16, kStageChunks = 2;
+constexpr int kBM = 128, kChunk = 16, kStageChunks = 2;
 constexpr int kRow = 24;   // bf16 per staged row: 16 used + 8 pad (48 B: conflict-free fragment reads)
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
@@ -41,6 +41,21 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, bool vali
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// ldmatrix: lane l supplies the address of row (l % 8) of 8x8 matrix (l / 8);
+// register j receives this lane's part of matrix j (transposed with .trans).
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_trans(unsigned (&r)[4], const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2])
 {
@@ -60,26 +75,32 @@ __device__ __forceinline__ int tap_offset(int t, int taps, int &dz, int &dy, int
 
 // ---------------------------------------------------------------------------
 // Convolution forward (also the input gradient with tap-reversed weights).
-// grid (ceil(M/128), ceil(Cout/32)), 128 threads (4 warps x 32 voxels).
+// Block tile 128 voxels x BN output channels; warps 4 (voxels) x BN/32
+// (channels), each 32 x 32. Fragments come from shared memory by ldmatrix.
+// grid (ceil(M/128), ceil(Cout/BN)), 4 * BN threads.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) conv_fwd_kernel(const __nv_bfloat16 *__restrict__ in,
-                                                       const __nv_bfloat16 *__restrict__ wt,
-                                                       const float *__restrict__ bias, __nv_bfloat16 *out_bf,
-                                                       float *out_f, int N, int D, int H, int W, int Cin, int Cout,
-                                                       int taps, int relu)
+template <int BN>
+__global__ void __launch_bounds__(4 * BN) conv_fwd_kernel(const __nv_bfloat16 *__restrict__ in,
+                                                          const __nv_bfloat16 *__restrict__ wt,
+                                                          const float *__restrict__ bias, __nv_bfloat16 *out_bf,
+                                                          float *out_f, int N, int D, int H, int W, int Cin,
+                                                          int Cout, int taps, int relu)
 {
+    constexpr int NT = 4 * BN;
     __shared__ __align__(16) __nv_bfloat16 sA[2][kStageChunks][kBM][kRow];
-    __shared__ __align__(16) __nv_bfloat16 sB[2][kStageChunks][kBN][kRow];
+    __shared__ __align__(16) __nv_bfloat16 sB[2][kStageChunks][BN][kRow];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, q = lane & 3;
+    const int wm = warp & 3, wn = warp >> 2;
     const long long M = (long long)N * D * H * W;
     const long long m0 = (long long)blockIdx.x * kBM;
-    const int co0 = blockIdx.y * kBN;
+    const int co0 = blockIdx.y * BN;
     const int cpt = Cin / kChunk;           // chunks per tap
     const int nchunks = taps * cpt;
 
-    // this thread stages voxel row `tid` of the A tile
-    const long long mv = m0 + tid;
+    // this thread stages voxel row `arow` of the A tile (halves ahalf0.. of it)
+    const int arow = tid % kBM;
+    const long long mv = m0 + arow;
     const bool mvalid = mv < M;
     int vz = 0, vy = 0, vx = 0;
     if (mvalid) {
@@ -99,9 +120,9 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const __nv_bfloat16 *__re
             const bool ok = live && mvalid && z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W;
             const long long nb = ok ? mv + ((long long)dz * H + dy) * W + dx : 0;
             const __nv_bfloat16 *src = in + nb * Cin + ci0;
-            cp_async16(&sA[buf][c][tid][0], src, ok);
-            cp_async16(&sA[buf][c][tid][8], src + 8, ok);
-            if (tid < 2 * kBN) {
+            for (int h = tid / kBM; h < 2; h += NT / kBM)
+                cp_async16(&sA[buf][c][arow][h * 8], src + h * 8, ok);
+            if (tid < 2 * BN) {
                 const int row = tid >> 1, half = tid & 1;
                 const bool okb = live && (co0 + row) < Cout;
                 const __nv_bfloat16 *wsrc = wt + ((long long)(t * Cout + (okb ? co0 + row : 0)) * Cin + ci0 + half * 8);
@@ -119,6 +140,10 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const __nv_bfloat16 *__re
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[a][b][e] = 0.f;
 
+    // ldmatrix row/column of this lane: A (16x16) and B (two 8-wide n tiles)
+    const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8, lcol = (lane >> 4) * 8;
+    const int brow = (lane & 7) + (lane >> 4) * 8, bcol = ((lane >> 3) & 1) * 8;
+
     const int nstages = (nchunks + kStageChunks - 1) / kStageChunks;
     stage(0, 0);
     for (int s = 0; s < nstages; ++s) {
@@ -130,27 +155,22 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const __nv_bfloat16 *__re
             cp_async_wait<0>();
         }
         __syncthreads();
+#pragma unroll
         for (int c = 0; c < kStageChunks; ++c) {
-            if (s * kStageChunks + c >= nchunks) break;
-            unsigned af[2][4], bf[4][2];
+            if (s * kStageChunks + c < nchunks) {
+                unsigned af[2][4], bf[2][4];
 #pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-                const int r = warp * 32 + mi * 16 + g;
-                af[mi][0] = *reinterpret_cast<const unsigned *>(&sA[buf][c][r][q * 2]);
-                af[mi][1] = *reinterpret_cast<const unsigned *>(&sA[buf][c][r + 8][q * 2]);
-                af[mi][2] = *reinterpret_cast<const unsigned *>(&sA[buf][c][r][q * 2 + 8]);
-                af[mi][3] = *reinterpret_cast<const unsigned *>(&sA[buf][c][r + 8][q * 2 + 8]);
+                for (int mi = 0; mi < 2; ++mi) ldsm_x4(af[mi], &sA[buf][c][wm * 32 + mi * 16 + lrow][lcol]);
+#pragma unroll
+                for (int jp = 0; jp < 2; ++jp) ldsm_x4(bf[jp], &sB[buf][c][wn * 32 + jp * 16 + brow][bcol]);
+#pragma unroll
+                for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                    for (int nj = 0; nj < 4; ++nj) {
+                        const unsigned b2[2] = {bf[nj >> 1][(nj & 1) * 2], bf[nj >> 1][(nj & 1) * 2 + 1]};
+                        mma_bf16(acc[mi][nj], af[mi], b2);
+                    }
             }
-#pragma unroll
-            for (int nj = 0; nj < 4; ++nj) {
-                const int n = nj * 8 + g;
-                bf[nj][0] = *reinterpret_cast<const unsigned *>(&sB[buf][c][n][q * 2]);
-                bf[nj][1] = *reinterpret_cast<const unsigned *>(&sB[buf][c][n][q * 2 + 8]);
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int nj = 0; nj < 4; ++nj) mma_bf16(acc[mi][nj], af[mi], bf[nj]);
         }
         __syncthreads();
     }
@@ -160,11 +180,11 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const __nv_bfloat16 *__re
     for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
-            const long long m = m0 + warp * 32 + mi * 16 + g + half * 8;
+            const long long m = m0 + wm * 32 + mi * 16 + g + half * 8;
             if (m >= M) continue;
 #pragma unroll
             for (int nj = 0; nj < 4; ++nj) {
-                const int co = co0 + nj * 8 + q * 2;
+                const int co = co0 + wn * 32 + nj * 8 + q * 2;
                 if (co >= Cout) continue;
                 float v0 = acc[mi][nj][half * 2], v1 = acc[mi][nj][half * 2 + 1];
                 if (bias) { v0 += bias[co]; v1 += (co + 1 < Cout) ? bias[co + 1] : 0.f; }
@@ -236,24 +256,17 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(const __nv_bfloat16 *__
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kWV; kk += 16) {
-            // A[m=i][k=p] = sI[p][i]; B[k=p][n=o] = sG[p][o]
-            unsigned a[4], b[2][2];
-            auto pack = [](__nv_bfloat16 lo, __nv_bfloat16 hi) -> unsigned {
-                return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
-            };
-            const int k0 = kk + q * 2;
-            a[0] = pack(sI[k0][wi + g], sI[k0 + 1][wi + g]);
-            a[1] = pack(sI[k0][wi + g + 8], sI[k0 + 1][wi + g + 8]);
-            a[2] = pack(sI[k0 + 8][wi + g], sI[k0 + 9][wi + g]);
-            a[3] = pack(sI[k0 + 8][wi + g + 8], sI[k0 + 9][wi + g + 8]);
-#pragma unroll
-            for (int nj = 0; nj < 2; ++nj) {
-                const int n = wo + nj * 8 + g;
-                b[nj][0] = pack(sG[k0][n], sG[k0 + 1][n]);
-                b[nj][1] = pack(sG[k0 + 8][n], sG[k0 + 9][n]);
-            }
-            mma_bf16(acc[0], a, b[0]);
-            mma_bf16(acc[1], a, b[1]);
+            // A[m=i][k=p] = sI[p][i] and B[k=p][n=o] = sG[p][o]: both are the
+            // transposes of the staged (voxel-major) tiles, read with ldmatrix.trans.
+            // Matrix j of the A load: voxels kk + 8 (j >> 1) .., channels wi + 8 (j & 1) ..
+            // Matrix j of the B load: voxels kk + 8 (j & 1) .., channels wo + 8 (j >> 1) ..
+            unsigned a[4], bb[4];
+            const int mj = lane >> 3, mr = lane & 7;
+            ldsm_x4_trans(a, &sI[kk + (mj >> 1) * 8 + mr][wi + (mj & 1) * 8]);
+            ldsm_x4_trans(bb, &sG[kk + (mj & 1) * 8 + mr][wo + (mj >> 1) * 8]);
+            const unsigned b0[2] = {bb[0], bb[1]}, b1[2] = {bb[2], bb[3]};
+            mma_bf16(acc[0], a, b0);
+            mma_bf16(acc[1], a, b1);
         }
         if (gb && t == 0 && i0 == 0 && tid < 32)
             for (int v = 0; v < kWV; ++v) bacc += __bfloat162float(sG[v][tid]);
@@ -530,10 +543,17 @@ int nn_conv3d_fwd(const void *in, const void *wt, const float *bias, void *out_b
     if (out_bf16 && Cout % 2 != 0) return inval("nn_conv3d_fwd: BF16 output needs an even Cout");
     if (ksize != 1 && ksize != 3) return inval("nn_conv3d_fwd: ksize must be 1 or 3");
     const long long M = (long long)N * D * H * W;
-    dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((Cout + kBN - 1) / kBN));
-    conv_fwd_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(
-        (const __nv_bfloat16 *)in, (const __nv_bfloat16 *)wt, bias, (__nv_bfloat16 *)out_bf16, out_f32, N, D, H, W,
-        Cin, Cout, ksize == 3 ? 27 : 1, relu);
+    if (Cout >= 64) {
+        dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((Cout + 63) / 64));
+        conv_fwd_kernel<64><<<grid, 256, 0, (cudaStream_t)stream>>>(
+            (const __nv_bfloat16 *)in, (const __nv_bfloat16 *)wt, bias, (__nv_bfloat16 *)out_bf16, out_f32, N, D, H,
+            W, Cin, Cout, ksize == 3 ? 27 : 1, relu);
+    } else {
+        dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((Cout + 31) / 32));
+        conv_fwd_kernel<32><<<grid, 128, 0, (cudaStream_t)stream>>>(
+            (const __nv_bfloat16 *)in, (const __nv_bfloat16 *)wt, bias, (__nv_bfloat16 *)out_bf16, out_f32, N, D, H,
+            W, Cin, Cout, ksize == 3 ? 27 : 1, relu);
+    }
     return check_launch("nn_conv3d_fwd");
 }
 
