@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-ppc", type=int, default=16)
     p.add_argument("--no-denoise", action="store_true", help="skip the denoised-vs-plain time-to-RMSE leg")
+    p.add_argument("--no-coupled", action="store_true", help="skip the graph-replay coupled-step leg")
+    p.add_argument("--no-birth", action="store_true", help="skip the Sobol-vs-Philox start position leg")
     p.add_argument("--denoise-train", type=int, default=64, help="training scenes of the denoiser leg")
     p.add_argument("--no-autotune", action="store_true",
                    help="use the default launch parameters and the --coarse grid")
@@ -228,6 +230,82 @@ def denoise_leg(args):
             "network": {"params": net.n_params(), "forward_gflop": net.flops(shape) / 1e9}}
 
 
+# ---- coupled-model step: graph replay vs the ordinary calls ------------------------------
+
+def coupled_step_leg(t, d_in, d_alb, d_out, photons, eager_ms, eager_events, steps):
+    """Time the same step recorded as one CUDA graph (rt_step) with inputs
+    bound in place: no host synchronisation inside the step."""
+    import torch
+    from paper_2208_05247_b300 import rt
+    stream = torch.cuda.current_stream()
+    step = rt.rt_step_create(t.h, t.ncell, t.ncol, d_in, photons, albedo=d_alb, **d_out)
+    try:
+        for _ in range(3):
+            rt.rt_step_launch(step, SZA, AZ, F0, 0.0, SEED)
+        rt.rt_synchronize(t.h)
+        assert t.stats()["events"] == eager_events, "graph replay traced different histories"
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            rt.rt_step_launch(step, SZA, AZ, F0, 0.0, SEED)
+        e1.record(stream)
+        rt.rt_synchronize(t.h)
+        ms = e0.elapsed_time(e1) / steps
+        # the launch overhead alone: a step of one photon per column
+    finally:
+        rt.rt_step_destroy(step)
+    return {"graph_ms_per_step": ms, "eager_ms_per_step": eager_ms, "steps": steps,
+            "host_syncs_per_step": {"graph": 0, "eager": 2},
+            "note": "same kernels and arguments; the graph replays optics derivation, majorant, reset, "
+                    "transport and outputs from device buffers updated in place (Sec. 2.2 coupling)"}
+
+
+# ---- scrambled Sobol vs Philox start positions: error at equal photons ---------------------
+
+def birth_leg(scene, coarse, tuned):
+    """RMS error of surface GHI, direct irradiance and heating rate against a
+    2048-photon/column reference, for uniform random (Philox) and scrambled
+    Sobol start positions (Sec. 2.3) at 4, 16 and 64 photons/column, with the
+    transport time of each; the speed-up is the Philox time needed to reach the
+    Sobol error (RMSE ~ a / sqrt(ppc) and time ~ t0 + t1 ppc fitted on the
+    Philox runs)."""
+    import torch
+    from paper_2208_05247_b300 import rt
+    stream = torch.cuda.current_stream()
+    opts = {k: v for k, v in (tuned or {}).items() if k != "coarse"}
+
+    def run(birth, ppc, seed):
+        with rt.Tracer.from_scene(scene, *coarse, stream=stream, birth=birth, **opts) as t:
+            t.reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t.trace(SZA, AZ, F0, ppc * scene.ncol, seed)
+            e1.record(stream)
+            f = t.fields()
+            hr = t.heating_rate()
+            return {"ghi": f["sfc_dir"] + f["sfc_dif"], "dir": f["sfc_dir"], "hr": hr}, e0.elapsed_time(e1)
+
+    truth, _ = run(rt.RT_BIRTH_SOBOL, 2048, SEED + 500)
+    res = {}
+    for name, birth in (("philox", rt.RT_BIRTH_PHILOX), ("sobol", rt.RT_BIRTH_SOBOL)):
+        res[name] = {}
+        for q, ppc in enumerate((4, 16, 64)):
+            run(birth, ppc, SEED + 600)                      # warm
+            f, ms = run(birth, ppc, SEED + 601 + q)
+            res[name][ppc] = {k: float(np.sqrt(np.mean((f[k] - truth[k]) ** 2))) for k in f}
+            res[name][ppc]["ms"] = ms
+    ppcs = np.array([4, 16, 64], float)
+    t_fit = np.polyfit(ppcs, [res["philox"][p]["ms"] for p in (4, 16, 64)], 1)
+    speed = {}
+    for k in ("ghi", "dir", "hr"):
+        a = np.mean([res["philox"][p][k] * np.sqrt(p) for p in (4, 16, 64)])
+        need = (a / res["sobol"][16][k]) ** 2
+        speed[k] = float(np.polyval(t_fit, need) / res["sobol"][16]["ms"])
+    return {"workload": "benchmark scene, sza 30, reference 2048 photons/column (Sobol, independent scramble)",
+            "rmse": res, "speedup_at_16ppc": speed}
+
+
 # ---- our CUDA path --------------------------------------------------------------------
 
 def run_ours(args):
@@ -356,6 +434,12 @@ def run_ours(args):
         e2e = {"value": events_all * k2 / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * dt / k2}
 
+    cstep = births = None
+    if world == 1 and not args.no_coupled:
+        cstep = coupled_step_leg(t, d_in, d_alb, d_out, N, ms_max / args.steps, events, max(3, args.steps // 2))
+    if world == 1 and not args.no_birth:
+        births = birth_leg(scene, coarse, tuned)
+
     if rank != 0:
         return
     cpu = None
@@ -376,7 +460,8 @@ def run_ours(args):
             "real_scatters_per_s": st["scatters"] * world * args.steps / (ms_max / 1e3),
             "events_per_step": events_all, "real_scatter_fraction": st["scatters"] / max(1, events),
             "trace_kernel_ms": 1e3 * tk, "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": KERNELS_PER_STEP * args.steps, "time_to_rmse": dn}
+            "gpu_launches": KERNELS_PER_STEP * args.steps, "time_to_rmse": dn, "coupled_step": cstep,
+            "sobol_birth": births}
     print(json.dumps(line), flush=True)
     t.close()
     if dist is not None:

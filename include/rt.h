@@ -40,9 +40,10 @@
  * Errors
  *   - Every int-returning call returns RT_OK (0) or a negative RT_E_* code and
  *     records a message for rt_last_error() (thread-local).
- *   - Conditions found on the device (an event budget exhausted) are recorded
- *     in the handle's status and returned by rt_synchronize, rt_stats and
- *     rt_fields; the kernels never trap and every loop in them is bounded.
+ *   - Conditions found on the device (an event budget exhausted; invalid inputs
+ *     of an rt_step launch) are recorded in the handle's status and returned by
+ *     rt_synchronize, rt_stats and rt_fields; the kernels never trap and every
+ *     loop in them is bounded.
  */
 #ifndef RT_B300_H
 #define RT_B300_H
@@ -75,6 +76,15 @@ enum { RT_PCLD_SCATTERING = 0, RT_PCLD_EXTINCTION = 1 };
 /* Tally precision: FP64 global accumulators (default) or FP32 (precision study). */
 enum { RT_TALLY_FP64 = 0, RT_TALLY_FP32 = 1 };
 
+/* Start positions at the domain top. Sec. 2.3 starts photons at the points of a
+ * scrambled Sobol sequence. RT_BIRTH_PHILOX draws each photon's position in its
+ * column from its own Philox stream. RT_BIRTH_SOBOL gives photon p, the k-th
+ * photon (k = p div nx*ny) of column c = p mod nx*ny, the k-th point of the
+ * two-dimensional Sobol sequence, XORed per axis with a 32-bit word drawn for
+ * (column, seed) from Philox counter (c, 0, 0, 2); the photons of a column then
+ * stratify its area, and each start point is still uniform. */
+enum { RT_BIRTH_PHILOX = 0, RT_BIRTH_SOBOL = 1 };
+
 typedef struct {
     int block_size;              /* threads per block of the transport kernel; 0 = 256 */
     int blocks_per_sm;           /* resident blocks per SM; 0 = as many as fit */
@@ -88,6 +98,7 @@ typedef struct {
     int batch_optics;            /* 1: rt_set_optics also keeps gas and cloud apart and
                                     rt_build_accel builds the factored majorant, as
                                     rt_trace_batch needs (+20 B per cell); 0 (default): not */
+    int birth;                   /* RT_BIRTH_*; default RT_BIRTH_PHILOX */
 } rt_options;
 
 typedef struct {
@@ -106,7 +117,8 @@ typedef struct {
     double energy_created;       /* W added by roulette survivors (w -> 1) */
     double energy_destroyed;     /* W removed by roulette kills */
     double energy_capped;        /* W carried by photons stopped by the step cap */
-    int status;                  /* first device-side error (RT_OK or RT_E_BUDGET) */
+    int status;                  /* device-side error: RT_OK, RT_E_BUDGET, or RT_E_INVAL (an
+                                    rt_step launch found invalid inputs) */
 } rt_stats_t;
 
 /* Create a scene of nx*ny*nz cells of size dx*dy*dz metres on the current CUDA
@@ -234,7 +246,8 @@ int rt_reset_tallies(rt_handle h);
 /* Counters and energy ledger since the last reset. Synchronises. */
 int rt_stats(rt_handle h, rt_stats_t *out);
 
-/* Wait for the handle's stream; returns the device status (RT_OK or RT_E_BUDGET). */
+/* Wait for the handle's stream; returns the device status (RT_OK, RT_E_BUDGET,
+ * or RT_E_INVAL after an rt_step launch with invalid inputs). */
 int rt_synchronize(rt_handle h);
 
 /* Message of the last failed call on this thread ("" if none). */
@@ -243,6 +256,67 @@ const char *rt_last_error(void);
 /* RT_E_* code of the last failed call on this thread (RT_OK if none); the only
  * way to learn why rt_create returned NULL. */
 int rt_last_error_code(void);
+
+/* ---- coupled-model step: one graph replay per radiation call ---- */
+
+/* In the paper's coupled runs the tracer is called every 60 s of model time with
+ * the optics of the current model state (Sec. 2.2), and two experiments replace
+ * the surface fluxes or the heating rates by their horizontal means
+ * ("-hom" and "-hom-hr" runs, Sec. 2.4). An rt_step binds device input and
+ * output buffers once and records the whole radiation call -- validation and
+ * derivation of the optics, the majorant grid, a tally reset, the transport,
+ * the normalised outputs and the optional homogenisation -- as one CUDA graph.
+ * Each rt_step_launch replays it for the current contents of the inputs with
+ * no host synchronisation and no allocation.
+ *
+ * optics selects the meaning of field[0..4] (device float arrays [nz][ny][nx],
+ * read at every launch):
+ *   RT_OPTICS_SPLIT  k_gas, ssa_gas, k_cld, ssa_cld, g_cld (as rt_set_optics)
+ *   RT_OPTICS_TOTAL  k_ext, k_ext_cld, ssa, g; field[4] unused (as rt_set_optics_total)
+ * albedo: device [ny][nx] floats read at every launch, or NULL to use the
+ * handle's surface (which rt_set_surface may change between launches).
+ * Outputs (device doubles, each may be NULL) are overwritten at every launch:
+ * abs3d [W m^-3] and hr [K day^-1] nx*ny*nz; sfc_dir, sfc_dif, toa_up
+ * [W m^-2] nx*ny.
+ * homogenize: RT_HOM_SURFACE replaces sfc_dir and sfc_dif by their domain
+ * means (upward surface flux albedo * (dir + dif) then follows for a uniform
+ * albedo); RT_HOM_HEATING replaces every layer of abs3d and hr by its mean.
+ * Means are summed in a fixed order, so a replay is reproducible up to the
+ * order of the transport's atomic additions. */
+enum { RT_OPTICS_SPLIT = 0, RT_OPTICS_TOTAL = 1 };
+enum { RT_HOM_SURFACE = 1, RT_HOM_HEATING = 2 };
+
+typedef struct {
+    int optics;                  /* RT_OPTICS_* */
+    const float *field[5];
+    const float *albedo;
+    uint64_t photons;            /* photons per launch (> 0) */
+    double *abs3d, *hr, *sfc_dir, *sfc_dif, *toa_up;
+    int homogenize;              /* RT_HOM_* bits */
+} rt_step_desc;
+
+typedef struct rt_step_s *rt_step;
+
+/* Record the step of handle h. The handle must hold valid optics, a surface and
+ * an acceleration grid (RT_E_STATE otherwise): the grid's coarsening factors,
+ * the handle's options and its tally precision are fixed at this call. While
+ * the step exists the handle belongs to it: rt_set_optics, rt_set_optics_total,
+ * rt_build_accel, rt_set_options, rt_trace*, and rt_destroy return RT_E_STATE;
+ * rt_fields, rt_fields_split, rt_heating_rate, rt_stats and rt_synchronize
+ * report the last launch. One step per handle. *out receives the step. */
+int rt_step_create(rt_handle h, const rt_step_desc *desc, rt_step *out);
+
+/* Replay the step on the handle's stream for one sun position, top flux,
+ * diffuse fraction (as rt_trace_ex) and seed; asynchronous. Invalid values in
+ * the bound inputs are found on the device: the launch then traces nothing,
+ * writes zero outputs and rt_synchronize / rt_stats of the handle report
+ * RT_E_INVAL. */
+int rt_step_launch(rt_step s, double sza_deg, double azimuth_deg, double toa_flux, double diffuse_fraction,
+                   uint64_t seed);
+
+/* Free the step's graph and give the handle back to the ordinary calls. NULL is
+ * accepted. */
+int rt_step_destroy(rt_step s);
 
 /* ---- tracing without any allocation ---- */
 
@@ -293,6 +367,11 @@ int rt_debug_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int
  * Henyey-Greenstein with asymmetry g, 2 Lambertian), drawn with the transport
  * kernel's own functions; out: n floats on the host. */
 int rt_debug_sample(int kind, float g, uint64_t n, uint64_t seed, float *out);
+
+/* n two-dimensional Sobol points k0 .. k0+n-1 as the transport kernel computes
+ * them, XORed with sx and sy: out[2i], out[2i+1] are 32-bit binary fractions
+ * (host array of 2n words). */
+int rt_debug_sobol(uint64_t k0, int n, uint32_t sx, uint32_t sy, uint32_t *out);
 
 /* n rotations by the transport kernel's own turn: out[3i..3i+2] is the unit
  * vector at angle acos(mu[i]) from d and azimuth phi[i] about it (host arrays). */

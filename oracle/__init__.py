@@ -62,10 +62,11 @@ def _load():
         lib.or_sample_mu.restype = i32
         lib.or_turn.argtypes = [P, u64, P, P, P]
         lib.or_trace.argtypes = ([i32, i32, i32, f64, f64, f64] + [P] * 6 +
-                                 [f64, f64, u64, u64, u64, u64, i32, i32, u64, f64] + [P] * 9)
+                                 [f64, f64, u64, u64, u64, u64, i32, i32, u64, f64, i32] + [P] * 9)
         lib.or_trace.restype = i32
         lib.or_direct_beam.argtypes = [i32, i32, i32, f64, f64, f64, P, P, f64, f64, i32, i32, P]
         lib.or_direct_beam.restype = i32
+        lib.or_sobol2.argtypes = [u64, i32, P]
         _lib = lib
     return _lib
 
@@ -105,6 +106,14 @@ def turn(d, mu, phi) -> np.ndarray:
     return out
 
 
+def sobol2(n: int, k0: int = 0) -> np.ndarray:
+    """(n, 2) uint32: points k0..k0+n-1 of the 2D Sobol sequence (Sec. 2.3 start
+    positions), as 32-bit binary fractions."""
+    out = np.empty((n, 2), dtype=np.uint32)
+    _load().or_sobol2(int(k0), int(n), _ptr(out))
+    return out
+
+
 def sun_mu0(sza_deg: float) -> float:
     return float(np.cos(np.deg2rad(sza_deg)))
 
@@ -123,6 +132,18 @@ def heating_rate(abs_w_m3: np.ndarray, dz: float) -> np.ndarray:
     """K/day from absorbed power density [W m^-3], layout [nz][ny][nx]."""
     rho = air_density(abs_w_m3.shape[0], dz)
     return SECONDS_PER_DAY * abs_w_m3 / (rho[:, None, None] * CP_AIR)
+
+
+def homogenize(field: np.ndarray) -> np.ndarray:
+    """Horizontal homogenisation of the "-hom" and "-hom-hr" experiments
+    (Sec. 2.4): every horizontal layer of a [nz][ny][nx] field, or the single
+    layer of a [ny][nx] field, replaced by its mean over the layer's columns."""
+    f = np.asarray(field, dtype=np.float64)
+    layers = f.reshape(-1, f.shape[-2] * f.shape[-1])
+    out = np.empty_like(layers)
+    for k in range(layers.shape[0]):
+        out[k, :] = layers[k].sum() / layers.shape[1]
+    return out.reshape(f.shape)
 
 
 @dataclass
@@ -149,15 +170,18 @@ class OracleResult:
 def trace(scene, sza_deg: float, az_deg: float, toa_flux: float, photons: int, seed: int,
           id_begin: int = 0, photons_total: int | None = None, col_offset: int = 0,
           pcld_mode: int = 0, nthreads: int = 0, max_steps: int = 10**9,
-          diffuse_fraction: float = 0.0) -> OracleResult:
+          diffuse_fraction: float = 0.0, birth: str = "philox") -> OracleResult:
     """Analog FP64 Monte Carlo estimate (Sec. 2.3) for photon ids [id_begin, id_begin+photons).
 
     `photons_total` (default `photons`) sets the energy per photon, so that
     disjoint id ranges traced separately add up to one run. A share
     `diffuse_fraction` of the photons starts diffuse (isotropic downwelling
-    radiance at the domain top, Sec. 2.3).
+    radiance at the domain top, Sec. 2.3). `birth` "sobol" starts the photons of
+    each column at its scrambled Sobol points (Sec. 2.3) instead of uniform
+    random positions.
     """
     lib = _load()
+    birth_mode = {"philox": 0, "sobol": 1}[birth]
     nx, ny, nz = scene.nx, scene.ny, scene.nz
     ncell, ncol = nx * ny * nz, nx * ny
     arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in
@@ -170,7 +194,7 @@ def trace(scene, sza_deg: float, az_deg: float, toa_flux: float, photons: int, s
     st = lib.or_trace(nx, ny, nz, scene.dx, scene.dy, scene.dz, *[_ptr(a) for a in arrs],
                       float(sza_deg), float(az_deg), int(id_begin), int(id_begin + photons),
                       int(col_offset), int(seed), int(pcld_mode), int(nthreads), int(max_steps),
-                      float(diffuse_fraction),
+                      float(diffuse_fraction), birth_mode,
                       _ptr(tl_dir), _ptr(tl_dif), _ptr(n_adir), _ptr(n_adif), _ptr(n_sdir),
                       _ptr(n_sdif), _ptr(n_sabs), _ptr(n_toa), _ptr(tot))
     if st != 0:

@@ -105,6 +105,33 @@ static double stream_uniform(stream_t *s)
     return ((double)((hi << 26) | lo) + 0.5) * (1.0 / 9007199254740992.0);
 }
 
+/* ---------------- Sobol start positions (Sec. 2.3) ---------------- */
+
+/* Point k of the two-dimensional Sobol sequence in natural order, as 32-bit
+ * binary fractions (Sobol' 1967; Bratley & Fox 1988). Coordinate 1 is the
+ * base-2 radical inverse of k: bit i-1 of k contributes 2^-i. Coordinate 2 is
+ * the XOR, over the set bits i-1 of k, of the direction numbers v_i = m_i 2^-i
+ * of the primitive polynomial x + 1, whose recurrence is
+ * m_i = 2 m_(i-1) XOR m_(i-1) from m_1 = 1 (so m = 1, 3, 5, 15, 17, ...). */
+static void sobol2_point(uint32_t k, uint32_t out[2])
+{
+    uint32_t x = 0, y = 0, m = 1;
+    for (int i = 1; i <= 32; ++i) {
+        if ((k >> (i - 1)) & 1u) {
+            x ^= 1u << (32 - i);
+            y ^= m << (32 - i);
+        }
+        m = (m << 1) ^ m;
+    }
+    out[0] = x;
+    out[1] = y;
+}
+
+void or_sobol2(uint64_t k0, int n, uint32_t *out)
+{
+    for (int q = 0; q < n; ++q) sobol2_point((uint32_t)(k0 + (uint64_t)q), out + 2 * q);
+}
+
 /* ---------------- phase functions and directions (Sec. 2.3) ---------------- */
 
 /* Rayleigh: p(mu) = 3/8 (1 + mu^2) on [-1,1]; rejection from the uniform law. */
@@ -244,7 +271,8 @@ typedef struct {
 
 /* One analog photon history; returns 0 or OR_ESTEPS. */
 static int trace_photon(const scene_t *S, const double sun[3], uint64_t seed, uint64_t id,
-                        uint64_t col_offset, double diffuse_frac, uint64_t max_steps, tally_t *T, uint64_t loc[8])
+                        uint64_t col_offset, double diffuse_frac, int birth, uint64_t max_steps, tally_t *T,
+                        uint64_t loc[8])
 {
     stream_t rs;
     stream_init(&rs, seed, id);
@@ -252,8 +280,21 @@ static int trace_photon(const scene_t *S, const double sun[3], uint64_t seed, ui
     uint64_t c = (id + col_offset) % ncol;
     int i = (int)(c % S->nx), j = (int)(c / S->nx), k = S->nz - 1;
     double p[3], d[3] = {sun[0], sun[1], sun[2]};
-    p[0] = (i + stream_uniform(&rs)) * S->dx;
-    p[1] = (j + stream_uniform(&rs)) * S->dy;
+    if (birth == 1) {
+        /* the k-th photon of column c takes the column's k-th Sobol point,
+         * XOR-scrambled per axis by two words of its own Philox block for
+         * (column, seed) (a random digital shift) */
+        uint32_t pt[2], hs[4];
+        uint32_t ctr[4] = {(uint32_t)c, (uint32_t)(c >> 32), 0u, 0x5C7A3B1Eu};
+        uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        sobol2_point((uint32_t)((id + col_offset) / ncol), pt);
+        or_philox4x32_10(ctr, key, hs);
+        p[0] = (i + ((double)(pt[0] ^ hs[0]) + 0.5) * (1.0 / 4294967296.0)) * S->dx;
+        p[1] = (j + ((double)(pt[1] ^ hs[1]) + 0.5) * (1.0 / 4294967296.0)) * S->dy;
+    } else {
+        p[0] = (i + stream_uniform(&rs)) * S->dx;
+        p[1] = (j + stream_uniform(&rs)) * S->dy;
+    }
     p[2] = S->H;
     int direct = 1;
     /* Sec. 2.3: a share of the top flux enters as isotropic downwelling
@@ -342,8 +383,9 @@ static int scene_check(const scene_t *S)
 
 /*
  * Trace photon ids [id_begin, id_end). Photon id p starts in column
- * (p + col_offset) mod (nx*ny) at a uniform position, at the domain top, along
- * the sun beam (Sec. 2.3: rays start at the top of the domain; samples per
+ * (p + col_offset) mod (nx*ny) at a uniform position (birth 0) or at the
+ * column's scrambled Sobol point number (p + col_offset) div (nx*ny) (birth 1),
+ * at the domain top, along the sun beam (Sec. 2.3: rays start at the top of the domain; samples per
  * pixel = rays per column). All outputs are ACCUMULATED (+=), in raw units:
  * counts and k_abs*length [dimensionless]. totals[8] as in tally_t.tot.
  */
@@ -352,7 +394,7 @@ int or_trace(int nx, int ny, int nz, double dx, double dy, double dz,
              const float *ssa_cld, const float *g_cld, const float *albedo,
              double sza_deg, double az_deg, uint64_t id_begin, uint64_t id_end,
              uint64_t col_offset, uint64_t seed, int pcld_mode, int nthreads,
-             uint64_t max_steps, double diffuse_frac,
+             uint64_t max_steps, double diffuse_frac, int birth,
              double *tl_dir, double *tl_dif, uint64_t *n_abs_dir, uint64_t *n_abs_dif,
              uint64_t *n_sfc_dir, uint64_t *n_sfc_dif, uint64_t *n_sfc_abs, uint64_t *n_toa,
              uint64_t *totals)
@@ -361,6 +403,7 @@ int or_trace(int nx, int ny, int nz, double dx, double dy, double dz,
                  k_gas, ssa_gas, k_cld, ssa_cld, g_cld, albedo, pcld_mode};
     if (scene_check(&S) != OR_OK || !(sza_deg >= 0.0 && sza_deg < 90.0)) return OR_EINVAL;
     if (id_end < id_begin || !(diffuse_frac >= 0.0 && diffuse_frac <= 1.0)) return OR_EINVAL;
+    if (birth != 0 && birth != 1) return OR_EINVAL;
     tally_t T = {tl_dir, tl_dif, n_abs_dir, n_abs_dif, n_sfc_dir, n_sfc_dif, n_sfc_abs, n_toa, {0}};
     double sun[3];
     sun_direction(sza_deg, az_deg, sun);
@@ -374,7 +417,8 @@ int or_trace(int nx, int ny, int nz, double dx, double dy, double dz,
         int st = OR_OK;
 #pragma omp for schedule(dynamic, 1024)
         for (int64_t p = (int64_t)id_begin; p < (int64_t)id_end; ++p) {
-            if (trace_photon(&S, sun, seed, (uint64_t)p, col_offset, diffuse_frac, max_steps, &T, loc) != OR_OK)
+            if (trace_photon(&S, sun, seed, (uint64_t)p, col_offset, diffuse_frac, birth, max_steps, &T, loc) !=
+                OR_OK)
                 st = OR_ESTEPS;
         }
 #pragma omp critical

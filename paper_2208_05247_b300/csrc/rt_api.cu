@@ -110,6 +110,20 @@ struct rt_scene {
 
     bool optics_ok = false, surface_ok = false, accel_ok = false;
     double energy_in = 0.0;
+
+    rt_step step = nullptr;   // a recorded coupled-model step that owns the handle
+};
+
+struct rt_step_s {
+    rt_handle h = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t trace_node = nullptr;
+    cudaKernelNodeParams trace_params{};   // launch shape of the recorded transport node
+    bool fp64 = true;
+    rt::TraceArgs<double> a64{};
+    rt::TraceArgs<float> a32{};
+    uint64_t photons = 0;
 };
 
 namespace {
@@ -119,6 +133,15 @@ int check(rt_handle h)
     if (!h) return fail(RT_E_INVAL, "null handle");
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return fail(RT_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return RT_OK;
+}
+
+// check() for the calls that a recorded rt_step forbids on its handle.
+int check_free(rt_handle h, const char *who)
+{
+    int rc = check(h);
+    if (rc) return rc;
+    if (h->step) return fail(RT_E_STATE, "%s: the handle belongs to an rt_step; destroy the step first", who);
     return RT_OK;
 }
 
@@ -236,6 +259,9 @@ int device_status(rt_handle h)
     int st = 0;
     RT_CUDA(cudaMemcpyAsync(&st, &h->scr->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     RT_CUDA(cudaStreamSynchronize(h->stream));
+    if (st & rt::kStatusInput)
+        return fail(RT_E_INVAL, "the last rt_step launch found an invalid optical property or albedo "
+                                "in its inputs and traced nothing");
     if (st & rt::kStatusBudget)
         return fail(RT_E_BUDGET, "a photon reached the step cap; tallies are incomplete");
     return RT_OK;
@@ -256,6 +282,7 @@ rt::SceneDev<T> scene_desc(rt_handle h, T *base, bool batch)
     S.NX = h->NX; S.NY = h->NY; S.NZ = h->NZ;
     S.cx = h->cx; S.cy = h->cy; S.cz = h->cz;
     S.pcld_mode = h->opt.pcld_mode;
+    S.birth = h->opt.birth;
     S.dx = (float)h->dx; S.dy = (float)h->dy; S.dz = (float)h->dz;
     S.inv_dx = (float)(1.0 / h->dx); S.inv_dy = (float)(1.0 / h->dy); S.inv_dz = (float)(1.0 / h->dz);
     S.Lx = (float)(h->nx * h->dx); S.Ly = (float)(h->ny * h->dy); S.H = (float)(h->nz * h->dz);
@@ -375,6 +402,78 @@ int launch_batch(rt_handle home, const std::vector<rt_handle> &scenes, const std
     return RT_OK;
 }
 
+// Record one coupled-model step on capture stream cs (see rt_step_create). The
+// transport node is recorded with placeholder sun and seed; rt_step_launch
+// rewrites its arguments before every replay.
+template <typename T>
+int record_step(rt_handle h, const rt_step_desc *d, rt_step s, cudaStream_t cs, T *base, int bps)
+{
+    const size_t n = h->ncell, nc = (size_t)h->NX * h->NY * h->NZ;
+    RT_CUDA(cudaMemsetAsync(h->scr, 0, sizeof(rt::Scratch), cs));
+    RT_CUDA(cudaMemsetAsync(h->bad, 0, sizeof(int), cs));
+    RT_CUDA(cudaMemsetAsync(base, 0, tally_len(h) * sizeof(T), cs));
+    if (d->albedo) {
+        RT_CUDA(cudaMemcpyAsync(h->alb, d->albedo, h->ncol * sizeof(float), cudaMemcpyDeviceToDevice, cs));
+        rt::check_albedo<<<grid_for(h->ncol), 256, 0, cs>>>(h->alb, h->ncol, h->bad);
+        RT_CUDA(cudaGetLastError());
+    }
+    const float *const *f = d->field;
+    if (d->optics == RT_OPTICS_SPLIT)
+        rt::derive_optics<<<grid_for(n), 256, 0, cs>>>(f[0], f[1], f[2], f[3], f[4], h->rec, n, h->opt.pcld_mode,
+                                                       h->bad);
+    else
+        rt::derive_optics_total<<<grid_for(n), 256, 0, cs>>>(f[0], f[1], f[2], f[3], h->rec, n, h->bad);
+    RT_CUDA(cudaGetLastError());
+    rt::build_majorant<<<grid_for(nc), 256, 0, cs>>>(h->rec, h->kmax, h->nx, h->ny, h->nz, h->cx, h->cy, h->cz,
+                                                     h->NX, h->NY, h->NZ);
+    RT_CUDA(cudaGetLastError());
+    rt::step_gate<<<1, 32, 0, cs>>>(h->bad, h->scr);
+    RT_CUDA(cudaGetLastError());
+
+    rt::TraceArgs<T> A{};
+    A.scene = scene_desc<T>(h, base, false);
+    A.job = job_desc(h, 0.0, 0.0, 0.0, 1.0, d->photons, 0, 0);
+    A.count = d->photons;
+    A.scr = h->scr;
+    fill_launch(h, A);
+    if constexpr (std::is_same<T, double>::value) s->a64 = A;
+    else s->a32 = A;
+    const int block = h->opt.block_size > 0 ? h->opt.block_size : 256;
+    rt::trace_kernel<T, false><<<h->num_sms * bps, block, 0, cs>>>(A);
+    RT_CUDA(cudaGetLastError());
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    RT_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &deps, nullptr, &ndeps));
+    if (st != cudaStreamCaptureStatusActive || ndeps != 1)
+        return fail(RT_E_CUDA, "rt_step_create: unexpected capture state after the transport launch");
+    s->trace_node = deps[0];
+
+    const rt::Tallies<T> t = tallies_of(base, h->ncell, h->ncol);
+    if (d->abs3d) {
+        rt::sum_fields<T><<<grid_for(n), 256, 0, cs>>>(t.abs_dir, t.abs_dif, d->abs3d, n);
+        RT_CUDA(cudaGetLastError());
+        if (d->homogenize & RT_HOM_HEATING) rt::homogenize_layers<<<h->nz, 1024, 0, cs>>>(d->abs3d, h->ncol);
+        RT_CUDA(cudaGetLastError());
+    }
+    if (d->hr) {
+        rt::heating_rate<T><<<grid_for(n), 256, 0, cs>>>(t.abs_dir, t.abs_dif, h->hr_factor, d->hr, h->ncol, n);
+        RT_CUDA(cudaGetLastError());
+        if (d->homogenize & RT_HOM_HEATING) rt::homogenize_layers<<<h->nz, 1024, 0, cs>>>(d->hr, h->ncol);
+        RT_CUDA(cudaGetLastError());
+    }
+    double *out2[3] = {d->sfc_dir, d->sfc_dif, d->toa_up};
+    const T *src2[3] = {t.sfc_dir, t.sfc_dif, t.toa};
+    for (int q = 0; q < 3; ++q) {
+        if (!out2[q]) continue;
+        rt::sum_fields<T><<<grid_for(h->ncol), 256, 0, cs>>>(src2[q], nullptr, out2[q], h->ncol);
+        RT_CUDA(cudaGetLastError());
+        if (q < 2 && (d->homogenize & RT_HOM_SURFACE)) rt::homogenize_layers<<<1, 1024, 0, cs>>>(out2[q], h->ncol);
+        RT_CUDA(cudaGetLastError());
+    }
+    return RT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -448,6 +547,7 @@ rt_handle rt_create(int nx, int ny, int nz, double dx, double dy, double dz)
 int rt_destroy(rt_handle h)
 {
     if (!h) return RT_OK;
+    if (h->step) return fail(RT_E_STATE, "rt_destroy: destroy the handle's rt_step first");
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
@@ -480,7 +580,7 @@ int rt_set_stream(rt_handle h, void *stream)
 
 int rt_set_options(rt_handle h, const rt_options *o)
 {
-    int rc = check(h);
+    int rc = check_free(h, "rt_set_options");
     if (rc) return rc;
     if (!o) return fail(RT_E_INVAL, "rt_set_options: null options");
     if (o->block_size < 0 || o->block_size % 32 != 0 || o->block_size > 256)
@@ -499,6 +599,8 @@ int rt_set_options(rt_handle h, const rt_options *o)
         return fail(RT_E_INVAL, "rt_set_options: batch_optics must be 0 or 1");
     if (o->tally_precision != RT_TALLY_FP64 && o->tally_precision != RT_TALLY_FP32)
         return fail(RT_E_INVAL, "rt_set_options: unknown tally_precision");
+    if (o->birth != RT_BIRTH_PHILOX && o->birth != RT_BIRTH_SOBOL)
+        return fail(RT_E_INVAL, "rt_set_options: unknown birth mode");
     if (o->blocks_per_sm > 0) {
         int fit = 0;
         const int block = o->block_size > 0 ? o->block_size : 256;
@@ -522,7 +624,7 @@ int rt_get_options(rt_handle h, rt_options *o)
 int rt_set_optics(rt_handle h, const float *k_gas, const float *ssa_gas, const float *k_cld,
                   const float *ssa_cld, const float *g_cld, int mem)
 {
-    int rc = check(h);
+    int rc = check_free(h, "rt_set_optics");
     if (rc) return rc;
     if (!k_gas || !ssa_gas || !k_cld || !ssa_cld || !g_cld)
         return fail(RT_E_INVAL, "rt_set_optics: null field pointer");
@@ -566,7 +668,7 @@ int rt_set_optics(rt_handle h, const float *k_gas, const float *ssa_gas, const f
 int rt_set_optics_total(rt_handle h, const float *k_ext, const float *k_ext_cld, const float *ssa,
                         const float *g_cld, int mem)
 {
-    int rc = check(h);
+    int rc = check_free(h, "rt_set_optics_total");
     if (rc) return rc;
     if (!k_ext || !k_ext_cld || !ssa || !g_cld) return fail(RT_E_INVAL, "rt_set_optics_total: null field pointer");
     if (mem != RT_HOST && mem != RT_DEVICE) return fail(RT_E_INVAL, "rt_set_optics_total: bad mem flag");
@@ -617,7 +719,7 @@ int rt_set_surface(rt_handle h, const float *albedo, int mem)
 
 int rt_build_accel(rt_handle h, int cx, int cy, int cz)
 {
-    int rc = check(h);
+    int rc = check_free(h, "rt_build_accel");
     if (rc) return rc;
     if (!h->optics_ok) return fail(RT_E_STATE, "rt_build_accel: set valid optics first");
     if (cx == 0 && cy == 0 && cz == 0) {
@@ -662,7 +764,7 @@ int rt_build_accel(rt_handle h, int cx, int cy, int cz)
 int rt_trace_ex(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux, double diffuse_fraction,
                 uint64_t photon_begin, uint64_t photon_count, uint64_t photons_total, uint64_t seed)
 {
-    int rc = check(h);
+    int rc = check_free(h, "rt_trace");
     if (rc) return rc;
     if (!h->optics_ok || !h->surface_ok || !h->accel_ok)
         return fail(RT_E_STATE, "rt_trace: set optics and surface and build the acceleration grid first");
@@ -691,7 +793,7 @@ int rt_trace_range(rt_handle h, double sza_deg, double azimuth_deg, double toa_f
 
 int rt_trace(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux, uint64_t photons, uint64_t seed)
 {
-    if (photons == 0) return check(h);
+    if (photons == 0) return check_free(h, "rt_trace");
     return rt_trace_range(h, sza_deg, azimuth_deg, toa_flux, 0, photons, photons, seed);
 }
 
@@ -708,6 +810,7 @@ int rt_trace_batch(const rt_job *jobs, int njobs, uint64_t total_photons, uint64
         const rt_job &jb = jobs[j];
         rt_handle h = jb.scene;
         if (!h) return fail(RT_E_INVAL, "rt_trace_batch: job %d has no scene", j);
+        if (h->step) return fail(RT_E_STATE, "rt_trace_batch: job %d: the scene belongs to an rt_step", j);
         if (h->device != home->device) return fail(RT_E_INVAL, "rt_trace_batch: all scenes must be on one device");
         if (!h->optics_ok || !h->surface_ok || !h->accel_ok)
             return fail(RT_E_STATE, "rt_trace_batch: job %d: set optics and surface and build the "
@@ -778,6 +881,112 @@ int rt_trace_batch(const rt_job *jobs, int njobs, uint64_t total_photons, uint64
     }
     for (int j = 0; j < njobs; ++j)
         if (n[j]) jobs[j].scene->energy_in += energy[j];
+    return RT_OK;
+}
+
+int rt_step_create(rt_handle h, const rt_step_desc *d, rt_step *out)
+{
+    if (out) *out = nullptr;
+    int rc = check_free(h, "rt_step_create");
+    if (rc) return rc;
+    if (!d || !out) return fail(RT_E_INVAL, "rt_step_create: null descriptor or output");
+    if (d->optics != RT_OPTICS_SPLIT && d->optics != RT_OPTICS_TOTAL)
+        return fail(RT_E_INVAL, "rt_step_create: unknown optics kind");
+    for (int q = 0; q < (d->optics == RT_OPTICS_SPLIT ? 5 : 4); ++q)
+        if (!d->field[q]) return fail(RT_E_INVAL, "rt_step_create: null optics field %d", q);
+    if (d->photons == 0) return fail(RT_E_INVAL, "rt_step_create: photons must be positive");
+    if (d->homogenize & ~(RT_HOM_SURFACE | RT_HOM_HEATING))
+        return fail(RT_E_INVAL, "rt_step_create: unknown homogenize bits");
+    if (!h->optics_ok || !h->surface_ok || !h->accel_ok)
+        return fail(RT_E_STATE, "rt_step_create: set optics and surface and build the acceleration grid first");
+    if ((rc = ensure_tallies(h))) return rc;
+
+    rt_step s = new (std::nothrow) rt_step_s;
+    if (!s) return fail(RT_E_OOM, "rt_step_create: host allocation failed");
+    s->h = h;
+    s->photons = d->photons;
+    s->fp64 = h->tally_prec == RT_TALLY_FP64;
+    const int block = h->opt.block_size > 0 ? h->opt.block_size : 256;
+    int bps = h->opt.blocks_per_sm;
+    cudaStream_t cs = nullptr;
+    auto bail = [&](int code) {
+        if (s->exec) cudaGraphExecDestroy(s->exec);
+        if (s->graph) cudaGraphDestroy(s->graph);
+        if (cs) cudaStreamDestroy(cs);
+        delete s;
+        return code;
+    };
+    cudaError_t e = cudaSuccess;
+    if (bps <= 0) {
+        e = s->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rt::trace_kernel<double, false>, block, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rt::trace_kernel<float, false>, block, 0);
+        bps = std::max(1, bps);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bail(fail(RT_E_CUDA, "rt_step_create: %s", cudaGetErrorString(e)));
+    rc = s->fp64 ? record_step<double>(h, d, s, cs, h->t64, bps) : record_step<float>(h, d, s, cs, h->t32, bps);
+    e = cudaStreamEndCapture(cs, &s->graph);
+    if (rc) return bail(rc);
+    if (e != cudaSuccess) return bail(fail(RT_E_CUDA, "rt_step_create: capture: %s", cudaGetErrorString(e)));
+    e = cudaGraphKernelNodeGetParams(s->trace_node, &s->trace_params);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->exec, s->graph, 0);
+    if (e != cudaSuccess) return bail(fail(RT_E_CUDA, "rt_step_create: %s", cudaGetErrorString(e)));
+    cudaStreamDestroy(cs);
+    cs = nullptr;
+    // later rt_trace_batch use would need the split record, which replays do not refresh
+    h->split_ok = false;
+    h->accel2_ok = false;
+    h->step = s;
+    *out = s;
+    return RT_OK;
+}
+
+int rt_step_launch(rt_step s, double sza_deg, double azimuth_deg, double toa_flux, double diffuse_fraction,
+                   uint64_t seed)
+{
+    if (!s) return fail(RT_E_INVAL, "rt_step_launch: null step");
+    rt_handle h = s->h;
+    int rc = check(h);
+    if (rc) return rc;
+    if (!(sza_deg >= 0.0 && sza_deg < 90.0)) return fail(RT_E_INVAL, "rt_step_launch: sza must be in [0, 90)");
+    if (!std::isfinite(azimuth_deg)) return fail(RT_E_INVAL, "rt_step_launch: azimuth must be finite");
+    if (!(toa_flux >= 0.0) || !std::isfinite(toa_flux))
+        return fail(RT_E_INVAL, "rt_step_launch: toa_flux must be >= 0");
+    if (!(diffuse_fraction >= 0.0 && diffuse_fraction <= 1.0))
+        return fail(RT_E_INVAL, "rt_step_launch: diffuse_fraction must be in [0, 1]");
+    rt::JobDev J = job_desc(h, sza_deg, azimuth_deg, toa_flux, 1.0, s->photons, seed, 0);
+    J.diffuse = (float)diffuse_fraction;
+    J.start = 0;
+    J.id_begin = 0;
+    cudaKernelNodeParams p = s->trace_params;
+    void *args[1];
+    if (s->fp64) {
+        s->a64.job = J;
+        args[0] = &s->a64;
+    } else {
+        s->a32.job = J;
+        args[0] = &s->a32;
+    }
+    p.kernelParams = args;
+    p.extra = nullptr;
+    RT_CUDA(cudaGraphExecKernelNodeSetParams(s->exec, s->trace_node, &p));
+    RT_CUDA(cudaGraphLaunch(s->exec, h->stream));
+    h->energy_in = toa_flux * std::cos(sza_deg * kPi / 180.0) * h->nx * h->dx * h->ny * h->dy;
+    return RT_OK;
+}
+
+int rt_step_destroy(rt_step s)
+{
+    if (!s) return RT_OK;
+    rt_handle h = s->h;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    if (s->exec) cudaGraphExecDestroy(s->exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    h->step = nullptr;
+    delete s;
     return RT_OK;
 }
 
@@ -885,7 +1094,7 @@ int rt_stats(rt_handle h, rt_stats_t *out)
     out->energy_created = s.created;
     out->energy_destroyed = s.destroyed;
     out->energy_capped = s.capped_energy;
-    out->status = (s.status & rt::kStatusBudget) ? RT_E_BUDGET : RT_OK;
+    out->status = (s.status & rt::kStatusInput) ? RT_E_INVAL : (s.status & rt::kStatusBudget) ? RT_E_BUDGET : RT_OK;
     return RT_OK;
 }
 
@@ -926,6 +1135,21 @@ int rt_debug_sample(int kind, float g, uint64_t n, uint64_t seed, float *out)
     cudaError_t e = cudaMemcpy(out, d, n * sizeof(float), cudaMemcpyDeviceToHost);
     cudaFree(d);
     if (e != cudaSuccess) return fail(RT_E_CUDA, "rt_debug_sample: %s", cudaGetErrorString(e));
+    return RT_OK;
+}
+
+int rt_debug_sobol(uint64_t k0, int n, uint32_t sx, uint32_t sy, uint32_t *out)
+{
+    if (n <= 0 || !out || k0 + (uint64_t)n > ((uint64_t)1 << 32))
+        return fail(RT_E_INVAL, "rt_debug_sobol: need 0 < n and k0 + n <= 2^32");
+    uint32_t *d = nullptr;
+    int rc = dev_alloc(&d, 2 * (size_t)n);
+    if (rc) return rc;
+    rt::debug_sobol<<<(n + 255) / 256, 256>>>(k0, n, sx, sy, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(out, d, 2 * (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(RT_E_CUDA, "rt_debug_sobol: %s", cudaGetErrorString(e));
     return RT_OK;
 }
 

@@ -46,6 +46,35 @@ __device__ __forceinline__ float u01(uint32_t x)
 }
 
 // ---------------------------------------------------------------------------
+// Sobol start positions (Sec. 2.3: photons enter the domain top at the points
+// of a scrambled Sobol sequence). The first two Sobol dimensions in natural
+// order, as 32-bit binary fractions: dimension 1 is the base-2 radical inverse
+// of k (bit reversal); dimension 2 XORs the direction numbers V_i of the
+// primitive polynomial x + 1 (m_1 = 1), V_1 = 2^31 and V_i = V_(i-1) ^
+// (V_(i-1) >> 1), over the set bits of k. Each aligned block of 2^m points is a
+// (0,m,2)-net; XOR with a fixed random word per axis (a random digital shift)
+// keeps that property and makes each point uniform.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t sobol_dim1(uint32_t k)
+{
+#ifdef __CUDA_ARCH__
+    return __brev(k);
+#else
+    uint32_t r = 0;
+    for (int b = 0; b < 32; ++b) r |= ((k >> b) & 1u) << (31 - b);
+    return r;
+#endif
+}
+
+__host__ __device__ __forceinline__ uint32_t sobol_dim2(uint32_t k)
+{
+    uint32_t v = 0x80000000u, r = 0u;
+    for (; k; k >>= 1, v ^= v >> 1)
+        if (k & 1u) r ^= v;
+    return r;
+}
+
+// ---------------------------------------------------------------------------
 // Phase functions (Sec. 2.3): Rayleigh for gas, Henyey-Greenstein without
 // delta-scaling for cloud droplets. Both by exact inversion of the CDF.
 // ---------------------------------------------------------------------------

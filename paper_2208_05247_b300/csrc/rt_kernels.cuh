@@ -18,6 +18,8 @@
 namespace rt {
 
 constexpr int kStatusBudget = 1;
+constexpr int kStatusInput = 2;                        // an rt_step launch found invalid inputs
+constexpr unsigned long long kQueueClosed = 1ull << 62; // queue head that no launch ever reaches
 
 // Per-handle device scratch: the photon queue head, counters and ledger.
 struct Scratch {
@@ -53,6 +55,8 @@ struct SceneDev {
     int nx, ny, nz, NX, NY, NZ, cx, cy, cz, pcld_mode;
     float dx, dy, dz, inv_dx, inv_dy, inv_dz, Lx, Ly, H;
     float cdx, cdy, cdz;   // coarse cell size [m] (the last cell may be smaller)
+    int birth;             // start positions: 0 Philox uniforms, 1 scrambled Sobol
+    int pad_[3];
 };
 
 // One traced job: a scene, a sun position, an energy per photon and a range of
@@ -282,6 +286,16 @@ enum : int { kNone = 0, kEvent = 1, kSurface = 2, kTop = 3, kCap = 4 };
 #define RT_SC(f) (BATCH ? s_scenes[sid].f : A.scene.f)
 #define RT_JB(f) (BATCH ? s_jobs[jid].f : A.job.f)
 
+// Scrambled Sobol start point k of column col (Sec. 2.3): the column's two
+// scramble words come from Philox counter (col, 0, 0, 2) under the job's key.
+// Kept out of line: it runs once per photon, and inlining it into the refill
+// phase made the batched kernel spill.
+__device__ __noinline__ uint2 sobol_start(uint32_t k, uint32_t col, uint32_t k0, uint32_t k1)
+{
+    const uint4 h = philox4x32_10(make_uint4(col, 0u, 0u, 2u), k0, k1);
+    return make_uint2(sobol_dim1(k) ^ h.x, sobol_dim2(k) ^ h.y);
+}
+
 template <typename T, bool BATCH>
 __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ TraceArgs<T> A)
 {
@@ -410,8 +424,17 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
                 const int ci = (int)(col % (unsigned)RT_SC(nx)), cj = (int)(col / (unsigned)RT_SC(nx));
                 const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), 0u, 0u),
                                               RT_JB(key0), RT_JB(key1));
-                ox = ((float)ci + u01(r.x)) * RT_SC(dx);
-                oy = ((float)cj + u01(r.y)) * RT_SC(dy);
+                uint32_t bx = r.x, by = r.y;
+                if (RT_SC(birth)) {
+                    // photon k = gid / ncol of its column takes the column's k-th
+                    // Sobol point, shifted by that column's scramble words
+                    const uint32_t k = (gid >> 32) ? (uint32_t)(gid / ncol) : (uint32_t)gid / (uint32_t)ncol;
+                    const uint2 p = sobol_start(k, col, RT_JB(key0), RT_JB(key1));
+                    bx = p.x;
+                    by = p.y;
+                }
+                ox = ((float)ci + u01(bx)) * RT_SC(dx);
+                oy = ((float)cj + u01(by)) * RT_SC(dy);
                 oz = RT_SC(H);
                 ux = RT_JB(sx); uy = RT_JB(sy); uz = RT_JB(sz);
                 direct = true;
@@ -718,6 +741,44 @@ __global__ void ledger_reduce(Tallies<T> t, const float *__restrict__ alb, size_
 }
 
 // ---------------------------------------------------------------------------
+// Coupled-model step (Sec. 2.2: one radiation call per model step).
+// ---------------------------------------------------------------------------
+
+// Runs after the step's inputs were validated into *bad: on invalid input the
+// photon queue is closed, so the transport launch that follows takes no photon,
+// and the status records why.
+__global__ void step_gate(const int *__restrict__ bad, Scratch *scr)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0 && *bad) {
+        scr->queue_head = kQueueClosed;
+        scr->status |= kStatusInput;
+    }
+}
+
+// Horizontal homogenisation of the "-hom" experiments (Sec. 2.4): every value
+// of a layer of n_layer values becomes the layer's mean. One block per layer;
+// each thread sums a fixed strided subset, then a fixed shuffle tree, so the
+// result does not depend on scheduling.
+__global__ void homogenize_layers(double *__restrict__ f, size_t n_layer)
+{
+    __shared__ double part[32];
+    double *row = f + (size_t)blockIdx.x * n_layer;
+    double s = 0.0;
+    for (size_t i = threadIdx.x; i < n_layer; i += blockDim.x) s += row[i];
+    s = warp_sum_f64(s);
+    if ((threadIdx.x & 31u) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+        v = warp_sum_f64(v);
+        if (threadIdx.x == 0) part[0] = v / (double)n_layer;
+    }
+    __syncthreads();
+    const double m = part[0];
+    for (size_t i = threadIdx.x; i < n_layer; i += blockDim.x) row[i] = m;
+}
+
+// ---------------------------------------------------------------------------
 // Test kernels: the device RNG, samplers and rotation on small arrays.
 // ---------------------------------------------------------------------------
 __global__ void debug_philox(const uint4 *ctr, const uint2 *key, uint4 *out, int n)
@@ -736,6 +797,15 @@ __global__ void debug_sample(int kind, float g, unsigned long long n, uint32_t k
     else if (kind == 1) mu = hg_mu(g, u01(r.x));
     else { float x, y, z; lambert_up(x, y, z, u01(r.x), u01(r.y)); mu = z; }
     out[i] = mu;
+}
+
+__global__ void debug_sobol(unsigned long long k0, int n, uint32_t sx, uint32_t sy, uint32_t *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t k = (uint32_t)(k0 + i);
+    out[2 * i] = sobol_dim1(k) ^ sx;
+    out[2 * i + 1] = sobol_dim2(k) ^ sy;
 }
 
 __global__ void debug_turn(float dx, float dy, float dz, const float *mu, const float *phi, float *out, int n)

@@ -18,6 +18,9 @@ RT_OK, RT_E_INVAL, RT_E_STATE, RT_E_CUDA, RT_E_OOM, RT_E_BUDGET = 0, -1, -2, -3,
 RT_HOST, RT_DEVICE = 0, 1
 RT_PCLD_SCATTERING, RT_PCLD_EXTINCTION = 0, 1
 RT_TALLY_FP64, RT_TALLY_FP32 = 0, 1
+RT_OPTICS_SPLIT, RT_OPTICS_TOTAL = 0, 1
+RT_HOM_SURFACE, RT_HOM_HEATING = 1, 2
+RT_BIRTH_PHILOX, RT_BIRTH_SOBOL = 0, 1
 
 _ERRNAMES = {RT_E_INVAL: "RT_E_INVAL", RT_E_STATE: "RT_E_STATE", RT_E_CUDA: "RT_E_CUDA",
              RT_E_OOM: "RT_E_OOM", RT_E_BUDGET: "RT_E_BUDGET"}
@@ -34,13 +37,20 @@ class rt_options(ctypes.Structure):
                 ("refill_chunk", ctypes.c_int), ("max_steps", ctypes.c_uint32),
                 ("pcld_mode", ctypes.c_int), ("tally_precision", ctypes.c_int),
                 ("ready_threshold", ctypes.c_int), ("max_inner", ctypes.c_int),
-                ("batch_optics", ctypes.c_int)]
+                ("batch_optics", ctypes.c_int), ("birth", ctypes.c_int)]
 
 
 class rt_job(ctypes.Structure):
     _fields_ = [("scene", ctypes.c_void_p), ("sza_deg", ctypes.c_double), ("azimuth_deg", ctypes.c_double),
                 ("toa_flux", ctypes.c_double), ("gas_scale", ctypes.c_double), ("photons", ctypes.c_uint64),
                 ("diffuse_fraction", ctypes.c_double)]
+
+
+class rt_step_desc(ctypes.Structure):
+    _fields_ = [("optics", ctypes.c_int), ("field", ctypes.c_void_p * 5), ("albedo", ctypes.c_void_p),
+                ("photons", ctypes.c_uint64), ("abs3d", ctypes.c_void_p), ("hr", ctypes.c_void_p),
+                ("sfc_dir", ctypes.c_void_p), ("sfc_dif", ctypes.c_void_p), ("toa_up", ctypes.c_void_p),
+                ("homogenize", ctypes.c_int)]
 
 
 class rt_stats_t(ctypes.Structure):
@@ -89,9 +99,13 @@ def library() -> ctypes.CDLL:
             "rt_last_error_code": ([], i32),
             "rt_trace_noalloc": ([i32, i32, i32, f64, f64, f64] + [P] * 6 + [i32, i32, i32, f64, f64, f64,
                                                                             u64, u64] + [P] * 5 + [P, P], i32),
+            "rt_step_create": ([H, ctypes.POINTER(rt_step_desc), ctypes.POINTER(ctypes.c_void_p)], i32),
+            "rt_step_launch": ([P, f64, f64, f64, f64, u64], i32),
+            "rt_step_destroy": ([P], i32),
             "rt_debug_philox": ([P, P, P, i32], i32),
             "rt_debug_sample": ([i32, ctypes.c_float, u64, u64, P], i32),
             "rt_debug_turn": ([P, P, P, P, i32], i32),
+            "rt_debug_sobol": ([u64, i32, ctypes.c_uint32, ctypes.c_uint32, P], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -302,6 +316,44 @@ def rt_trace_noalloc(nx, ny, nz, dx, dy, dz, k_gas, ssa_gas, k_cld, ssa_cld, g_c
     return ev.value
 
 
+def rt_step_create(h, ncell, ncol, fields, photons, albedo=None, abs3d=None, hr=None, sfc_dir=None,
+                   sfc_dif=None, toa_up=None, homogenize=0, optics=None) -> int:
+    """Record a coupled-model step over CUDA tensors; returns the step pointer.
+
+    `fields` are the five split optics fields (or four total-optics fields, with
+    optics=RT_OPTICS_TOTAL); every buffer must be a CUDA tensor and stay alive
+    until rt_step_destroy.
+    """
+    optics = (RT_OPTICS_SPLIT if len(fields) == 5 else RT_OPTICS_TOTAL) if optics is None else optics
+    ins = [_buf(a, ncell, np.float32, "field%d" % q) for q, a in enumerate(fields)]
+    ins.append(_buf(albedo, ncol, np.float32, "albedo"))
+    outs = [_buf(abs3d, ncell, np.float64, "abs3d", True), _buf(hr, ncell, np.float64, "hr", True)]
+    outs += [_buf(a, ncol, np.float64, n, True) for a, n in
+             zip((sfc_dir, sfc_dif, toa_up), ("sfc_dir", "sfc_dif", "toa_up"))]
+    if _same_mem(*ins, *outs) != RT_DEVICE:
+        raise ValueError("rt_step_create takes device buffers only")
+    d = rt_step_desc()
+    d.optics = int(optics)
+    for q, (ptr, _) in enumerate(ins[:-1]):
+        d.field[q] = ptr
+    d.albedo = ins[-1][0]
+    d.photons = int(photons)
+    d.abs3d, d.hr, d.sfc_dir, d.sfc_dif, d.toa_up = [ptr for ptr, _ in outs]
+    d.homogenize = int(homogenize)
+    out = ctypes.c_void_p(0)
+    _check(library().rt_step_create(h, ctypes.byref(d), ctypes.byref(out)))
+    return out.value
+
+
+def rt_step_launch(step, sza_deg, azimuth_deg, toa_flux, diffuse_fraction=0.0, seed=1):
+    _check(library().rt_step_launch(step, float(sza_deg), float(azimuth_deg), float(toa_flux),
+                                    float(diffuse_fraction), int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+
+def rt_step_destroy(step):
+    _check(library().rt_step_destroy(step))
+
+
 def rt_debug_philox(ctr, key) -> np.ndarray:
     ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
     key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
@@ -316,6 +368,13 @@ def rt_debug_sample(kind: str, n: int, seed: int = 1, g: float = 0.0) -> np.ndar
     k = {"rayleigh": 0, "hg": 1, "lambert": 2}[kind]
     out = np.empty(n, dtype=np.float32)
     _check(library().rt_debug_sample(k, float(g), int(n), int(seed), out.ctypes.data))
+    return out
+
+
+def rt_debug_sobol(k0: int, n: int, sx: int = 0, sy: int = 0) -> np.ndarray:
+    """(n, 2) uint32 Sobol points k0..k0+n-1 from the device, XORed with (sx, sy)."""
+    out = np.empty((n, 2), dtype=np.uint32)
+    _check(library().rt_debug_sobol(int(k0), int(n), int(sx), int(sy), out.ctypes.data))
     return out
 
 

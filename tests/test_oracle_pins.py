@@ -336,3 +336,83 @@ def test_mc_diffuse_fraction_through_an_absorbing_slab():
     n = r.counts["sfc_dif"].sum()
     assert r.counts["sfc_dir"].sum() == 0
     assert abs(n - p * N) < 4 * np.sqrt(N * p * (1 - p))
+
+
+def test_homogenize_layer_means():
+    """Sec. 2.4 homogenisation: a field that already is horizontally uniform is
+    left alone (a mean over the wrong axis would change it), a field varying
+    only in x becomes its x-mean in every layer, and layer sums are kept."""
+    nz, ny, nx = 4, 3, 5
+    zonly = np.broadcast_to(np.arange(1.0, nz + 1)[:, None, None], (nz, ny, nx)).copy()
+    assert np.array_equal(oracle.homogenize(zonly), zonly)
+    xonly = np.broadcast_to(np.array([1.0, 2.0, 4.0, 8.0, 16.0])[None, None, :], (nz, ny, nx)).copy()
+    assert np.allclose(oracle.homogenize(xonly), 31.0 / 5.0, rtol=0, atol=1e-15)
+    rng = np.random.default_rng(0)
+    f = rng.random((nz, ny, nx))
+    h = oracle.homogenize(f)
+    for k in range(nz):                      # brute force: each layer's own mean
+        tot = 0.0
+        for j in range(ny):
+            for i in range(nx):
+                tot += f[k, j, i]
+        assert np.allclose(h[k], tot / (nx * ny), rtol=1e-15, atol=0)
+    assert np.allclose(oracle.homogenize(h), h, rtol=1e-15, atol=0)
+    s2 = rng.random((ny, nx))
+    assert np.allclose(oracle.homogenize(s2), s2.mean(), rtol=1e-15, atol=0)
+
+
+# --- Sobol start positions (Sec. 2.3) -------------------------------------------------
+
+# Natural-order points 0..7 of the first two Sobol dimensions (dimension 1 is the
+# van der Corput sequence; dimension 2 from the polynomial x + 1), as fractions.
+SOBOL2_FIRST8 = [(0, 0), (1 / 2, 1 / 2), (1 / 4, 3 / 4), (3 / 4, 1 / 4), (1 / 8, 5 / 8), (5 / 8, 1 / 8),
+                 (3 / 8, 3 / 8), (7 / 8, 7 / 8)]
+
+
+def _is_net(pts: np.ndarray, m: int) -> bool:
+    """Each of the 2^m elementary boxes of every shape 2^-a x 2^-b (a + b = m)
+    holds exactly one of the 2^m points."""
+    x, y = pts[:, 0].astype(np.uint64), pts[:, 1].astype(np.uint64)
+    for a in range(m + 1):
+        b = m - a
+        box = (x >> np.uint64(32 - a)) * np.uint64(1 << b) + (y >> np.uint64(32 - b)) if m else x * 0
+        if np.unique(box).size != (1 << m):
+            return False
+    return True
+
+
+def test_sobol_points_and_net_property():
+    pts = oracle.sobol2(1 << 12)
+    assert [tuple(p) for p in pts[:8] / 2.0 ** 32] == SOBOL2_FIRST8
+    for m in range(1, 11):
+        for blk in range(2):                   # the first two aligned blocks of 2^m points
+            assert _is_net(pts[blk << m:(blk + 1) << m], m), m
+    # a random digital shift (XOR with one word per axis) keeps the net property
+    rng = np.random.default_rng(4)
+    sx, sy = rng.integers(0, 2 ** 32, size=2, dtype=np.uint64).astype(np.uint32)
+    sh = pts ^ np.array([sx, sy], dtype=np.uint32)
+    for m in (3, 6, 9):
+        assert _is_net(sh[:1 << m], m)
+    # a plain random sample is not a net (the check has teeth)
+    assert not _is_net(rng.integers(0, 2 ** 32, size=(512, 2), dtype=np.uint64).astype(np.uint32), 9)
+    # the continuation far along the sequence: points 2^20 .. 2^20 + 2^8 form a net too
+    assert _is_net(oracle.sobol2(256, 1 << 20), 8)
+
+
+def test_sobol_birth_is_unbiased_and_stratifies_the_direct_beam(small_scene):
+    """With Sobol start points the surface direct irradiance still has the
+    deterministic Beer-Lambert column means as its expectation, and its error
+    per column is smaller than with uniform random starts at equal photons."""
+    sc = small_scene
+    F, sza, az = 1000.0, 30.0, 30.0
+    truth = F * np.cos(np.deg2rad(sza)) * oracle.direct_beam(sc, sza, az, nsub=16)
+    N = 16 * sc.ncol
+    err = {}
+    for birth in ("philox", "sobol"):
+        runs = [oracle.trace(sc, sza, az, F, N, 900 + s, birth=birth).sfc_dir for s in range(8)]
+        r = np.stack(runs)
+        m = r.mean(axis=0)
+        se = r.std(axis=0, ddof=1).mean() / np.sqrt(len(runs))
+        assert abs(m.mean() - truth.mean()) < 4 * se + 1e-9, birth
+        err[birth] = np.sqrt(((r - truth) ** 2).mean())
+    assert err["sobol"] < 0.7 * err["philox"], err
