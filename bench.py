@@ -67,6 +67,9 @@ def parse():
                    help="use the default launch parameters and the --coarse grid")
     p.add_argument("--coarse", type=int, nargs=3, default=None,
                    help="coarse grid factors; implies --no-autotune")
+    p.add_argument("--launch", type=int, nargs=3, default=None, metavar=("READY", "INNER", "CHUNK"),
+                   help="ready_threshold, max_inner and refill_chunk of the transport launch "
+                        "(with --coarse: the autotuner's choice without rerunning it)")
     return p.parse_args()
 
 
@@ -341,7 +344,11 @@ def run_ours(args):
     t.set_surface(d_alb)
     coarse = tuple(args.coarse) if args.coarse else COARSE
     tuned = None
-    if not args.no_autotune and not args.coarse:
+    if args.launch:
+        tuned = {"coarse": list(coarse), "ready_threshold": args.launch[0], "max_inner": args.launch[1],
+                 "refill_chunk": args.launch[2], "block_size": 256, "blocks_per_sm": 0}
+        t.set_options(**{k: v for k, v in tuned.items() if k != "coarse"})
+    elif not args.no_autotune and not args.coarse:
         # untimed: pick coarse factors and launch parameters by photons/s
         from paper_2208_05247_b300 import autotune
         tuned, _ = autotune.autotune(t, args.sza, AZ, F0, N, seed=SEED + 1000)

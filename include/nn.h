@@ -17,7 +17,10 @@
  *     ("wt") and, for the input gradient, [taps][C_in][C_out] with the taps
  *     reversed ("wd"); nn_weights_bf16 writes both.
  *   - Padding is "same" with zeros outside the volume.
- *   - All products are accumulated in FP32 by mma.sync (BF16 inputs).
+ *   - All products are accumulated in FP32 (BF16 inputs). 3x3x3 convolutions
+ *     with output channels a multiple of 16 run on tcgen05.mma with
+ *     tensor-memory accumulators and TMA-staged operands; the others, the
+ *     1x1x1 convolutions and the weight gradient use mma.sync.
  *   - Every call is ordered on `stream` (NULL = default stream) and returns
  *     NN_OK or a negative NN_E_* code; nn_last_error() gives the message.
  */
@@ -30,9 +33,23 @@
 extern "C" {
 #endif
 
-enum { NN_OK = 0, NN_E_INVAL = -1, NN_E_CUDA = -3 };
+enum { NN_OK = 0, NN_E_INVAL = -1, NN_E_CUDA = -3, NN_E_DEVICE = -4 };
 
 const char *nn_last_error(void);
+
+/* Which kernel nn_conv3d_fwd uses for 3x3x3 convolutions:
+ *   NN_CONV_AUTO     tcgen05 where supported (Cin and Cout multiples of 16),
+ *                    else mma.sync
+ *   NN_CONV_MMA_SYNC always the mma.sync kernel
+ *   NN_CONV_TCGEN05  always tcgen05; NN_E_INVAL for unsupported shapes
+ * Process-wide; returns the previous setting. */
+enum { NN_CONV_AUTO = 0, NN_CONV_MMA_SYNC = 1, NN_CONV_TCGEN05 = 2 };
+int nn_set_conv_path(int path);
+
+/* Wait for `stream`, then report and clear device-side failures of the
+ * tcgen05 kernels: NN_E_DEVICE if one of their bounded waits gave up (the
+ * outputs of that launch are then incomplete), else NN_OK. */
+int nn_status(void *stream);
 
 /* out[p][o] = act(bias[o] + sum_t sum_i in[p + off(t)][i] W[t][i][o]) with
  * act = ReLU if relu != 0. wt: BF16 [taps][Cout][Cin]. bias may be NULL.

@@ -13,7 +13,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "librt_b300.so")
-SOURCES = [os.path.join(CSRC, "rt_api.cu"), os.path.join(CSRC, "rt_noalloc.cu"), os.path.join(CSRC, "nn_kernels.cu")]
+SOURCES = [os.path.join(CSRC, "rt_api.cu"), os.path.join(CSRC, "rt_noalloc.cu"), os.path.join(CSRC, "nn_kernels.cu"),
+           os.path.join(CSRC, "conv_tc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + \
     [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
 

@@ -1,0 +1,464 @@
+// conv_tc.cu -- 3x3x3 "same" convolution on the fifth-generation tensor cores.
+//
+// The convolution is the implicit GEMM of nn_kernels.cu,
+//   out[p][o] = bias[o] + sum_t sum_i in[p + off(t)][i] * Wt[t][o][i],
+// with M = voxels, N = output channels, K = 27 taps x input channels. One CTA
+// computes a tile of 128 voxels (a Wt x Ht x Dt box of the volume) by BN
+// output channels:
+//
+//   - one thread streams the operands with TMA: for every (tap, channel chunk)
+//     the activation box shifted by the tap offset (5D tensor map over
+//     [N][D][H][W][C]; coordinates outside the volume read as zeros, which is
+//     the "same" padding) and the weight slice Wt[t][n0:n0+BN][c0:c0+CK];
+//   - one thread issues tcgen05.mma (kind::f16, BF16 operands, FP32
+//     accumulator of 128 lanes x BN columns in tensor memory), releasing each
+//     stage back to the producer with tcgen05.commit;
+//   - all four warps read the accumulator with tcgen05.ld (warp w owns tensor
+//     memory lanes 32w..32w+31 = voxel rows), add the bias, apply ReLU and
+//     write FP32 and/or BF16 channels-last outputs.
+//
+// Operand tiles are K-major with the TMA swizzle that matches the channel
+// chunk (CK = 16, 32 or 64 BF16 = 32, 64 or 128 bytes per row), so the same
+// bytes are the canonical tcgen05 shared-memory layout. Every wait on an
+// mbarrier is bounded; on time-out the CTA records an error, waits (bounded)
+// for its own copies and products in flight, frees its tensor memory and
+// returns.
+#include <cstdint>
+#include <cstdio>
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include "nn.h"
+
+namespace nn_tc {
+
+__device__ unsigned int g_status;   // bit 0: an mbarrier wait timed out
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr long long kSpinCycles = 2000000000LL;   // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of parity `parity` to complete, for at most ~1 s.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (clock64() - t0 > kSpinCycles) {
+            atomicOr(&g_status, 1u);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1,
+                                            int c2, int c3, int c4)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+        "%6, %7}], [%2];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1,
+                                            int c2)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, "
+        "%5}], [%2];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+// tcgen05 shared-memory matrix descriptor: start address, leading byte offset
+// (unused by swizzled K-major operands), stride byte offset between 8-row
+// groups, descriptor version 1 (bit 46) and the swizzle mode (bits 61-63).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t sbo_bytes, uint64_t layout)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) |
+           ((uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | (layout << 61);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// 32 lanes x 16 columns of 32-bit words from tensor memory: this thread gets
+// its lane's 16 consecutive columns.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// tensor memory is allocated in powers of two of at least 32 columns
+__host__ __device__ constexpr uint32_t tmem_cols(int bn) { return bn <= 32 ? 32u : bn <= 64 ? 64u : bn <= 128 ? 128u : 256u; }
+
+struct ConvTile {
+    int N, D, H, W, Cin, Cout;
+    int Wt, Ht, Dt;             // box of 128 voxels
+    int tw, th, td;             // tiles per axis
+    int relu;
+};
+
+// BN output channels per CTA (16..256), CK input channels per K stage
+// (16/32/64 -> 32/64/128-byte swizzle), S pipeline stages.
+template <int BN, int CK, int S>
+__global__ void __launch_bounds__(kThreads) conv3d_tc_kernel(const __grid_constant__ CUtensorMap map_x,
+                                                             const __grid_constant__ CUtensorMap map_w,
+                                                             const float *__restrict__ bias,
+                                                             __nv_bfloat16 *__restrict__ out_bf16,
+                                                             float *__restrict__ out_f32, const ConvTile P)
+{
+    constexpr uint32_t kRowBytes = CK * 2;                 // = swizzle span
+    constexpr uint32_t kABytes = 128 * kRowBytes, kBBytes = BN * kRowBytes;
+    constexpr uint32_t kStageBytes = kABytes + kBBytes;
+    constexpr uint64_t kLayout = CK == 64 ? 2 : CK == 32 ? 4 : 6;   // SWIZZLE_128B / 64B / 32B
+    constexpr uint32_t kCols = tmem_cols(BN);
+    // kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
+    // K-major, N >> 3 at bit 17, M >> 4 at bit 24 (M = 128)
+    constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | (8u << 24);
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned stage buffers (the swizzle pattern repeats every 1024 B)
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    unsigned char *gbase = smem_raw + (base - smem_u32(smem_raw));
+    __shared__ __align__(8) unsigned long long bar_full[S], bar_empty[S], bar_acc;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kchunks = P.Cin / CK, kb_total = 27 * kchunks;
+
+    // tile coordinates
+    int tile = blockIdx.x;
+    const int tx = tile % P.tw; tile /= P.tw;
+    const int ty = tile % P.th; tile /= P.th;
+    const int tz = tile % P.td; tile /= P.td;
+    const int n = tile;
+    const int w0 = tx * P.Wt, h0 = ty * P.Ht, d0 = tz * P.Dt;
+    const int n0 = blockIdx.y * BN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(smem_u32(&bar_full[s]), 1);
+            mbar_init(smem_u32(&bar_empty[s]), 1);
+        }
+        mbar_init(smem_u32(&bar_acc), 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    int issued = 0;      // producer: stages loaded
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer: TMA loads of (tap, channel chunk) stages ----
+            for (int kb = 0; kb < kb_total; ++kb) {
+                const int s = kb % S;
+                if (kb >= S && !mbar_wait(smem_u32(&bar_empty[s]), ((kb / S) - 1) & 1)) {
+                    s_abort = 1;
+                    break;
+                }
+                if (*(volatile int *)&s_abort) break;
+                const int t = kb / kchunks, c0 = (kb % kchunks) * CK;
+                const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                const uint32_t a = base + s * kStageBytes, b = a + kABytes, fb = smem_u32(&bar_full[s]);
+                mbar_expect_tx(fb, kStageBytes);
+                tma_load_5d(a, &map_x, fb, c0, w0 + dx, h0 + dy, d0 + dz, n);
+                tma_load_3d(b, &map_w, fb, c0, n0, t);
+                ++issued;
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            int kb = 0;
+            for (; kb < kb_total; ++kb) {
+                const int s = kb % S;
+                if (!mbar_wait(smem_u32(&bar_full[s]), (kb / S) & 1)) {
+                    s_abort = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a = base + s * kStageBytes, b = a + kABytes;
+#pragma unroll
+                for (int k = 0; k < CK / 16; ++k)
+                    umma_f16(tmem, umma_desc(a + 32 * k, 8 * kRowBytes, kLayout),
+                             umma_desc(b + 32 * k, 8 * kRowBytes, kLayout), kIdesc, (kb | k) != 0);
+                umma_commit(smem_u32(&bar_empty[s]));
+            }
+            // the accumulator barrier fires once every product issued so far is done
+            umma_commit(smem_u32(&bar_acc));
+        }
+        __syncwarp();
+    }
+
+    // ---- epilogue: tensor memory -> registers -> global ----
+    const bool done = mbar_wait(smem_u32(&bar_acc), 0);
+    tc_fence_after();
+    const int r = warp * 32 + lane;
+    const int w = w0 + r % P.Wt, h = h0 + (r / P.Wt) % P.Ht, d = d0 + r / (P.Wt * P.Ht);
+    const bool valid = done && !*(volatile int *)&s_abort && w < P.W && h < P.H && d < P.D;
+    const long long vox = (((long long)n * P.D + d) * P.H + h) * P.W + w;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        // every lane of the warp takes part in the load (.sync.aligned)
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+        if (!valid) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            float x = v[j] + (bias ? __ldg(bias + n0 + c + j) : 0.f);
+            v[j] = P.relu ? fmaxf(x, 0.f) : x;
+        }
+        const long long o = vox * P.Cout + n0 + c;
+        if (out_f32) {
+            float4 *dst = reinterpret_cast<float4 *>(out_f32 + o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+        if (out_bf16) {
+            uint4 pk[2];
+            uint32_t *pw = reinterpret_cast<uint32_t *>(pk);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                __nv_bfloat162 t2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                pw[q] = *reinterpret_cast<uint32_t *>(&t2);
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(out_bf16 + o);
+            dst[0] = pk[0];
+            dst[1] = pk[1];
+        }
+    }
+
+    // ---- after an abort: let this CTA's copies land before its memory goes ----
+    if (threadIdx.x == 0 && *(volatile int *)&s_abort) {
+        for (int kb = (issued > S ? issued - S : 0); kb < issued; ++kb)
+            mbar_wait(smem_u32(&bar_full[kb % S]), (kb / S) & 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+int pow2_at_least(int x, int cap)
+{
+    int p = 1;
+    while (p < x && p < cap) p <<= 1;
+    return p;
+}
+
+template <int BN, int CK, int S>
+int launch(const CUtensorMap &mx, const CUtensorMap &mw, const float *bias, __nv_bfloat16 *ob, float *of,
+           const ConvTile &P, int ntiles, int ny, cudaStream_t st, char *err, size_t errlen)
+{
+    constexpr uint32_t kStage = (128 + BN) * CK * 2;
+    constexpr int kCols = (int)tmem_cols(BN);
+    // at most 512 / kCols CTAs may hold tensor memory on one SM at a time:
+    // ask for enough shared memory that no more than that become resident
+    const int min_smem = 232448 / (512 / kCols) + 1024;
+    int smem = (int)(S * kStage + 1024);
+    if (smem < min_smem) smem = min_smem;
+    auto kern = conv3d_tc_kernel<BN, CK, S>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) {
+        kern<<<dim3((unsigned)ntiles, (unsigned)ny), kThreads, smem, st>>>(mx, mw, bias, ob, of, P);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "conv3d_tc: %s", cudaGetErrorString(e));
+        return NN_E_CUDA;
+    }
+    return NN_OK;
+}
+
+template <int CK>
+int dispatch_bn(int BN, const CUtensorMap &mx, const CUtensorMap &mw, const float *bias, __nv_bfloat16 *ob,
+                float *of, const ConvTile &P, int ntiles, int ny, cudaStream_t st, char *err, size_t errlen)
+{
+    switch (BN) {
+    case 16: return launch<16, CK, 4>(mx, mw, bias, ob, of, P, ntiles, ny, st, err, errlen);
+    case 32: return launch<32, CK, 4>(mx, mw, bias, ob, of, P, ntiles, ny, st, err, errlen);
+    case 48: return launch<48, CK, 4>(mx, mw, bias, ob, of, P, ntiles, ny, st, err, errlen);
+    case 64: return launch<64, CK, 4>(mx, mw, bias, ob, of, P, ntiles, ny, st, err, errlen);
+    case 128: return launch<128, CK, 4>(mx, mw, bias, ob, of, P, ntiles, ny, st, err, errlen);
+    case 256: return launch<256, CK, 3>(mx, mw, bias, ob, of, P, ntiles, ny, st, err, errlen);
+    default: break;
+    }
+    snprintf(err, errlen, "conv3d_tc: no kernel for %d output channels per tile", BN);
+    return NN_E_INVAL;
+}
+
+}  // namespace
+
+// Shapes the tensor-core path takes: 3x3x3 kernels with input and output
+// channel counts that are positive multiples of 16.
+bool supported(int Cin, int Cout) { return Cin > 0 && Cout > 0 && Cin % 16 == 0 && Cout % 16 == 0; }
+
+namespace {
+// Channels per K stage: the widest of 64, 32, 16 that divides Cin.
+int chunk_for(int Cin) { return Cin % 64 == 0 ? 64 : Cin % 32 == 0 ? 32 : 16; }
+// Output channels per CTA: the widest tile width that divides Cout.
+int tile_n_for(int Cout)
+{
+    for (int bn : {256, 128, 64, 48, 32, 16})
+        if (Cout % bn == 0) return bn;
+    return 0;
+}
+}  // namespace
+
+int conv3d_fwd(const void *in, const void *wt, const float *bias, void *out_bf16, float *out_f32, int N, int D, int H,
+               int W, int Cin, int Cout, int relu, cudaStream_t st, char *err, size_t errlen)
+{
+    if (!supported(Cin, Cout)) {
+        snprintf(err, errlen, "conv3d_tc: unsupported channels %d -> %d", Cin, Cout);
+        return NN_E_INVAL;
+    }
+    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(wt) | reinterpret_cast<uintptr_t>(out_bf16) |
+         reinterpret_cast<uintptr_t>(out_f32)) & 15u) {
+        snprintf(err, errlen, "conv3d_tc: buffers must be 16-byte aligned");
+        return NN_E_INVAL;
+    }
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) {
+        snprintf(err, errlen, "conv3d_tc: cuTensorMapEncodeTiled is not available");
+        return NN_E_CUDA;
+    }
+    const int CK = chunk_for(Cin);
+    const int BN = tile_n_for(Cout);
+    ConvTile P{};
+    P.N = N; P.D = D; P.H = H; P.W = W; P.Cin = Cin; P.Cout = Cout; P.relu = relu;
+    P.Wt = pow2_at_least(W, 128);
+    P.Ht = pow2_at_least(H, 128 / P.Wt);
+    P.Dt = 128 / (P.Wt * P.Ht);
+    P.tw = (W + P.Wt - 1) / P.Wt;
+    P.th = (H + P.Ht - 1) / P.Ht;
+    P.td = (D + P.Dt - 1) / P.Dt;
+    const long long ntiles = (long long)P.tw * P.th * P.td * N;
+    if (ntiles > 0x7FFFFFFFLL) {
+        snprintf(err, errlen, "conv3d_tc: volume too large");
+        return NN_E_INVAL;
+    }
+    const CUtensorMapSwizzle sw = CK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : CK == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                             : CU_TENSOR_MAP_SWIZZLE_32B;
+    CUtensorMap mx, mw;
+    const cuuint64_t gx[5] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)N};
+    const cuuint64_t sx[4] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2,
+                              (cuuint64_t)D * H * W * Cin * 2};
+    const cuuint32_t bx[5] = {(cuuint32_t)CK, (cuuint32_t)P.Wt, (cuuint32_t)P.Ht, (cuuint32_t)P.Dt, 1};
+    const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
+    CUresult r1 = enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(in), gx, sx, bx, ones,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const cuuint64_t gw[3] = {(cuuint64_t)Cin, (cuuint64_t)Cout, 27};
+    const cuuint64_t sw_[2] = {(cuuint64_t)Cin * 2, (cuuint64_t)Cout * Cin * 2};
+    const cuuint32_t bw[3] = {(cuuint32_t)CK, (cuuint32_t)BN, 1};
+    CUresult r2 = enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(wt), gw, sw_, bw, ones,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
+        snprintf(err, errlen, "conv3d_tc: tensor map encoding failed (%d, %d)", (int)r1, (int)r2);
+        return NN_E_INVAL;
+    }
+    const int ny = Cout / BN;
+    auto *ob = static_cast<__nv_bfloat16 *>(out_bf16);
+    if (CK == 64) return dispatch_bn<64>(BN, mx, mw, bias, ob, out_f32, P, (int)ntiles, ny, st, err, errlen);
+    if (CK == 32) return dispatch_bn<32>(BN, mx, mw, bias, ob, out_f32, P, (int)ntiles, ny, st, err, errlen);
+    return dispatch_bn<16>(BN, mx, mw, bias, ob, out_f32, P, (int)ntiles, ny, st, err, errlen);
+}
+
+// Read and clear the device-side status word (bit 0: an mbarrier wait timed out).
+int take_status(cudaStream_t st, unsigned *out)
+{
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_status, sizeof v, 0, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && v) {
+        const unsigned zero = 0;
+        e = cudaMemcpyToSymbolAsync(g_status, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    *out = v;
+    return e == cudaSuccess ? NN_OK : NN_E_CUDA;
+}
+
+}  // namespace nn_tc

@@ -23,7 +23,16 @@
 
 #include "nn.h"
 
+namespace nn_tc {   // conv_tc.cu
+bool supported(int Cin, int Cout);
+int conv3d_fwd(const void *in, const void *wt, const float *bias, void *out_bf16, float *out_f32, int N, int D, int H,
+               int W, int Cin, int Cout, int relu, cudaStream_t st, char *err, size_t errlen);
+int take_status(cudaStream_t st, unsigned *out);
+}  // namespace nn_tc
+
 namespace {
+
+int g_conv_path = NN_CONV_AUTO;
 
 constexpr int kBM = 128, kChunk = 16, kStageChunks = 2;
 constexpr int kRow = 24;   // bf16 per staged row: 16 used + 8 pad (48 B: conflict-free fragment reads)
@@ -534,6 +543,26 @@ extern "C" {
 
 const char *nn_last_error(void) { return g_err; }
 
+int nn_set_conv_path(int path)
+{
+    if (path != NN_CONV_AUTO && path != NN_CONV_MMA_SYNC && path != NN_CONV_TCGEN05)
+        return inval("nn_set_conv_path: unknown path");
+    const int old = g_conv_path;
+    g_conv_path = path;
+    return old;
+}
+
+int nn_status(void *stream)
+{
+    unsigned v = 0;
+    if (nn_tc::take_status((cudaStream_t)stream, &v) != NN_OK) return check_launch("nn_status");
+    if (v) {
+        snprintf(g_err, sizeof g_err, "a tcgen05 convolution gave up waiting for its operands (status %u)", v);
+        return NN_E_DEVICE;
+    }
+    return NN_OK;
+}
+
 int nn_conv3d_fwd(const void *in, const void *wt, const float *bias, void *out_bf16, float *out_f32, int N, int D,
                   int H, int W, int Cin, int Cout, int ksize, int relu, void *stream)
 {
@@ -542,6 +571,11 @@ int nn_conv3d_fwd(const void *in, const void *wt, const float *bias, void *out_b
     if (Cin % 16 != 0) return inval("nn_conv3d_fwd: Cin must be a multiple of 16");
     if (out_bf16 && Cout % 2 != 0) return inval("nn_conv3d_fwd: BF16 output needs an even Cout");
     if (ksize != 1 && ksize != 3) return inval("nn_conv3d_fwd: ksize must be 1 or 3");
+    if (ksize == 3 && g_conv_path != NN_CONV_MMA_SYNC &&
+        (g_conv_path == NN_CONV_TCGEN05 || nn_tc::supported(Cin, Cout)))
+        return nn_tc::conv3d_fwd(in, wt, bias, out_bf16, out_f32, N, D, H, W, Cin, Cout, relu, (cudaStream_t)stream,
+                                 g_err, sizeof g_err);
+    if (g_conv_path == NN_CONV_TCGEN05) return inval("nn_conv3d_fwd: the tcgen05 path takes 3x3x3 kernels only");
     const long long M = (long long)N * D * H * W;
     if (Cout >= 64) {
         dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((Cout + 63) / 64));

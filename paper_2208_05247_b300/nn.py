@@ -10,6 +10,7 @@ import ctypes
 from .rt import library
 
 NN_OK = 0
+NN_CONV_AUTO, NN_CONV_MMA_SYNC, NN_CONV_TCGEN05 = 0, 1, 2
 
 _sig_done = False
 
@@ -21,6 +22,8 @@ def _lib():
         P, i32, i64, f32, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_float, ctypes.c_double
         sig = {
             "nn_last_error": ([], ctypes.c_char_p),
+            "nn_set_conv_path": ([i32], i32),
+            "nn_status": ([P], i32),
             "nn_conv3d_fwd": ([P, P, P, P, P] + [i32] * 8 + [P], i32),
             "nn_conv3d_wgrad": ([P, P, P, P] + [i32] * 7 + [P], i32),
             "nn_relu_bwd": ([P, P, i64, P], i32),
@@ -59,6 +62,19 @@ def _p(t):
 
 def _s(stream):
     return None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+
+
+def nn_set_conv_path(path: int) -> int:
+    """Select the 3x3x3 convolution kernel (NN_CONV_*); returns the previous choice."""
+    old = _lib().nn_set_conv_path(int(path))
+    if old < 0:
+        raise NnError(_lib().nn_last_error().decode())
+    return old
+
+
+def nn_status(stream=None):
+    """Wait for the stream; raise if a tcgen05 convolution gave up waiting."""
+    _check(_lib().nn_status(_s(stream)))
 
 
 def nn_conv3d_fwd(x, wt, bias, out_bf16, out_f32, N, D, H, W, Cin, Cout, ksize, relu, stream=None):

@@ -68,9 +68,80 @@ def test_conv_forward(ksize, shape, Cin, Cout, relu):
     assert np.all(np.abs(gotb - ref) <= 2 ** -8 * np.abs(ref) + _tol(x, W, b))
 
 
+@pytest.fixture
+def conv_path():
+    """Select a convolution kernel for one test; restores the automatic choice."""
+    old = []
+
+    def use(path):
+        old.append(nn.nn_set_conv_path(path))
+
+    yield use
+    if old:
+        nn.nn_set_conv_path(old[0])
+
+
+# ragged volumes (partial tiles on every axis), batch > 1, every channel chunk
+# (16, 32, 64 input channels per stage) and output tile width
+@pytest.mark.parametrize("shape,Cin,Cout,relu", [
+    ((1, 1, 1, 1), 16, 16, False),
+    ((2, 3, 5, 7), 16, 32, True),
+    ((1, 4, 6, 9), 32, 16, False),
+    ((1, 8, 8, 8), 32, 64, False),
+    ((2, 5, 3, 20), 64, 48, True),
+    ((1, 3, 17, 33), 128, 128, False),
+    ((1, 4, 4, 130), 64, 32, True),
+    ((1, 6, 5, 4), 256, 256, False),
+    ((1, 2, 3, 16), 64, 512, True),
+    ((1, 6, 7, 8), 96, 32, True),
+    ((1, 5, 4, 6), 48, 96, False),
+    ((1, 3, 4, 5), 192, 80, False),
+])
+def test_conv_forward_tcgen05(conv_path, shape, Cin, Cout, relu):
+    """The tcgen05/TMA kernel against the FP64 reference, including borders."""
+    conv_path(nn.NN_CONV_TCGEN05)
+    rng = np.random.default_rng(Cin * 7 + Cout)
+    x = nn_ref.bf16_round(rng.normal(size=shape + (Cin,)))
+    W = nn_ref.bf16_round(rng.normal(size=(27, Cin, Cout)) / np.sqrt(27 * Cin))
+    b = rng.normal(size=Cout).astype(np.float32)
+    ref = nn_ref.conv3d(x, W, b, 3, relu)
+    wt, _ = weights_dev(W, 3)
+    vox = int(np.prod(shape))
+    out = torch.full((vox * Cout,), float("nan"), dtype=torch.float32, device="cuda")
+    outb = torch.empty(vox * Cout, dtype=torch.bfloat16, device="cuda")
+    nn.nn_conv3d_fwd(bf(x), wt, f32(b), outb, out, *shape, Cin, Cout, 3, relu)
+    nn.nn_status()
+    got = host(out).reshape(ref.shape)
+    assert np.all(np.abs(got - ref) <= _tol(x, W, b)), np.nanmax(np.abs(got - ref))
+    gotb = host(outb).reshape(ref.shape)
+    assert np.all(np.abs(gotb - ref) <= 2 ** -8 * np.abs(ref) + _tol(x, W, b))
+
+
+def test_conv_paths_agree_and_unsupported_shapes_are_refused(conv_path):
+    rng = np.random.default_rng(11)
+    shape, Cin, Cout = (1, 9, 10, 11), 32, 64
+    x = bf(nn_ref.bf16_round(rng.normal(size=shape + (Cin,))))
+    wt, _ = weights_dev(nn_ref.bf16_round(rng.normal(size=(27, Cin, Cout)) / 30.0), 3)
+    vox = int(np.prod(shape))
+    outs = []
+    for path in (nn.NN_CONV_MMA_SYNC, nn.NN_CONV_TCGEN05):
+        conv_path(path)
+        o = torch.empty(vox * Cout, dtype=torch.float32, device="cuda")
+        nn.nn_conv3d_fwd(x, wt, None, None, o, *shape, Cin, Cout, 3, False)
+        outs.append(host(o))
+    nn.nn_status()
+    assert np.allclose(outs[0], outs[1], rtol=1e-5, atol=1e-5)
+    conv_path(nn.NN_CONV_TCGEN05)
+    o = torch.empty(vox * 40, dtype=torch.float32, device="cuda")
+    with pytest.raises(nn.NnError):                 # 40 output channels: not a multiple of 16
+        nn.nn_conv3d_fwd(x, wt, None, None, o, *shape, Cin, 40, 3, False)
+
+
+@pytest.mark.parametrize("path", [nn.NN_CONV_MMA_SYNC, nn.NN_CONV_AUTO])
 @pytest.mark.parametrize("ksize,shape,Cin,Cout", [(3, (2, 3, 4, 5), 16, 32), (3, (1, 6, 5, 4), 32, 48),
                                                   (1, (1, 4, 4, 4), 32, 16)])
-def test_conv_input_and_weight_gradients(ksize, shape, Cin, Cout):
+def test_conv_input_and_weight_gradients(conv_path, path, ksize, shape, Cin, Cout):
+    conv_path(path)
     rng = np.random.default_rng(7 + Cin)
     taps = 27 if ksize == 3 else 1
     x = nn_ref.bf16_round(rng.normal(size=shape + (Cin,)))
