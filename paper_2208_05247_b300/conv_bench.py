@@ -1,0 +1,121 @@
+"""Time the denoiser's 3x3x3 convolution kernels on one layer shape.
+
+    python -m paper_2208_05247_b300.conv_bench --shape 128 128 128 --cin 32 --cout 32 [--path tcgen05]
+    python -m paper_2208_05247_b300.conv_bench --unet 128
+    python -m paper_2208_05247_b300.conv_bench --layers 128
+
+Prints one JSON line per kernel: CUDA-event time per launch (after warm-up, on
+the current stream) and the dense FLOP rate 2 * 27 * Cin * Cout * voxels / t.
+With --unet D it times the whole U-Net forward and backward at D^3 instead;
+with --layers D every 3x3x3 layer shape of the U-Net's forward pass and input
+gradients at D^3, with both kernels.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+from . import build, nn
+
+PATHS = {"mma.sync": nn.NN_CONV_MMA_SYNC, "tcgen05": nn.NN_CONV_TCGEN05, "auto": nn.NN_CONV_AUTO}
+
+
+def time_layer(shape, cin, cout, path, reps=10, warmup=3, relu=True):
+    import torch
+    vox = int(np.prod(shape))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(vox * cin, device="cuda", generator=g).to(torch.bfloat16)
+    wt = (torch.randn(27 * cin * cout, device="cuda", generator=g) * 0.05).to(torch.bfloat16)
+    out = torch.empty(vox * cout, dtype=torch.bfloat16, device="cuda")
+    old = nn.nn_set_conv_path(PATHS[path])
+    try:
+        for _ in range(warmup):
+            nn.nn_conv3d_fwd(x, wt, None, out, None, 1, *shape, cin, cout, 3, relu)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            nn.nn_conv3d_fwd(x, wt, None, out, None, 1, *shape, cin, cout, 3, relu)
+        b.record()
+        torch.cuda.synchronize()
+        nn.nn_status()
+    finally:
+        nn.nn_set_conv_path(old)
+    ms = a.elapsed_time(b) / reps
+    return {"kernel": path, "shape": list(shape), "cin": cin, "cout": cout, "us": 1e3 * ms,
+            "tflops": 2.0 * 27 * cin * cout * vox / (ms * 1e-3) / 1e12}
+
+
+def time_unet(d, path, reps=3):
+    import torch
+    from . import denoise
+    net = denoise.UNet(seed=0)
+    shape = (d, d, d)
+    x = torch.randn(d ** 3 * denoise.CIN, device="cuda").to(torch.bfloat16)
+    old = nn.nn_set_conv_path(PATHS[path])
+    try:
+        for _ in range(2):
+            net.forward(x, shape)
+            net.backward(x, shape)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fwd = bwd = 0.0
+        for _ in range(reps):
+            ev[0].record()
+            net.forward(x, shape)
+            ev[1].record()
+            net.backward(x, shape)
+            ev[2].record()
+            torch.cuda.synchronize()
+            fwd += ev[0].elapsed_time(ev[1])
+            bwd += ev[1].elapsed_time(ev[2])
+        nn.nn_status()
+    finally:
+        nn.nn_set_conv_path(old)
+    return {"kernel": path, "unet": d, "forward_ms": fwd / reps, "backward_ms": bwd / reps,
+            "forward_tflops": net.flops(shape) / (fwd / reps * 1e-3) / 1e12}
+
+
+def unet_layers(d):
+    """(shape, Cin, Cout) of the U-Net's 3x3x3 forward convolutions and input
+    gradients at d^3 (an input gradient is a convolution with Cin and Cout swapped)."""
+    from . import denoise
+    c0, c1, c2, c3 = denoise.LEVELS
+    fwd = [(0, denoise.CIN, c0), (0, c0, c0), (1, c0, c1), (1, c1, c1), (2, c1, c2), (2, c2, c2), (3, c2, c3),
+           (3, c3, c3), (2, c3 + c2, c2), (1, c2 + c1, c1), (0, c1 + c0, c0)]
+    out, seen = [], set()
+    for lvl, a, b in fwd + [(lvl, b, a) for lvl, a, b in fwd]:
+        key = (lvl, a, b)
+        if key not in seen:
+            seen.add(key)
+            out.append(((d >> lvl,) * 3, a, b))
+    return out
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--shape", type=int, nargs=3, default=(128, 128, 128), help="D H W")
+    p.add_argument("--cin", type=int, default=32)
+    p.add_argument("--cout", type=int, default=32)
+    p.add_argument("--path", choices=sorted(PATHS), default=None, help="one kernel (default: mma.sync and tcgen05)")
+    p.add_argument("--reps", type=int, default=10)
+    p.add_argument("--unet", type=int, default=0, help="time the whole U-Net at this edge length instead")
+    p.add_argument("--layers", type=int, default=0, help="time every U-Net layer shape at this edge length")
+    a = p.parse_args(argv)
+    build.build()
+    if a.layers:
+        for shape, cin, cout in unet_layers(a.layers):
+            for path in ("mma.sync", "tcgen05"):
+                print(json.dumps(time_layer(shape, cin, cout, path, reps=a.reps)), flush=True)
+        return
+    paths = [a.path] if a.path else ["mma.sync", "tcgen05" if not a.unet else "auto"]
+    for path in paths:
+        if a.unet:
+            r = time_unet(a.unet, path)
+        else:
+            r = time_layer(tuple(a.shape), a.cin, a.cout, path, reps=a.reps)
+        print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main()

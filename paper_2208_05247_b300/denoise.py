@@ -255,12 +255,25 @@ def make_scenes(seeds, nx, ny, nz, workers=8):
 
 
 class FieldTracer:
-    """Traces scenes of one shape into device FP64 fields (handle reused)."""
+    """Traces scenes of one shape into device FP64 fields (handle reused).
 
-    def __init__(self, shape, dx=50.0, dy=50.0, dz=25.0, stream=None):
+    spectral=False traces one quadrature point (TOA flux 1000 W m^-2).
+    spectral=True traces the broadband field the paper's heating rates and GHI
+    are: all quadrature points of `scenes.gpoint_table()` (gas extinction scale
+    and TOA flux per point, fluxes summing to 1000 W m^-2) in one batched launch,
+    `ppc` photons per column per quadrature point on average, split in
+    proportion to each point's energy (Sec. 2.3 traces every point
+    independently; N_sample counts rays per column per point, Sec. 2.4).
+    """
+
+    def __init__(self, shape, dx=50.0, dy=50.0, dz=25.0, stream=None, spectral=False):
         torch = _torch()
         nz, ny, nx = shape
         self.t = rt.Tracer(nx, ny, nz, dx, dy, dz, stream=stream)
+        self.spectral = spectral
+        if spectral:
+            self.t.set_options(batch_optics=1)
+            self.gas_scale, self.gflux = scenes.gpoint_table()
         self.shape = shape
         self.dz = dz
         dev = "cuda"
@@ -285,7 +298,12 @@ class FieldTracer:
                    torch.empty(self.ncol, dtype=torch.float64, device="cuda"),
                    torch.empty(self.ncol, dtype=torch.float64, device="cuda"))
         self.t.reset()
-        self.t.trace(sza, 0.0, 1000.0, ppc * self.ncol, seed)
+        if self.spectral:
+            jobs = [dict(scene=self.t, sza_deg=sza, toa_flux=float(f), gas_scale=float(g))
+                    for g, f in zip(self.gas_scale, self.gflux)]
+            rt.rt_trace_batch(jobs, total_photons=ppc * len(jobs) * self.ncol, seed=seed)
+        else:
+            self.t.trace(sza, 0.0, 1000.0, ppc * self.ncol, seed)
         rt.rt_fields(self.t.h, self.ncell, self.ncol, out[0], out[1], out[2], None)
         return out
 
@@ -308,11 +326,11 @@ class FieldTracer:
 SZAS = (0.0, 30.0, 60.0)
 
 
-def make_pairs(seeds, shape, lo_ppc=4, hi_ppc=1024, workers=8):
+def make_pairs(seeds, shape, lo_ppc=4, hi_ppc=1024, workers=8, spectral=False):
     """Training pairs (low-photon input, correction target) traced on the GPU."""
     nz, ny, nx = shape
     scs = make_scenes(seeds, nx, ny, nz, workers)
-    ft = FieldTracer(shape)
+    ft = FieldTracer(shape, spectral=spectral)
     out = []
     for seed, sc in zip(seeds, scs):
         sza = SZAS[seed % 3]
@@ -393,7 +411,7 @@ def _errors(fields, truth, hf, shape):
 
 
 def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), truth_ppc=16384, workers=8,
-             repeats=3):
+             repeats=3, spectral=False):
     """Time-to-RMSE of denoised low-photon runs against the plain tracer.
 
     For each held-out scene: a truth run at `truth_ppc`, plain runs at each
@@ -407,7 +425,7 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), trut
     torch = _torch()
     nz, ny, nx = shape
     scs = make_scenes(seeds, nx, ny, nz, workers)
-    ft = FieldTracer(shape)
+    ft = FieldTracer(shape, spectral=spectral)
     hf = heating_factor(nz, ft.dz)
     stream = torch.cuda.current_stream()
     acc = {p: [0.0, 0.0, 0.0] for p in plain_ppc}
@@ -448,7 +466,8 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), trut
     n = len(seeds)
     plain = {p: {"rmse_ghi": math.sqrt(v[0] / n), "rmse_hr": math.sqrt(v[1] / n), "ms": v[2] / n}
              for p, v in acc.items()}
-    res = {"shape": shape, "scenes": n, "truth_ppc": truth_ppc, "plain": plain,
+    res = {"shape": shape, "scenes": n, "truth_ppc": truth_ppc, "spectral": spectral,
+           "quadrature_points": len(ft.gflux) if spectral else 1, "plain": plain,
            "denoised": {"ppc": lo_ppc, "rmse_ghi": math.sqrt(den[0] / n), "rmse_hr": math.sqrt(den[1] / n),
                         "ms": den[2] / n},
            "noisy_input": {"rmse_ghi": math.sqrt(noisy[0] / n), "rmse_hr": math.sqrt(noisy[1] / n)}}
@@ -478,12 +497,17 @@ def main(argv=None):
     p.add_argument("--lr", type=float, default=1e-3)
     p.add_argument("--shape", type=int, nargs=3, default=(128, 128, 128), help="nz ny nx")
     p.add_argument("--truth-ppc", type=int, default=16384)
+    p.add_argument("--hi-ppc", type=int, default=1024, help="photons/column of the training targets")
+    p.add_argument("--plain-ppc", type=int, nargs="+", default=(4, 16, 64, 256, 1024))
+    p.add_argument("--spectral", action="store_true",
+                   help="broadband fields: all quadrature points of the g-point table in one batched launch")
     p.add_argument("--workers", type=int, default=16)
     p.add_argument("--out", default=None, help="write the result JSON here")
     a = p.parse_args(argv)
     shape = tuple(a.shape)
     t0 = time.time()
-    pairs = make_pairs(list(range(1000, 1000 + a.train)), shape, workers=a.workers)
+    pairs = make_pairs(list(range(1000, 1000 + a.train)), shape, hi_ppc=a.hi_ppc, workers=a.workers,
+                       spectral=a.spectral)
     t_pairs = time.time() - t0
     net = UNet(seed=0)
     t0 = time.time()
@@ -491,8 +515,8 @@ def main(argv=None):
     t_train = time.time() - t0
     del pairs
     res = evaluate(net, list(range(1000 + a.train, 1000 + a.train + a.eval)), shape, truth_ppc=a.truth_ppc,
-                   workers=a.workers)
-    res.update({"train_scenes": a.train, "epochs": a.epochs, "pairs_s": t_pairs, "train_s": t_train,
+                   workers=a.workers, plain_ppc=tuple(a.plain_ppc), spectral=a.spectral)
+    res.update({"train_scenes": a.train, "epochs": a.epochs, "hi_ppc": a.hi_ppc, "pairs_s": t_pairs, "train_s": t_train,
                 "loss_first": losses[0][1], "loss_last": losses[-1][1], "params": net.n_params(),
                 "forward_gflop": net.flops(shape) / 1e9})
     print(json.dumps(res), flush=True)
