@@ -62,7 +62,7 @@ def parse():
     p.add_argument("--no-denoise", action="store_true", help="skip the denoised-vs-plain time-to-RMSE leg")
     p.add_argument("--no-coupled", action="store_true", help="skip the graph-replay coupled-step leg")
     p.add_argument("--no-birth", action="store_true", help="skip the Sobol-vs-Philox start position leg")
-    p.add_argument("--denoise-train", type=int, default=64, help="training scenes of the denoiser leg")
+    p.add_argument("--denoise-train", type=int, default=256, help="training scenes of the denoiser leg")
     p.add_argument("--no-autotune", action="store_true",
                    help="use the default launch parameters and the --coarse grid")
     p.add_argument("--coarse", type=int, nargs=3, default=None,
@@ -209,26 +209,23 @@ def run_reference(args):
 # ---- denoised vs plain: wall time to a target RMS error ----------------------------------
 
 def denoise_leg(args):
-    """Train the 3D U-Net on broadband tracer pairs (all 112 quadrature points
-    in one batched launch; 4 vs 256 photons/column per point, 128^3 cumulus
-    scenes) and time denoised 4-photon runs against the plain tracer at
-    matched RMS error of GHI and heating rate on held-out scenes."""
+    """Train the 3D U-Net on tracer pairs (4 vs 1024 photons/column of one
+    quadrature point, 128^3 cumulus scenes) and time denoised 4-photon runs
+    against the plain tracer at matched RMS error of GHI and heating rate on
+    held-out scenes."""
     from paper_2208_05247_b300 import denoise
     shape = (128, 128, 128)
     t0 = time.time()
-    pairs = denoise.make_pairs(list(range(1000, 1000 + args.denoise_train)), shape, hi_ppc=256,
-                               workers=os.cpu_count() or 8, spectral=True)
+    pairs = denoise.make_pairs(list(range(1000, 1000 + args.denoise_train)), shape, workers=os.cpu_count() or 8)
     t_pairs = time.time() - t0
     net = denoise.UNet(seed=0)
     t0 = time.time()
     losses = denoise.train(net, pairs, epochs=4, lr=1e-3)
     t_train = time.time() - t0
     del pairs
-    res = denoise.evaluate(net, list(range(1512, 1520)), shape, plain_ppc=(4, 16, 64, 256), truth_ppc=2048,
-                           workers=os.cpu_count() or 8, spectral=True)
-    return {"workload": "broadband (112 quadrature points, one batched launch) on cumulus 128x128x128 "
-                        "(dx=dy=50 m, dz=25 m), sza 0/30/60, held-out seeds 1512-1519, truth 2048 photons/column "
-                        "per point, training targets 256",
+    res = denoise.evaluate(net, list(range(1512, 1520)), shape, truth_ppc=4096, workers=os.cpu_count() or 8)
+    return {"workload": "one quadrature point on cumulus 128x128x128 (dx=dy=50 m, dz=25 m), sza 0/30/60, "
+                        "held-out seeds 1512-1519, truth 4096 photons/column",
             "training": {"scenes": args.denoise_train, "epochs": 4, "pairs_s": t_pairs, "train_s": t_train,
                          "loss_first": losses[0][1], "loss_last": losses[-1][1]},
             "plain": res["plain"], "denoised": res["denoised"], "noisy_input": res["noisy_input"],

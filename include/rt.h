@@ -85,6 +85,18 @@ enum { RT_TALLY_FP64 = 0, RT_TALLY_FP32 = 1 };
  * stratify its area, and each start point is still uniform. */
 enum { RT_BIRTH_PHILOX = 0, RT_BIRTH_SOBOL = 1 };
 
+/* Order in which a launch starts its photons. A launch lasts as long as its
+ * longest photon history, typically a random walk through thick cloud.
+ * RT_SCHEDULE_IDS starts photons in id order. RT_SCHEDULE_THICK_FIRST starts
+ * all photons of one column in turn (a warp's lanes then share a column and
+ * follow similar paths), columns in decreasing majorant optical depth, so the
+ * long histories overlap the rest of the launch. It is used by single-scene
+ * launches of whole rounds (photon range start and count multiples of nx*ny)
+ * with at least 64 photons per column; other launches use id order. A
+ * photon's history depends only on its id, so results are the same either way
+ * up to the order of FP64 additions. */
+enum { RT_SCHEDULE_IDS = 0, RT_SCHEDULE_THICK_FIRST = 1 };
+
 typedef struct {
     int block_size;              /* threads per block of the transport kernel; 0 = 256 */
     int blocks_per_sm;           /* resident blocks per SM; 0 = as many as fit */
@@ -99,6 +111,8 @@ typedef struct {
                                     rt_build_accel builds the factored majorant, as
                                     rt_trace_batch needs (+20 B per cell); 0 (default): not */
     int birth;                   /* RT_BIRTH_*; default RT_BIRTH_PHILOX */
+    int schedule;                /* RT_SCHEDULE_*; applies from the next rt_build_accel;
+                                    default RT_SCHEDULE_THICK_FIRST */
 } rt_options;
 
 typedef struct {

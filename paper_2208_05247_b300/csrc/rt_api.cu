@@ -41,6 +41,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr uint32_t kDefaultMaxSteps = 10000000u;
 constexpr int kDefaultReadyThreshold = 16;
 constexpr int kDefaultMaxInner = 16;
+constexpr uint64_t kOrderMinPhotonsPerColumn = 64;
 
 template <typename T>
 int dev_alloc(T **p, size_t n)
@@ -91,6 +92,12 @@ struct rt_scene {
     float *kmax = nullptr;
     int cx = 0, cy = 0, cz = 0, NX = 0, NY = 0, NZ = 0;
     size_t kmax_cap = 0;
+
+    // launch order of the columns (RT_SCHEDULE_THICK_FIRST) and its sort keys
+    uint32_t *order = nullptr;
+    unsigned char *okey = nullptr;
+    size_t okey_cap = 0;
+    bool order_ok = false;
 
     // staging for host-side inputs (allocated on first host upload)
     float *stage = nullptr;
@@ -254,6 +261,53 @@ int fields_split_impl(rt_handle h, T *base, double *abs_dir, double *abs_dif, do
     return RT_OK;
 }
 
+// Buffers of the launch order: the fine-column permutation and one key per
+// coarse column.
+int ensure_order(rt_handle h)
+{
+    int rc;
+    if (!h->order && (rc = dev_alloc(&h->order, h->ncol))) return rc;
+    const size_t ncc = (size_t)h->NX * h->NY;
+    if (ncc > h->okey_cap) {
+        cudaFree(h->okey);
+        h->okey = nullptr;
+        h->okey_cap = 0;
+        if ((rc = dev_alloc(&h->okey, ncc))) return rc;
+        h->okey_cap = ncc;
+    }
+    return RT_OK;
+}
+
+// Columns in decreasing majorant optical depth, from the current majorant grid.
+int order_columns(rt_handle h, cudaStream_t st)
+{
+    rt::column_keys<<<grid_for((size_t)h->NX * h->NY), 256, 0, st>>>(h->kmax, h->NX, h->NY, h->NZ,
+                                                                      (float)(h->cz * h->dz),
+                                                                      (float)(h->nz * h->dz), h->okey);
+    RT_CUDA(cudaGetLastError());
+    rt::order_columns<<<1, 1024, 0, st>>>(h->okey, h->nx, h->ny, h->cx, h->cy, h->NX, h->order);
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+// Photon order of a single-scene launch of ids [begin, begin + count) out of
+// `total`: columns thickest first when the launch covers whole rounds.
+template <typename T>
+void set_order(rt_handle h, rt::TraceArgs<T> &A, uint64_t begin, uint64_t count)
+{
+    A.order = nullptr;
+    if (!h->order_ok || h->opt.schedule != RT_SCHEDULE_THICK_FIRST) return;
+    if (begin % h->ncol != 0 || count % h->ncol != 0 || count / h->ncol > 0xFFFFFFFFull) return;
+    // Below ~64 photons per column the longest history alone sets the launch
+    // time, and warps filled with the photons of a few thick columns diverge
+    // more than mixed ones: on the 256 x 256 x 128 cumulus scene the ordered
+    // launch was 19 % slower at 4 photons/column, 2-7 % faster from 64 up.
+    if (count / h->ncol < kOrderMinPhotonsPerColumn) return;
+    A.order = h->order;
+    A.order_ppc = (uint32_t)(count / h->ncol);
+    A.order_k0 = begin / h->ncol;
+}
+
 int device_status(rt_handle h)
 {
     int st = 0;
@@ -332,6 +386,7 @@ int launch_trace(rt_handle h, T *base, double sza, double az, double toa_flux, d
     A.count = count;
     A.scr = h->scr;
     fill_launch(h, A);
+    set_order(h, A, begin, count);
 
     const int block = h->opt.block_size > 0 ? h->opt.block_size : 256;
     int bps = h->opt.blocks_per_sm;
@@ -427,6 +482,10 @@ int record_step(rt_handle h, const rt_step_desc *d, rt_step s, cudaStream_t cs, 
     rt::build_majorant<<<grid_for(nc), 256, 0, cs>>>(h->rec, h->kmax, h->nx, h->ny, h->nz, h->cx, h->cy, h->cz,
                                                      h->NX, h->NY, h->NZ);
     RT_CUDA(cudaGetLastError());
+    if (h->order_ok) {
+        int rc = order_columns(h, cs);
+        if (rc) return rc;
+    }
     rt::step_gate<<<1, 32, 0, cs>>>(h->bad, h->scr);
     RT_CUDA(cudaGetLastError());
 
@@ -436,6 +495,7 @@ int record_step(rt_handle h, const rt_step_desc *d, rt_step s, cudaStream_t cs, 
     A.count = d->photons;
     A.scr = h->scr;
     fill_launch(h, A);
+    set_order(h, A, 0, d->photons);
     if constexpr (std::is_same<T, double>::value) s->a64 = A;
     else s->a32 = A;
     const int block = h->opt.block_size > 0 ? h->opt.block_size : 256;
@@ -541,6 +601,7 @@ rt_handle rt_create(int nx, int ny, int nz, double dx, double dy, double dz)
     h->opt.max_inner = kDefaultMaxInner;
     h->opt.pcld_mode = RT_PCLD_SCATTERING;
     h->opt.tally_precision = RT_TALLY_FP64;
+    h->opt.schedule = RT_SCHEDULE_THICK_FIRST;
     return h;
 }
 
@@ -558,6 +619,8 @@ int rt_destroy(rt_handle h)
     cudaFree(h->desc);
     cudaFree(h->alb);
     cudaFree(h->kmax);
+    cudaFree(h->order);
+    cudaFree(h->okey);
     cudaFree(h->stage);
     cudaFree(h->t64);
     cudaFree(h->t32);
@@ -601,6 +664,8 @@ int rt_set_options(rt_handle h, const rt_options *o)
         return fail(RT_E_INVAL, "rt_set_options: unknown tally_precision");
     if (o->birth != RT_BIRTH_PHILOX && o->birth != RT_BIRTH_SOBOL)
         return fail(RT_E_INVAL, "rt_set_options: unknown birth mode");
+    if (o->schedule != RT_SCHEDULE_IDS && o->schedule != RT_SCHEDULE_THICK_FIRST)
+        return fail(RT_E_INVAL, "rt_set_options: unknown schedule");
     if (o->blocks_per_sm > 0) {
         int fit = 0;
         const int block = o->block_size > 0 ? o->block_size : 256;
@@ -743,6 +808,12 @@ int rt_build_accel(rt_handle h, int cx, int cy, int cz)
     rt::build_majorant<<<grid_for(nc), 256, 0, h->stream>>>(h->rec, h->kmax, h->nx, h->ny, h->nz, cx, cy, cz,
                                                             NX, NY, NZ);
     RT_CUDA(cudaGetLastError());
+    h->order_ok = false;
+    if (h->opt.schedule == RT_SCHEDULE_THICK_FIRST) {
+        if ((rc = ensure_order(h))) return rc;
+        if ((rc = order_columns(h, h->stream))) return rc;
+        h->order_ok = true;
+    }
     h->accel2_ok = false;
     if (h->split_ok) {
         if (nc > h->kmax2_cap) {

@@ -91,6 +91,12 @@ struct TraceArgs {
     uint32_t chunk;
     int ready_threshold;           // lanes that must be ready before an interaction sweep
     int max_inner;                 // bound on face-crossing sweeps per interaction sweep
+    // single-scene launches of whole photon rounds: queue index q takes photon
+    // (order_k0 + q mod order_ppc) * ncol + order[q div order_ppc], i.e. all
+    // photons of one column in turn, columns in the order of `order`
+    const uint32_t *order;
+    uint32_t order_ppc;
+    unsigned long long order_k0;
 };
 
 // ---------------------------------------------------------------------------
@@ -171,6 +177,78 @@ __global__ void build_majorant(const float4 *__restrict__ rec, float *__restrict
                 }
             }
         kmax[q] = m;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launch order. A launch lasts as long as its longest photon history, and the
+// longest histories are random walks through thick cloud. Starting the photons
+// of the optically thickest columns first lets those histories overlap with
+// the rest of the launch instead of trailing it. A photon's history depends
+// only on its id, so the order changes no result (FP64 atomic rounding aside).
+// ---------------------------------------------------------------------------
+constexpr int kOrderKeys = 256;
+
+// Key of each coarse column: 255 - min(255, 16 log2(1 + tau)), with tau the
+// majorant optical depth of the column (sum of k_max times coarse cell height).
+// Thick columns get low keys.
+__global__ void column_keys(const float *__restrict__ kmax, int NX, int NY, int NZ, float cdz, float H,
+                            unsigned char *__restrict__ key)
+{
+    const int n = NX * NY;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        float tau = 0.f;
+        for (int K = 0; K < NZ; ++K)
+            tau = fmaf(__ldg(kmax + (size_t)K * n + q), fminf(cdz, H - (float)K * cdz), tau);
+        key[q] = (unsigned char)(255 - min(255, (int)(16.f * log2f(1.f + tau))));
+    }
+}
+
+// One block of 1024 threads: counting sort of the fine columns by the key of
+// their coarse column; order[r] is the fine column of rank r. Columns with
+// equal keys come in an unspecified order. Most columns share a few keys
+// (clear sky), so lanes with equal keys add to a counter once per warp.
+// Slot for this lane's key k in counter array cnt: lanes of the warp with equal
+// keys share one atomic. Every lane of the warp must call it; k >= kOrderKeys
+// marks a lane without a column.
+__device__ __forceinline__ unsigned int warp_claim(unsigned int *cnt, unsigned int k)
+{
+    const unsigned int lane = threadIdx.x & 31u;
+    const unsigned int peers = __match_any_sync(0xffffffffu, k);
+    const int leader = __ffs(peers) - 1;
+    unsigned int base = 0;
+    if ((int)lane == leader && k < (unsigned int)kOrderKeys) base = atomicAdd(&cnt[k], (unsigned int)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+__global__ void __launch_bounds__(1024) order_columns(const unsigned char *__restrict__ key, int nx, int ny, int cx,
+                                                      int cy, int NX, uint32_t *__restrict__ order)
+{
+    __shared__ unsigned int cnt[kOrderKeys];
+    const int ncol = nx * ny;
+    const int rounds = (ncol + (int)blockDim.x - 1) / (int)blockDim.x;   // equal for every thread
+    for (int b = threadIdx.x; b < kOrderKeys; b += blockDim.x) cnt[b] = 0;
+    __syncthreads();
+    for (int r = 0; r < rounds; ++r) {
+        const int c = r * (int)blockDim.x + (int)threadIdx.x;
+        warp_claim(cnt, c < ncol ? key[(c / nx / cy) * NX + (c % nx) / cx] : (unsigned int)kOrderKeys);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int run = 0;
+        for (int b = 0; b < kOrderKeys; ++b) {
+            const unsigned int v = cnt[b];
+            cnt[b] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    for (int r = 0; r < rounds; ++r) {
+        const int c = r * (int)blockDim.x + (int)threadIdx.x;
+        const unsigned int k = c < ncol ? key[(c / nx / cy) * NX + (c % nx) / cx] : (unsigned int)kOrderKeys;
+        const unsigned int pos = warp_claim(cnt, k);
+        if (c < ncol) order[pos] = (uint32_t)c;
     }
 }
 
@@ -418,7 +496,13 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
                     sid = s_jobs[jid].scene;
                 }
                 // ---- a3: birth at the domain top, along the sun beam ----
-                gid = RT_JB(id_begin) + (mine - RT_JB(start));
+                if (!BATCH && A.order) {
+                    const unsigned long long cr =
+                        (mine >> 32) ? mine / A.order_ppc : (unsigned long long)((uint32_t)mine / A.order_ppc);
+                    gid = (A.order_k0 + (mine - cr * A.order_ppc)) * RT_JB(ncol) + __ldg(A.order + cr);
+                } else {
+                    gid = RT_JB(id_begin) + (mine - RT_JB(start));
+                }
                 const unsigned long long ncol = RT_JB(ncol);
                 const unsigned col = (gid >> 32) ? (unsigned)(gid % ncol) : (uint32_t)gid % (uint32_t)ncol;
                 const int ci = (int)(col % (unsigned)RT_SC(nx)), cj = (int)(col / (unsigned)RT_SC(nx));

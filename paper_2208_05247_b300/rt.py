@@ -21,6 +21,7 @@ RT_TALLY_FP64, RT_TALLY_FP32 = 0, 1
 RT_OPTICS_SPLIT, RT_OPTICS_TOTAL = 0, 1
 RT_HOM_SURFACE, RT_HOM_HEATING = 1, 2
 RT_BIRTH_PHILOX, RT_BIRTH_SOBOL = 0, 1
+RT_SCHEDULE_IDS, RT_SCHEDULE_THICK_FIRST = 0, 1
 
 _ERRNAMES = {RT_E_INVAL: "RT_E_INVAL", RT_E_STATE: "RT_E_STATE", RT_E_CUDA: "RT_E_CUDA",
              RT_E_OOM: "RT_E_OOM", RT_E_BUDGET: "RT_E_BUDGET"}
@@ -37,7 +38,7 @@ class rt_options(ctypes.Structure):
                 ("refill_chunk", ctypes.c_int), ("max_steps", ctypes.c_uint32),
                 ("pcld_mode", ctypes.c_int), ("tally_precision", ctypes.c_int),
                 ("ready_threshold", ctypes.c_int), ("max_inner", ctypes.c_int),
-                ("batch_optics", ctypes.c_int), ("birth", ctypes.c_int)]
+                ("batch_optics", ctypes.c_int), ("birth", ctypes.c_int), ("schedule", ctypes.c_int)]
 
 
 class rt_job(ctypes.Structure):
