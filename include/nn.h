@@ -38,12 +38,20 @@ enum { NN_OK = 0, NN_E_INVAL = -1, NN_E_CUDA = -3, NN_E_DEVICE = -4 };
 const char *nn_last_error(void);
 
 /* Which kernel nn_conv3d_fwd uses for 3x3x3 convolutions:
- *   NN_CONV_AUTO     tcgen05 where supported (Cin and Cout multiples of 16),
- *                    else mma.sync
- *   NN_CONV_MMA_SYNC always the mma.sync kernel
- *   NN_CONV_TCGEN05  always tcgen05; NN_E_INVAL for unsupported shapes
- * Process-wide; returns the previous setting. */
-enum { NN_CONV_AUTO = 0, NN_CONV_MMA_SYNC = 1, NN_CONV_TCGEN05 = 2 };
+ *   NN_CONV_AUTO         tcgen05 where supported (Cin and Cout multiples of 16),
+ *                        else mma.sync
+ *   NN_CONV_MMA_SYNC     always the mma.sync kernel
+ *   NN_CONV_TCGEN05      always tcgen05 (NN_E_INVAL for unsupported shapes): the
+ *                        halo-tiled persistent kernel when its shared memory
+ *                        fits (at most 64 output channels per tile), else the
+ *                        per-tap kernel
+ *   NN_CONV_TCGEN05_TAP  always the per-tap tcgen05 kernel
+ *   NN_CONV_TCGEN05_HALO always the halo-tiled kernel; NN_E_INVAL where it does
+ *                        not fit
+ * 1x1x1 convolutions always use the mma.sync kernel. Process-wide; returns the
+ * previous setting. */
+enum { NN_CONV_AUTO = 0, NN_CONV_MMA_SYNC = 1, NN_CONV_TCGEN05 = 2, NN_CONV_TCGEN05_TAP = 3,
+       NN_CONV_TCGEN05_HALO = 4 };
 int nn_set_conv_path(int path);
 
 /* Wait for `stream`, then report and clear device-side failures of the

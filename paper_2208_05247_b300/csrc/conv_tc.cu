@@ -23,6 +23,7 @@
 // mbarrier is bounded; on time-out the CTA records an error, waits (bounded)
 // for its own copies and products in flight, frees its tensor memory and
 // returns.
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 
@@ -37,9 +38,24 @@ namespace nn_tc {
 
 __device__ unsigned int g_status;   // bit 0: an mbarrier wait timed out
 
+// kernel variants of conv3d_fwd (0: the halo kernel where it fits, else per tap)
+constexpr int kVariantTap = 1, kVariantHalo = 2;
+
 namespace {
 
 constexpr int kThreads = 128;
+constexpr uint32_t kMaxDynSmem = 232448;   // opt-in shared memory per block (227 KB)
+
+// Let a kernel use all the opt-in shared memory its static shared memory leaves.
+cudaError_t allow_max_smem(const void *kern)
+{
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(kMaxDynSmem - (uint32_t)fa.sharedSizeBytes));
+}
+
 constexpr long long kSpinCycles = 2000000000LL;   // ~1 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -305,6 +321,251 @@ __global__ void __launch_bounds__(kThreads) conv3d_tc_kernel(const __grid_consta
     }
 }
 
+// ---------------------------------------------------------------------------
+// Halo-tiled persistent variant for narrow layers (at most 64 output channels
+// per tile). The per-tap kernel above reloads a 128-row box from L2 for each
+// of the 27 taps, which bounds the 32-channel layers by L2 throughput. Here a
+// tile is 8 (x) x 16 (y) voxels of one z slice, and one TMA box of
+// 8 x 18 x 3 voxels (the tile's y and z halo) per (x offset, channel chunk)
+// serves nine taps: tap (dy, dz) reads the 128 rows that start
+// 8 (dy + 1) + 144 (dz + 1) rows into the box, a multiple of the 8-row swizzle
+// atom, so the tcgen05 descriptor just starts there. The weights of the nine
+// taps come as one 4D box per stage, or stay resident in shared memory for the
+// whole launch when they fit (RESW). The CTA is persistent (one per SM) and
+// double-buffers the accumulator in tensor memory, so the epilogue of one tile
+// overlaps the products of the next. Warps 0-3 drain the accumulator, warp 4
+// loads, warp 5 issues the products and owns the tensor memory.
+// ---------------------------------------------------------------------------
+constexpr int kHaloW = 8, kHaloH = 16;                    // tile: 8 x 16 voxels = 128 rows
+constexpr int kHaloRows = kHaloW * (kHaloH + 2) * 3;       // 432 rows per halo box
+constexpr int kHaloThreads = 192;
+
+struct HaloTile {
+    int N, D, H, W, Cin, Cout;
+    int tw, th, ntn;            // tiles along x and y; output-channel tiles
+    long long ntiles;           // ntn * tw * th * D * N
+    int relu;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1,
+                                            int c2, int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+        "%6}], [%2];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+// Bytes of dynamic shared memory the halo kernel needs (plus alignment slack).
+__host__ __device__ constexpr uint32_t halo_stage_bytes(int BN, int CK, bool resw)
+{
+    return (uint32_t)(kHaloRows * CK * 2) + (resw ? 0u : (uint32_t)(9 * BN * CK * 2));
+}
+
+template <int BN, int CK, int S, bool RESW>
+__global__ void __launch_bounds__(kHaloThreads, 1) conv3d_tc_halo_kernel(
+    const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w,
+    const float *__restrict__ bias, __nv_bfloat16 *__restrict__ out_bf16, float *__restrict__ out_f32,
+    const HaloTile P)
+{
+    constexpr uint32_t kRow = CK * 2;
+    constexpr uint32_t kA = kHaloRows * kRow;
+    constexpr uint32_t kBtap = BN * kRow;                     // one tap's weight tile
+    constexpr uint32_t kStage = halo_stage_bytes(BN, CK, RESW);
+    constexpr uint64_t kLayout = CK == 64 ? 2 : CK == 32 ? 4 : 6;
+    constexpr uint32_t kCols = tmem_cols(BN);
+    constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | (8u << 24);
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const uint32_t wres = base + S * kStage;                  // resident weights (RESW)
+    __shared__ __align__(8) unsigned long long bar_full[S], bar_empty[S], bar_accf[2], bar_acce[2], bar_w,
+        bar_drain;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kchunks = P.Cin / CK, KB = 3 * kchunks;
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < S; ++q) {
+            mbar_init(smem_u32(&bar_full[q]), 1);
+            mbar_init(smem_u32(&bar_empty[q]), 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(smem_u32(&bar_accf[q]), 1);
+            mbar_init(smem_u32(&bar_acce[q]), 4);   // one arrival per epilogue warp
+        }
+        mbar_init(smem_u32(&bar_w), 1);
+        mbar_init(smem_u32(&bar_drain), 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(2 * kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    // tile -> (output-channel tile, x tile, y tile, z slice, sample); the
+    // channel tile varies fastest so concurrent CTAs share halo boxes in L2
+    auto decode = [&](long long tile, int &tn, int &w0, int &h0, int &d, int &n) {
+        tn = (int)(tile % P.ntn); tile /= P.ntn;
+        w0 = (int)(tile % P.tw) * kHaloW; tile /= P.tw;
+        h0 = (int)(tile % P.th) * kHaloH; tile /= P.th;
+        d = (int)(tile % P.D);
+        n = (int)(tile / P.D);
+    };
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // ---- producer ----
+            if (RESW) {
+                mbar_expect_tx(smem_u32(&bar_w), (uint32_t)(3 * kchunks * 9) * kBtap);
+                for (int dxp = 0; dxp < 3; ++dxp)
+                    for (int ch = 0; ch < kchunks; ++ch)
+                        tma_load_4d(wres + (uint32_t)((dxp * kchunks + ch) * 9) * kBtap, &map_w,
+                                    smem_u32(&bar_w), ch * CK, 0, dxp, 0);
+            }
+            long long g = 0;
+            for (long long tile = blockIdx.x; tile < P.ntiles && !*(volatile int *)&s_abort; tile += gridDim.x) {
+                int tn, w0, h0, d, n;
+                decode(tile, tn, w0, h0, d, n);
+                for (int kb = 0; kb < KB; ++kb, ++g) {
+                    const int q = (int)(g % S);
+                    if (g >= S && !mbar_wait(smem_u32(&bar_empty[q]), (uint32_t)((g / S) - 1) & 1u)) {
+                        s_abort = 1;
+                        break;
+                    }
+                    const int dxp = kb / kchunks, ch = kb % kchunks;
+                    const uint32_t a = base + (uint32_t)q * kStage, fb = smem_u32(&bar_full[q]);
+                    mbar_expect_tx(fb, kStage);
+                    tma_load_5d(a, &map_x, fb, ch * CK, w0 + dxp - 1, h0 - 1, d - 1, n);
+                    if (!RESW) tma_load_4d(a + kA, &map_w, fb, ch * CK, tn * BN, dxp, 0);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            bool ok = !RESW || mbar_wait(smem_u32(&bar_w), 0);
+            if (!ok) s_abort = 1;
+            long long g = 0;
+            int i = 0;
+            for (long long tile = blockIdx.x; ok && tile < P.ntiles; tile += gridDim.x, ++i) {
+                const int b = i & 1;
+                if (i >= 2 && !mbar_wait(smem_u32(&bar_acce[b]), (uint32_t)((i >> 1) - 1) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)b * kCols;
+                for (int kb = 0; kb < KB; ++kb, ++g) {
+                    const int q = (int)(g % S);
+                    if (!mbar_wait(smem_u32(&bar_full[q]), (uint32_t)(g / S) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const int dxp = kb / kchunks, ch = kb % kchunks;
+                    const uint32_t a = base + (uint32_t)q * kStage;
+#pragma unroll 1
+                    for (int m = 0; m < 9; ++m) {
+                        const uint32_t ra = a + (uint32_t)(kHaloW * (m % 3) + kHaloW * (kHaloH + 2) * (m / 3)) * kRow;
+                        const uint32_t rb = RESW ? wres + (uint32_t)((dxp * kchunks + ch) * 9 + m) * kBtap
+                                                 : a + kA + (uint32_t)m * kBtap;
+#pragma unroll
+                        for (int k = 0; k < CK / 16; ++k)
+                            umma_f16(dt, umma_desc(ra + 32 * k, 8 * kRow, kLayout),
+                                     umma_desc(rb + 32 * k, 8 * kRow, kLayout), kIdesc, (kb | m | k) != 0);
+                    }
+                    umma_commit(smem_u32(&bar_empty[q]));
+                }
+                if (!ok) break;
+                umma_commit(smem_u32(&bar_accf[b]));
+            }
+            if (!ok) s_abort = 1;
+            umma_commit(smem_u32(&bar_drain));     // fires once every product issued is done
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: warps 0-3, tensor memory lanes 32 warp .. 32 warp + 31 ----
+        int i = 0;
+        for (long long tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x, ++i) {
+            const int b = i & 1;
+            int ok = 0;
+            if (lane == 0) ok = mbar_wait(smem_u32(&bar_accf[b]), (uint32_t)(i >> 1) & 1u) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok || *(volatile int *)&s_abort) break;
+            tc_fence_after();
+            int tn, w0, h0, d, n;
+            decode(tile, tn, w0, h0, d, n);
+            const int r = warp * 32 + lane;
+            const int w = w0 + r % kHaloW, h = h0 + r / kHaloW;
+            const bool valid = w < P.W && h < P.H;
+            const long long vox = (((long long)n * P.D + d) * P.H + h) * P.W + w;
+            const int n0 = tn * BN;
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 16) {
+                float v[16];
+                tmem_ld16(tmem + (uint32_t)b * kCols + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+                if (!valid) continue;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float x = v[j] + (bias ? __ldg(bias + n0 + c + j) : 0.f);
+                    v[j] = P.relu ? fmaxf(x, 0.f) : x;
+                }
+                const long long o = vox * P.Cout + n0 + c;
+                if (out_f32) {
+                    float4 *dst = reinterpret_cast<float4 *>(out_f32 + o);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+                if (out_bf16) {
+                    uint4 pk[2];
+                    uint32_t *pw = reinterpret_cast<uint32_t *>(pk);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        __nv_bfloat162 t2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                        pw[q] = *reinterpret_cast<uint32_t *>(&t2);
+                    }
+                    uint4 *dst = reinterpret_cast<uint4 *>(out_bf16 + o);
+                    dst[0] = pk[0];
+                    dst[1] = pk[1];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bar_acce[b]));
+        }
+    }
+
+    // ---- teardown: every product done, copies landed, then free tensor memory ----
+    if (warp == 5 && lane == 0) mbar_wait(smem_u32(&bar_drain), 0);
+    if (warp == 4 && lane == 0 && *(volatile int *)&s_abort) {
+        // copies in flight at an abort: wait (bounded) for the stages' last phases
+        for (int q = 0; q < S; ++q) mbar_wait(smem_u32(&bar_full[q]), 0);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * kCols));
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -338,7 +599,12 @@ int launch(const CUtensorMap &mx, const CUtensorMap &mw, const float *bias, __nv
     int smem = (int)(S * kStage + 1024);
     if (smem < min_smem) smem = min_smem;
     auto kern = conv3d_tc_kernel<BN, CK, S>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    static bool attr_set = false;   // once per instantiation: allow the full opt-in shared memory
+    cudaError_t e = cudaSuccess;
+    if (!attr_set) {
+        e = allow_max_smem(reinterpret_cast<const void *>(kern));
+        attr_set = e == cudaSuccess;
+    }
     if (e == cudaSuccess) {
         kern<<<dim3((unsigned)ntiles, (unsigned)ny), kThreads, smem, st>>>(mx, mw, bias, ob, of, P);
         e = cudaGetLastError();
@@ -367,6 +633,102 @@ int dispatch_bn(int BN, const CUtensorMap &mx, const CUtensorMap &mw, const floa
     return NN_E_INVAL;
 }
 
+int num_sms()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess)
+            n = 148;
+    }
+    return n;
+}
+
+template <int BN, int CK, int S, bool RESW>
+int launch_halo(const CUtensorMap &mx, const CUtensorMap &mw, const float *bias, __nv_bfloat16 *ob, float *of,
+                const HaloTile &P, uint32_t smem, cudaStream_t st, char *err, size_t errlen)
+{
+    auto kern = conv3d_tc_halo_kernel<BN, CK, S, RESW>;
+    static bool attr_set = false;   // once per instantiation: allow the full opt-in shared memory
+    cudaError_t e = cudaSuccess;
+    if (!attr_set) {
+        e = allow_max_smem(reinterpret_cast<const void *>(kern));
+        attr_set = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) {
+        // persistent: as many CTAs as shared memory (228 KB per SM, 1 KB reserved
+        // per CTA) and tensor memory allow
+        const int fit = (int)(233472 / (smem + 1024 + 1024));
+        const int per_sm = std::max(1, std::min(fit, (int)(512 / (2 * tmem_cols(BN)))));
+        const long long grid = std::min<long long>(P.ntiles, (long long)num_sms() * per_sm);
+        kern<<<(unsigned)grid, kHaloThreads, smem, st>>>(mx, mw, bias, ob, of, P);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "conv3d_tc (halo): %s", cudaGetErrorString(e));
+        return NN_E_CUDA;
+    }
+    return NN_OK;
+}
+
+// Stages and weight residency of the halo kernel for this shape, or 0 stages
+// when it does not fit in shared memory.
+struct HaloPlan {
+    int stages;
+    bool resw;
+    uint32_t smem;
+};
+
+// Measured on the U-Net layers at 128^3: two resident CTAs per SM (one's
+// epilogue and loads overlapping the other's products) beat one CTA with a
+// deeper ring, so the plan first looks for the deepest ring that still lets two
+// CTAs share an SM, then for the deepest one that fits alone. Resident weights
+// win ties.
+HaloPlan plan_halo(int BN, int CK, int Cin, int ntn)
+{
+    const uint32_t wbytes = 27u * (uint32_t)Cin * (uint32_t)BN * 2u;
+    const uint32_t sa = halo_stage_bytes(BN, CK, true), sb = halo_stage_bytes(BN, CK, false);
+    const uint32_t two = 233472u / 2u - 2048u;   // per-CTA budget for two CTAs per SM
+    for (uint32_t budget : {two, kMaxDynSmem}) {
+        for (int st = 4; st >= 2; --st) {
+            const uint32_t r = (uint32_t)st * sa + wbytes + 1024, t = (uint32_t)st * sb + 1024;
+            if (ntn == 1 && r <= budget) return {st, true, r};
+            if (t <= budget) return {st, false, t};
+        }
+    }
+    return {0, false, 0};
+}
+
+template <int BN, int CK>
+int dispatch_halo_stages(const HaloPlan &pl, const CUtensorMap &mx, const CUtensorMap &mw, const float *bias,
+                         __nv_bfloat16 *ob, float *of, const HaloTile &P, cudaStream_t st, char *err, size_t errlen)
+{
+    if (pl.resw) {
+        if (pl.stages == 4) return launch_halo<BN, CK, 4, true>(mx, mw, bias, ob, of, P, pl.smem, st, err, errlen);
+        if (pl.stages == 3) return launch_halo<BN, CK, 3, true>(mx, mw, bias, ob, of, P, pl.smem, st, err, errlen);
+        return launch_halo<BN, CK, 2, true>(mx, mw, bias, ob, of, P, pl.smem, st, err, errlen);
+    }
+    if (pl.stages == 4) return launch_halo<BN, CK, 4, false>(mx, mw, bias, ob, of, P, pl.smem, st, err, errlen);
+    if (pl.stages == 3) return launch_halo<BN, CK, 3, false>(mx, mw, bias, ob, of, P, pl.smem, st, err, errlen);
+    return launch_halo<BN, CK, 2, false>(mx, mw, bias, ob, of, P, pl.smem, st, err, errlen);
+}
+
+template <int CK>
+int dispatch_halo(int BN, const HaloPlan &pl, const CUtensorMap &mx, const CUtensorMap &mw, const float *bias,
+                  __nv_bfloat16 *ob, float *of, const HaloTile &P, cudaStream_t st, char *err, size_t errlen)
+{
+    switch (BN) {
+    case 16: return dispatch_halo_stages<16, CK>(pl, mx, mw, bias, ob, of, P, st, err, errlen);
+    case 32: return dispatch_halo_stages<32, CK>(pl, mx, mw, bias, ob, of, P, st, err, errlen);
+    case 48: return dispatch_halo_stages<48, CK>(pl, mx, mw, bias, ob, of, P, st, err, errlen);
+    case 64: return dispatch_halo_stages<64, CK>(pl, mx, mw, bias, ob, of, P, st, err, errlen);
+    default: break;
+    }
+    snprintf(err, errlen, "conv3d_tc (halo): no kernel for %d output channels per tile", BN);
+    return NN_E_INVAL;
+}
+
 }  // namespace
 
 // Shapes the tensor-core path takes: 3x3x3 kernels with input and output
@@ -383,10 +745,64 @@ int tile_n_for(int Cout)
         if (Cout % bn == 0) return bn;
     return 0;
 }
+// The same for the halo kernel, which takes at most 64 channels per tile.
+int halo_n_for(int Cout)
+{
+    for (int bn : {64, 48, 32, 16})
+        if (Cout % bn == 0) return bn;
+    return 0;
+}
+
+// Halo kernel for this shape if it fits (stages > 0), with its tensor maps.
+int run_halo(const void *in, const void *wt, const float *bias, void *out_bf16, float *out_f32, int N, int D, int H,
+             int W, int Cin, int Cout, int relu, cudaStream_t st, char *err, size_t errlen, bool *taken)
+{
+    *taken = false;
+    const int CK = chunk_for(Cin), BN = halo_n_for(Cout);
+    if (!BN) return NN_OK;
+    const int ntn = Cout / BN;
+    const HaloPlan pl = plan_halo(BN, CK, Cin, ntn);
+    if (!pl.stages) return NN_OK;
+    HaloTile P{};
+    P.N = N; P.D = D; P.H = H; P.W = W; P.Cin = Cin; P.Cout = Cout; P.relu = relu;
+    P.tw = (W + kHaloW - 1) / kHaloW;
+    P.th = (H + kHaloH - 1) / kHaloH;
+    P.ntn = ntn;
+    P.ntiles = (long long)ntn * P.tw * P.th * D * N;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    const CUtensorMapSwizzle sw = CK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : CK == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                             : CU_TENSOR_MAP_SWIZZLE_32B;
+    CUtensorMap mx, mw;
+    const cuuint64_t gx[5] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)N};
+    const cuuint64_t sx[4] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2,
+                              (cuuint64_t)D * H * W * Cin * 2};
+    const cuuint32_t bx[5] = {(cuuint32_t)CK, (cuuint32_t)kHaloW, (cuuint32_t)(kHaloH + 2), 3, 1};
+    const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
+    CUresult r1 = enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(in), gx, sx, bx, ones,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    // weights [27][Cout][Cin] viewed as [9][3][Cout][Cin]: tap t = dx' + 3 m
+    const cuuint64_t gw[4] = {(cuuint64_t)Cin, (cuuint64_t)Cout, 3, 9};
+    const cuuint64_t swd[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)Cout * Cin * 2, 3ull * Cout * Cin * 2};
+    const cuuint32_t bw[4] = {(cuuint32_t)CK, (cuuint32_t)BN, 1, 9};
+    CUresult r2 = enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(wt), gw, swd, bw, ones,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
+        snprintf(err, errlen, "conv3d_tc (halo): tensor map encoding failed (%d, %d)", (int)r1, (int)r2);
+        return NN_E_INVAL;
+    }
+    *taken = true;
+    auto *ob = static_cast<__nv_bfloat16 *>(out_bf16);
+    if (CK == 64) return dispatch_halo<64>(BN, pl, mx, mw, bias, ob, out_f32, P, st, err, errlen);
+    if (CK == 32) return dispatch_halo<32>(BN, pl, mx, mw, bias, ob, out_f32, P, st, err, errlen);
+    return dispatch_halo<16>(BN, pl, mx, mw, bias, ob, out_f32, P, st, err, errlen);
+}
 }  // namespace
 
 int conv3d_fwd(const void *in, const void *wt, const float *bias, void *out_bf16, float *out_f32, int N, int D, int H,
-               int W, int Cin, int Cout, int relu, cudaStream_t st, char *err, size_t errlen)
+               int W, int Cin, int Cout, int relu, cudaStream_t st, char *err, size_t errlen, int variant)
 {
     if (!supported(Cin, Cout)) {
         snprintf(err, errlen, "conv3d_tc: unsupported channels %d -> %d", Cin, Cout);
@@ -401,6 +817,15 @@ int conv3d_fwd(const void *in, const void *wt, const float *bias, void *out_bf16
     if (!enc) {
         snprintf(err, errlen, "conv3d_tc: cuTensorMapEncodeTiled is not available");
         return NN_E_CUDA;
+    }
+    if (variant != kVariantTap) {
+        bool taken = false;
+        const int rc = run_halo(in, wt, bias, out_bf16, out_f32, N, D, H, W, Cin, Cout, relu, st, err, errlen, &taken);
+        if (taken || rc != NN_OK) return rc;
+        if (variant == kVariantHalo) {
+            snprintf(err, errlen, "conv3d_tc: the halo kernel does not take %d -> %d channels", Cin, Cout);
+            return NN_E_INVAL;
+        }
     }
     const int CK = chunk_for(Cin);
     const int BN = tile_n_for(Cout);

@@ -26,7 +26,7 @@
 namespace nn_tc {   // conv_tc.cu
 bool supported(int Cin, int Cout);
 int conv3d_fwd(const void *in, const void *wt, const float *bias, void *out_bf16, float *out_f32, int N, int D, int H,
-               int W, int Cin, int Cout, int relu, cudaStream_t st, char *err, size_t errlen);
+               int W, int Cin, int Cout, int relu, cudaStream_t st, char *err, size_t errlen, int variant);
 int take_status(cudaStream_t st, unsigned *out);
 }  // namespace nn_tc
 
@@ -545,7 +545,8 @@ const char *nn_last_error(void) { return g_err; }
 
 int nn_set_conv_path(int path)
 {
-    if (path != NN_CONV_AUTO && path != NN_CONV_MMA_SYNC && path != NN_CONV_TCGEN05)
+    if (path != NN_CONV_AUTO && path != NN_CONV_MMA_SYNC && path != NN_CONV_TCGEN05 && path != NN_CONV_TCGEN05_TAP &&
+        path != NN_CONV_TCGEN05_HALO)
         return inval("nn_set_conv_path: unknown path");
     const int old = g_conv_path;
     g_conv_path = path;
@@ -571,11 +572,14 @@ int nn_conv3d_fwd(const void *in, const void *wt, const float *bias, void *out_b
     if (Cin % 16 != 0) return inval("nn_conv3d_fwd: Cin must be a multiple of 16");
     if (out_bf16 && Cout % 2 != 0) return inval("nn_conv3d_fwd: BF16 output needs an even Cout");
     if (ksize != 1 && ksize != 3) return inval("nn_conv3d_fwd: ksize must be 1 or 3");
-    if (ksize == 3 && g_conv_path != NN_CONV_MMA_SYNC &&
-        (g_conv_path == NN_CONV_TCGEN05 || nn_tc::supported(Cin, Cout)))
+    const bool forced = g_conv_path == NN_CONV_TCGEN05 || g_conv_path == NN_CONV_TCGEN05_TAP ||
+                        g_conv_path == NN_CONV_TCGEN05_HALO;
+    if (ksize == 3 && g_conv_path != NN_CONV_MMA_SYNC && (forced || nn_tc::supported(Cin, Cout))) {
+        const int variant = g_conv_path == NN_CONV_TCGEN05_TAP ? 1 : g_conv_path == NN_CONV_TCGEN05_HALO ? 2 : 0;
         return nn_tc::conv3d_fwd(in, wt, bias, out_bf16, out_f32, N, D, H, W, Cin, Cout, relu, (cudaStream_t)stream,
-                                 g_err, sizeof g_err);
-    if (g_conv_path == NN_CONV_TCGEN05) return inval("nn_conv3d_fwd: the tcgen05 path takes 3x3x3 kernels only");
+                                 g_err, sizeof g_err, variant);
+    }
+    if (forced && ksize == 3) return inval("nn_conv3d_fwd: channel counts the tcgen05 kernels do not take");
     const long long M = (long long)N * D * H * W;
     if (Cout >= 64) {
         dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((Cout + 63) / 64));

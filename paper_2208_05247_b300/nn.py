@@ -10,7 +10,7 @@ import ctypes
 from .rt import library
 
 NN_OK = 0
-NN_CONV_AUTO, NN_CONV_MMA_SYNC, NN_CONV_TCGEN05 = 0, 1, 2
+NN_CONV_AUTO, NN_CONV_MMA_SYNC, NN_CONV_TCGEN05, NN_CONV_TCGEN05_TAP, NN_CONV_TCGEN05_HALO = 0, 1, 2, 3, 4
 
 _sig_done = False
 

@@ -98,8 +98,30 @@ def conv_path():
     ((1, 3, 4, 5), 192, 80, False),
 ])
 def test_conv_forward_tcgen05(conv_path, shape, Cin, Cout, relu):
-    """The tcgen05/TMA kernel against the FP64 reference, including borders."""
-    conv_path(nn.NN_CONV_TCGEN05)
+    """The per-tap tcgen05/TMA kernel against the FP64 reference, including borders."""
+    _check_tc_conv(conv_path, nn.NN_CONV_TCGEN05_TAP, shape, Cin, Cout, relu)
+
+
+# the halo-tiled persistent kernel: tiles of 8 x 16 voxels of one z slice,
+# ragged in x and y, several slices and samples per CTA, resident and streamed
+# weights, several output-channel tiles
+@pytest.mark.parametrize("shape,Cin,Cout,relu", [
+    ((1, 1, 1, 1), 16, 16, False),
+    ((2, 3, 5, 7), 16, 32, True),
+    ((1, 4, 20, 9), 32, 16, False),
+    ((1, 8, 8, 8), 32, 64, False),
+    ((2, 5, 17, 20), 64, 48, True),
+    ((1, 3, 33, 17), 96, 32, True),
+    ((1, 6, 7, 8), 32, 96, False),
+    ((1, 4, 16, 24), 48, 128, True),
+    ((1, 3, 16, 16), 64, 32, False),
+])
+def test_conv_forward_tcgen05_halo(conv_path, shape, Cin, Cout, relu):
+    _check_tc_conv(conv_path, nn.NN_CONV_TCGEN05_HALO, shape, Cin, Cout, relu)
+
+
+def _check_tc_conv(conv_path, path, shape, Cin, Cout, relu):
+    conv_path(path)
     rng = np.random.default_rng(Cin * 7 + Cout)
     x = nn_ref.bf16_round(rng.normal(size=shape + (Cin,)))
     W = nn_ref.bf16_round(rng.normal(size=(27, Cin, Cout)) / np.sqrt(27 * Cin))
