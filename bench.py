@@ -62,7 +62,7 @@ def parse():
     p.add_argument("--no-denoise", action="store_true", help="skip the denoised-vs-plain time-to-RMSE leg")
     p.add_argument("--no-coupled", action="store_true", help="skip the graph-replay coupled-step leg")
     p.add_argument("--no-birth", action="store_true", help="skip the Sobol-vs-Philox start position leg")
-    p.add_argument("--denoise-train", type=int, default=256, help="training scenes of the denoiser leg")
+    p.add_argument("--denoise-train", type=int, default=512, help="training scenes of the denoiser leg")
     p.add_argument("--no-autotune", action="store_true",
                    help="use the default launch parameters and the --coarse grid")
     p.add_argument("--coarse", type=int, nargs=3, default=None,
