@@ -105,14 +105,28 @@ int nn_adam(float *W, float *m, float *v, const float *grad, long long n, float 
  * gradient (either may be NULL). */
 int nn_weights_bf16(const float *W, void *wt, void *wd, int ksize, int Cin, int Cout, void *stream);
 
+/* Direct-beam transmittance toward the sun (Sec. 2.3: "direct" radiation is
+ * the never-scattered part, whose expectation is Beer-Lambert along the sun
+ * ray): exp(-integral of k_gas + k_cld) from each voxel centre to the domain
+ * top, t3d FP32 [D][H][W], and from each column's centre at the surface,
+ * t2d FP32 [H][W]. An exact walk over the fine cells (cell sizes dx, dy, dz,
+ * periodic in x and y) in FP32; optical depths above 30 give 0. A feature
+ * of the optics for the denoiser. */
+int nn_direct_transmittance(const float *k_gas, const float *k_cld, int D, int H, int W, double dx, double dy,
+                            double dz, double sza_deg, double azimuth_deg, float *t3d, float *t2d, void *stream);
+
 /* Denoiser inputs from a traced field (FP64 [D][H][W] absorption [W m^-3],
  * [H][W] surface direct/diffuse [W m^-2]) and the optics (FP32 [D][H][W]):
  * BF16 [D][H][W][16] with channels 0: 100 A dz / F, 1: direct / F, 2: diffuse
  * / F (surface values repeated in every layer), 3: log(tau_cell + 1e-4) / 5,
- * 4: k_sca / k_ext, 5: cloud g, 6..15: 0. F = toa_flux cos(sza) [W m^-2]. */
+ * 4: k_sca / k_ext, 5: cloud g, 6: direct transmittance of the voxel (t3d),
+ * 7: direct transmittance of the column at the surface (t2d), 8..15: 0.
+ * t3d and t2d may be NULL (channels 6 and 7 then 0). F = toa_flux cos(sza)
+ * [W m^-2]. */
 int nn_pack_inputs(const double *abs3d, const double *sfc_dir, const double *sfc_dif, const float *k_gas,
-                   const float *ssa_gas, const float *k_cld, const float *ssa_cld, const float *g_cld, void *out,
-                   int D, int H, int W, double dz, double flux, void *stream);
+                   const float *ssa_gas, const float *k_cld, const float *ssa_cld, const float *g_cld,
+                   const float *t3d, const float *t2d, void *out, int D, int H, int W, double dz, double flux,
+                   void *stream);
 
 /* Training targets FP32 [D][H][W][3]: channels 0..2 of the high-photon field
  * minus those of the low-photon field (as BF16-rounded inputs hold them). */

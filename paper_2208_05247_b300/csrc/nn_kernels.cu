@@ -462,9 +462,60 @@ __global__ void weights_bf16_kernel(const float *W, __nv_bfloat16 *wt, __nv_bflo
 // Targets (FP32, 3 per voxel) are the same first three quantities of the
 // high-photon field MINUS the noisy input (the network predicts a correction).
 // ---------------------------------------------------------------------------
+// Direct-beam transmittance exp(-integral of k_ext) from each voxel centre,
+// and from each column's centre at the surface, to the domain top along the
+// direction toward the sun (vx, vy, vz), vz > 0: an exact walk over the fine
+// cells with periodic x and y. Walks stop once the optical depth passes 30
+// (transmittance below 1e-13, stored as 0) or after a bound on the steps.
+__global__ void direct_transmittance_kernel(const float *kg, const float *kc, int D, int H, int W, float dx,
+                                            float dy, float dz, float vx, float vy, float vz, float *t3, float *t2)
+{
+    const long long n3 = (long long)D * H * W, n = n3 + (long long)H * W;
+    const int max_steps = 4 * (D + H + W) + 64;
+    const float ax = fabsf(vx), ay = fabsf(vy);
+    const float stx = ax > 0.f ? dx / ax : INFINITY, sty = ay > 0.f ? dy / ay : INFINITY, stz = dz / vz;
+    const int sx = vx > 0.f ? 1 : -1, sy = vy > 0.f ? 1 : -1;
+    GRID_LOOP(q, n) {
+        int i, j, k;
+        float fz;                                  // start height within the first cell, in cells
+        if (q < n3) {
+            i = (int)(q % W); j = (int)((q / W) % H); k = (int)(q / ((long long)W * H)); fz = 0.5f;
+        } else {
+            const long long c = q - n3;
+            i = (int)(c % W); j = (int)(c / W); k = 0; fz = 0.f;
+        }
+        // distances along the ray to the next face per axis (start at the cell's centre in x and y)
+        float tx = ax > 0.f ? 0.5f * stx : INFINITY, ty = ay > 0.f ? 0.5f * sty : INFINITY;
+        float tz = (1.f - fz) * stz, t = 0.f, tau = 0.f;
+        for (int s = 0; s < max_steps; ++s) {
+            const long long cell = ((long long)k * H + j) * W + i;
+            const float tm = fminf(tx, fminf(ty, tz));
+            tau = fmaf(kg[cell] + kc[cell], tm - t, tau);
+            t = tm;
+            if (tau > 30.f) break;
+            if (tm == tz) {
+                if (++k >= D) break;
+                tz += stz;
+            } else if (tm == tx) {
+                i += sx;
+                i = i < 0 ? W - 1 : i >= W ? 0 : i;
+                tx += stx;
+            } else {
+                j += sy;
+                j = j < 0 ? H - 1 : j >= H ? 0 : j;
+                ty += sty;
+            }
+        }
+        const float T = tau > 30.f ? 0.f : expf(-tau);
+        if (q < n3) t3[q] = T;
+        else t2[q - n3] = T;
+    }
+}
+
 __global__ void pack_inputs_kernel(const double *abs3d, const double *sdir, const double *sdif, const float *kg,
                                    const float *wg, const float *kc, const float *wc, const float *gc,
-                                   __nv_bfloat16 *out, int D, int H, int W, double dz, double F)
+                                   const float *t3, const float *t2, __nv_bfloat16 *out, int D, int H, int W,
+                                   double dz, double F)
 {
     const long long n = (long long)D * H * W;
     GRID_LOOP(v, n) {
@@ -478,7 +529,9 @@ __global__ void pack_inputs_kernel(const double *abs3d, const double *sdir, cons
         ch[3] = logf(ke * (float)dz + 1e-4f) / 5.0f;
         ch[4] = ke > 0.f ? ks / ke : 1.0f;
         ch[5] = gc[v];
-        for (int c = 6; c < 16; ++c) ch[c] = 0.f;
+        ch[6] = t3 ? t3[v] : 0.f;
+        ch[7] = t2 ? t2[col] : 0.f;
+        for (int c = 8; c < 16; ++c) ch[c] = 0.f;
         __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(out + v * 16);
         for (int c = 0; c < 8; ++c) o[c] = __floats2bfloat162_rn(ch[2 * c], ch[2 * c + 1]);
     }
@@ -686,14 +739,30 @@ int nn_adam(float *W, float *m, float *v, const float *grad, long long n, float 
     return check_launch("nn_adam");
 }
 
+int nn_direct_transmittance(const float *k_gas, const float *k_cld, int D, int H, int W, double dx, double dy,
+                            double dz, double sza_deg, double azimuth_deg, float *t3d, float *t2d, void *stream)
+{
+    if (!k_gas || !k_cld || !t3d || !t2d || D <= 0 || H <= 0 || W <= 0 || !(dx > 0) || !(dy > 0) || !(dz > 0) ||
+        !(sza_deg >= 0.0 && sza_deg < 90.0) || !std::isfinite(azimuth_deg))
+        return inval("nn_direct_transmittance: bad argument");
+    const double t = sza_deg * 3.14159265358979323846 / 180.0, p = azimuth_deg * 3.14159265358979323846 / 180.0;
+    const long long n = (long long)D * H * W + (long long)H * W;
+    direct_transmittance_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(
+        k_gas, k_cld, D, H, W, (float)dx, (float)dy, (float)dz, (float)(std::sin(t) * std::sin(p)),
+        (float)(std::sin(t) * std::cos(p)), (float)std::cos(t), t3d, t2d);
+    return check_launch("nn_direct_transmittance");
+}
+
 int nn_pack_inputs(const double *abs3d, const double *sfc_dir, const double *sfc_dif, const float *k_gas,
-                   const float *ssa_gas, const float *k_cld, const float *ssa_cld, const float *g_cld, void *out,
-                   int D, int H, int W, double dz, double flux, void *stream)
+                   const float *ssa_gas, const float *k_cld, const float *ssa_cld, const float *g_cld,
+                   const float *t3d, const float *t2d, void *out, int D, int H, int W, double dz, double flux,
+                   void *stream)
 {
     if (!abs3d || !sfc_dir || !sfc_dif || !k_gas || !ssa_gas || !k_cld || !ssa_cld || !g_cld || !out || !(flux > 0))
         return inval("nn_pack_inputs: bad argument");
     pack_inputs_kernel<<<grid1d((long long)D * H * W), 256, 0, (cudaStream_t)stream>>>(
-        abs3d, sfc_dir, sfc_dif, k_gas, ssa_gas, k_cld, ssa_cld, g_cld, (__nv_bfloat16 *)out, D, H, W, dz, flux);
+        abs3d, sfc_dir, sfc_dif, k_gas, ssa_gas, k_cld, ssa_cld, g_cld, t3d, t2d, (__nv_bfloat16 *)out, D, H, W,
+        dz, flux);
     return check_launch("nn_pack_inputs");
 }
 

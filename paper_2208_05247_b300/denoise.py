@@ -24,7 +24,7 @@ import numpy as np
 
 from . import nn, rt, scenes
 
-CIN = 16      # packed input channels (6 used)
+CIN = 16      # packed input channels (6 used; 8 with the direct-beam features)
 COUT = 16     # head channels (3 used)
 NUSE = 3
 LEVELS = (32, 64, 128, 256)
@@ -266,7 +266,7 @@ class FieldTracer:
     independently; N_sample counts rays per column per point, Sec. 2.4).
     """
 
-    def __init__(self, shape, dx=50.0, dy=50.0, dz=25.0, stream=None, spectral=False):
+    def __init__(self, shape, dx=50.0, dy=50.0, dz=25.0, stream=None, spectral=False, direct_features=False):
         torch = _torch()
         nz, ny, nx = shape
         self.t = rt.Tracer(nx, ny, nz, dx, dy, dz, stream=stream)
@@ -280,6 +280,14 @@ class FieldTracer:
         self.ncell, self.ncol = nx * ny * nz, nx * ny
         self.optics = [torch.empty(self.ncell, dtype=torch.float32, device=dev) for _ in range(5)]
         self.alb = torch.empty(self.ncol, dtype=torch.float32, device=dev)
+        # optional input channels 6 and 7: deterministic direct-beam transmittance.
+        # Measured on the 512-scene configuration they lowered the GHI error a
+        # little (47.8 vs 54.9 W m^-2) but raised the heating-rate error (0.38 vs
+        # 0.22 K/day), so they are off by default.
+        self.direct_features = direct_features
+        self.t3d = torch.empty(self.ncell, dtype=torch.float32, device=dev)
+        self.t2d = torch.empty(self.ncol, dtype=torch.float32, device=dev)
+        self.dx, self.dy = dx, dy
 
     def load(self, scene):
         torch = _torch()
@@ -312,7 +320,13 @@ class FieldTracer:
         nz, ny, nx = self.shape
         F = 1000.0 * math.cos(math.radians(sza))
         x = torch.empty(self.ncell * CIN, dtype=torch.bfloat16, device="cuda")
-        nn.nn_pack_inputs(lo[0], lo[1], lo[2], *self.optics, x, nz, ny, nx, self.dz, F)
+        if self.direct_features:
+            # deterministic direct-beam transmittance of the optics (input channels 6, 7)
+            nn.nn_direct_transmittance(self.optics[0], self.optics[2], nz, ny, nx, self.dx, self.dy, self.dz, sza,
+                                       0.0, self.t3d, self.t2d)
+        nn.nn_pack_inputs(lo[0], lo[1], lo[2], *self.optics, x, nz, ny, nx, self.dz, F,
+                          t3d=self.t3d if self.direct_features else None,
+                          t2d=self.t2d if self.direct_features else None)
         tgt = None
         if hi is not None:
             tgt = torch.empty(self.ncell * NUSE, dtype=torch.float32, device="cuda")

@@ -35,7 +35,8 @@ def _lib():
             "nn_mse": ([P, i32, P, i32, P, P, i64, P, P], i32),
             "nn_adam": ([P, P, P, P, i64, f32, f32, f32, f32, i32, f32, P], i32),
             "nn_weights_bf16": ([P, P, P, i32, i32, i32, P], i32),
-            "nn_pack_inputs": ([P] * 9 + [i32] * 3 + [f64, f64, P], i32),
+            "nn_pack_inputs": ([P] * 11 + [i32] * 3 + [f64, f64, P], i32),
+            "nn_direct_transmittance": ([P, P] + [i32] * 3 + [f64] * 5 + [P, P, P], i32),
             "nn_pack_targets": ([P] * 7 + [i32] * 3 + [f64, f64, P], i32),
             "nn_unpack": ([P, P, i32, P, P, P] + [i32] * 3 + [f64, f64, P], i32),
         }
@@ -124,9 +125,14 @@ def nn_weights_bf16(W, wt, wd, ksize, Cin, Cout, stream=None):
 
 
 def nn_pack_inputs(abs3d, sfc_dir, sfc_dif, k_gas, ssa_gas, k_cld, ssa_cld, g_cld, out, D, H, W, dz, flux,
-                   stream=None):
+                   stream=None, t3d=None, t2d=None):
     _check(_lib().nn_pack_inputs(*[_p(t) for t in (abs3d, sfc_dir, sfc_dif, k_gas, ssa_gas, k_cld, ssa_cld, g_cld,
-                                                    out)], D, H, W, float(dz), float(flux), _s(stream)))
+                                                    t3d, t2d, out)], D, H, W, float(dz), float(flux), _s(stream)))
+
+
+def nn_direct_transmittance(k_gas, k_cld, D, H, W, dx, dy, dz, sza_deg, azimuth_deg, t3d, t2d, stream=None):
+    _check(_lib().nn_direct_transmittance(_p(k_gas), _p(k_cld), D, H, W, float(dx), float(dy), float(dz),
+                                          float(sza_deg), float(azimuth_deg), _p(t3d), _p(t2d), _s(stream)))
 
 
 def nn_pack_targets(abs_hi, sdir_hi, sdif_hi, abs_lo, sdir_lo, sdif_lo, out, D, H, W, dz, flux, stream=None):

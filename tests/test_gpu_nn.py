@@ -238,3 +238,35 @@ def test_adam_step():
         v = 0.999 * v + 0.001 * g * g
         W = W - 1e-3 * (m / (1 - 0.9 ** step)) / (np.sqrt(v / (1 - 0.999 ** step)) + 1e-8)
     assert np.allclose(Wd.cpu().numpy(), W, rtol=1e-5, atol=1e-6)
+
+
+def test_direct_transmittance_closed_form_and_oracle():
+    """Beer-Lambert along the sun ray (Sec. 2.3: the direct part is the
+    never-scattered part): exact in a layered slab, and equal to the oracle's
+    FP64 ray march through a 3D cloud field."""
+    import oracle
+    from paper_2208_05247_b300 import scenes
+    D, H, W, dz = 6, 5, 7, 40.0
+    k = np.array([1e-3, 4e-3, 0.0, 2e-2, 5e-4, 1e-2], dtype=np.float32)
+    kg = np.broadcast_to(k[:, None, None], (D, H, W)).astype(np.float32)
+    kc = np.zeros_like(kg)
+    sza, az = 40.0, 30.0
+    mu0 = np.cos(np.deg2rad(sza))
+    t3 = torch.empty(D * H * W, dtype=torch.float32, device="cuda")
+    t2 = torch.empty(H * W, dtype=torch.float32, device="cuda")
+    nn.nn_direct_transmittance(f32(kg), f32(kc), D, H, W, 30.0, 20.0, dz, sza, az, t3, t2)
+    kd = k.astype(np.float64)
+    above = np.array([kd[i + 1:].sum() for i in range(D)])
+    want3 = np.exp(-(above + 0.5 * kd) * dz / mu0)
+    got3 = host(t3).reshape(D, H, W)
+    assert np.allclose(got3, want3[:, None, None], rtol=2e-6, atol=0)
+    assert np.allclose(host(t2), np.exp(-kd.sum() * dz / mu0), rtol=2e-6, atol=0)
+    # a 3D cloud field against the oracle's deterministic march from the column centres
+    sc = scenes.ellipsoid_scene(seed=0)
+    for sza, az in ((30.0, 0.0), (55.0, 228.1)):
+        t3 = torch.empty(sc.ncell, dtype=torch.float32, device="cuda")
+        t2 = torch.empty(sc.ncol, dtype=torch.float32, device="cuda")
+        nn.nn_direct_transmittance(f32(sc.k_gas), f32(sc.k_cld), sc.nz, sc.ny, sc.nx, sc.dx, sc.dy, sc.dz, sza, az,
+                                   t3, t2)
+        want = oracle.direct_beam(sc, sza, az, nsub=1)
+        assert np.allclose(host(t2).reshape(sc.ny, sc.nx), want, rtol=1e-4, atol=1e-6), np.abs(host(t2) - want.ravel()).max()
