@@ -44,7 +44,9 @@ COARSE = (4, 4, 4)
 # Algorithmic bytes of the transport kernel: 16 B optics record + 16 B FP64
 # tally read-modify-write per majorant event, 4 B majorant per coarse crossing.
 BYTES_PER_EVENT, BYTES_PER_CROSSING = 32, 4
-KERNELS_PER_STEP = 9   # derive, albedo check, majorant, transport, 4 field sums, heating rate
+# derive, albedo check, majorant, column keys + column order (launch order),
+# transport, 4 field sums, heating rate
+KERNELS_PER_STEP = 11
 PROFILE = os.path.join(ROOT, "profiles", "trace_kernel_cumulus256.md")
 
 
