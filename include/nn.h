@@ -135,7 +135,8 @@ int nn_pack_targets(const double *abs_hi, const double *sdir_hi, const double *s
                     double flux, void *stream);
 
 /* Denoised fields: input channel + predicted correction (pred FP32 [vox][Cp]),
- * back to W m^-3 and W m^-2; surface fields from the bottom layer. */
+ * back to W m^-3 and W m^-2. Every layer of a column predicts the surface
+ * correction (channels 1 and 2); the surface fields take the column mean. */
 int nn_unpack(const void *in, const float *pred, int Cp, double *abs3d, double *sfc_dir, double *sfc_dif, int D,
               int H, int W, double dz, double flux, void *stream);
 

@@ -555,7 +555,7 @@ __global__ void pack_targets_kernel(const double *abs_hi, const double *sdir_hi,
 }
 
 // denoised fields: noisy input channel + predicted correction, back to
-// physical units; surface fields from the bottom layer
+// physical units; surface fields from the mean correction over each column
 __global__ void unpack_kernel(const __nv_bfloat16 *in, const float *pred, int Cp, double *abs3d, double *sdir,
                               double *sdif, int D, int H, int W, double dz, double F)
 {
@@ -563,10 +563,18 @@ __global__ void unpack_kernel(const __nv_bfloat16 *in, const float *pred, int Cp
     GRID_LOOP(v, n) {
         const float a = __bfloat162float(in[v * 16 + 0]) + pred[v * Cp + 0];
         abs3d[v] = (double)a * F / (100.0 * dz);
-        if (v < (long long)H * W) {
-            sdir[v] = (double)(__bfloat162float(in[v * 16 + 1]) + pred[v * Cp + 1]) * F;
-            sdif[v] = (double)(__bfloat162float(in[v * 16 + 2]) + pred[v * Cp + 2]) * F;
+    }
+    // every layer of a column is trained to predict the same surface
+    // correction; their mean is the surface estimate
+    const long long nc = (long long)H * W;
+    GRID_LOOP(c, nc) {
+        float s1 = 0.f, s2 = 0.f;
+        for (int k = 0; k < D; ++k) {
+            s1 += pred[(k * nc + c) * Cp + 1];
+            s2 += pred[(k * nc + c) * Cp + 2];
         }
+        sdir[c] = (double)(__bfloat162float(in[c * 16 + 1]) + s1 / D) * F;
+        sdif[c] = (double)(__bfloat162float(in[c * 16 + 2]) + s2 / D) * F;
     }
 }
 

@@ -270,3 +270,32 @@ def test_direct_transmittance_closed_form_and_oracle():
                                    t3, t2)
         want = oracle.direct_beam(sc, sza, az, nsub=1)
         assert np.allclose(host(t2).reshape(sc.ny, sc.nx), want, rtol=1e-4, atol=1e-6), np.abs(host(t2) - want.ravel()).max()
+
+
+def test_pack_and_unpack_round_trip():
+    """Inputs are the noisy fields scaled by the incoming flux; the denoised
+    fields add the predicted corrections back, the surface ones averaged over
+    each column (every layer predicts the same surface correction)."""
+    rng = np.random.default_rng(21)
+    D, H, W, dz, F = 4, 3, 5, 25.0, 700.0
+    abs3d = rng.random((D, H, W)) * 0.02
+    sdir, sdif = rng.random((H, W)) * 600, rng.random((H, W)) * 200
+    opt = [rng.random((D, H, W)).astype(np.float32) * s for s in (1e-3, 1.0, 1e-2, 1.0, 0.9)]
+    d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).cuda()   # noqa: E731
+    x = torch.empty(D * H * W * 16, dtype=torch.bfloat16, device="cuda")
+    nn.nn_pack_inputs(d64(abs3d), d64(sdir), d64(sdif), *[f32(o) for o in opt], x, D, H, W, dz, F)
+    xs = host(x).reshape(D, H, W, 16)
+    assert np.allclose(xs[..., 0], nn_ref.bf16_round(100 * abs3d * dz / F), rtol=0, atol=0)
+    assert np.allclose(xs[..., 1], nn_ref.bf16_round(np.broadcast_to(sdir / F, (D, H, W))), rtol=0, atol=0)
+    assert np.all(xs[..., 6:] == 0)
+    pred = rng.normal(size=(D, H, W, 16)).astype(np.float32) * 0.01
+    o3, o1, o2 = (torch.empty(D * H * W, dtype=torch.float64, device="cuda"),
+                  torch.empty(H * W, dtype=torch.float64, device="cuda"),
+                  torch.empty(H * W, dtype=torch.float64, device="cuda"))
+    nn.nn_unpack(x, f32(pred), 16, o3, o1, o2, D, H, W, dz, F)
+    want3 = (xs[..., 0] + pred[..., 0].astype(np.float64)) * F / (100 * dz)
+    want1 = (xs[0, :, :, 1] + pred[..., 1].astype(np.float64).mean(axis=0)) * F
+    want2 = (xs[0, :, :, 2] + pred[..., 2].astype(np.float64).mean(axis=0)) * F
+    assert np.allclose(host(o3).reshape(D, H, W), want3, rtol=1e-6, atol=1e-9)
+    assert np.allclose(host(o1).reshape(H, W), want1, rtol=1e-6, atol=1e-6)
+    assert np.allclose(host(o2).reshape(H, W), want2, rtol=1e-6, atol=1e-6)
