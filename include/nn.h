@@ -100,6 +100,10 @@ int nn_mse(const float *pred, int Cp, const float *target, int Cuse, const float
 int nn_adam(float *W, float *m, float *v, const float *grad, long long n, float lr, float b1, float b2, float eps,
             int step, float weight_decay, void *stream);
 
+/* Exponential moving average of parameters: avg = decay avg + (1 - decay) W
+ * over n FP32 values (weights averaged over the last steps of training). */
+int nn_ema(float *avg, const float *W, long long n, float decay, void *stream);
+
 /* BF16 copies of FP32 W [taps][Cin][Cout]: wt [taps][Cout][Cin] for the
  * forward pass and wd [taps][Cin][Cout] with reversed taps for the input
  * gradient (either may be NULL). */

@@ -435,6 +435,11 @@ __global__ void adam_kernel(float *W, float *m, float *v, const float *grad, lon
     }
 }
 
+__global__ void ema_kernel(float *avg, const float *W, long long n, float decay)
+{
+    GRID_LOOP(i, n) avg[i] = fmaf(decay, avg[i] - W[i], W[i]);
+}
+
 __global__ void weights_bf16_kernel(const float *W, __nv_bfloat16 *wt, __nv_bfloat16 *wd, int taps, int Cin, int Cout)
 {
     GRID_LOOP(idx, (long long)taps * Cin * Cout) {
@@ -792,6 +797,14 @@ int nn_unpack(const void *in, const float *pred, int Cp, double *abs3d, double *
     unpack_kernel<<<grid1d((long long)D * H * W), 256, 0, (cudaStream_t)stream>>>(
         (const __nv_bfloat16 *)in, pred, Cp, abs3d, sfc_dir, sfc_dif, D, H, W, dz, flux);
     return check_launch("nn_unpack");
+}
+
+int nn_ema(float *avg, const float *W, long long n, float decay, void *stream)
+{
+    if (!avg || !W || n < 0 || !(decay >= 0.f && decay <= 1.f)) return inval("nn_ema: bad argument");
+    if (n == 0) return NN_OK;
+    ema_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>(avg, W, n, decay);
+    return check_launch("nn_ema");
 }
 
 int nn_weights_bf16(const float *W, void *wt, void *wd, int ksize, int Cin, int Cout, void *stream)

@@ -52,6 +52,7 @@ class Conv:
         self.mb, self.vb = torch.zeros_like(self.b), torch.zeros_like(self.b)
         self.wt = torch.empty(self.W.numel(), dtype=torch.bfloat16, device=dev)
         self.wd = torch.empty_like(self.wt)
+        self.We, self.be = self.W.clone(), self.b.clone()     # moving averages
         self.refresh()
 
     def refresh(self, stream=None):
@@ -73,6 +74,15 @@ class Conv:
         nn.nn_adam(self.W, self.mW, self.vW, self.gW, lr, t, weight_decay=weight_decay, stream=stream)
         nn.nn_adam(self.b, self.mb, self.vb, self.gb, lr, t, stream=stream)
         self.refresh(stream)
+
+    def ema(self, decay, stream=None):
+        nn.nn_ema(self.We, self.W, decay, stream)
+        nn.nn_ema(self.be, self.b, decay, stream)
+
+    def apply_ema(self):
+        self.W.copy_(self.We)
+        self.b.copy_(self.be)
+        self.refresh()
 
     def state(self):
         return {"W": self.W.cpu().numpy(), "b": self.b.cpu().numpy()}
@@ -219,6 +229,15 @@ class UNet:
         self.t += 1
         for c in self.layers():
             c.step(lr, self.t, weight_decay, stream)
+
+    def ema(self, decay, stream=None):
+        for c in self.layers():
+            c.ema(decay, stream)
+
+    def apply_ema(self):
+        """Replace the weights by their moving averages."""
+        for c in self.layers():
+            c.apply_ema()
 
     def state(self):
         return [c.state() for c in self.layers()]
@@ -367,8 +386,12 @@ def channel_weights(samples, device="cuda"):
     return torch.tensor((1.0 / np.maximum(v, 1e-12)).astype(np.float32), device=device)
 
 
-def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, seed=0):
-    """Adam over the samples (one scene per step), cosine learning-rate decay."""
+def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, seed=0, ema=True):
+    """Adam over the samples (one scene per step), cosine learning-rate decay.
+
+    With `ema` the returned network holds the moving average of its weights
+    over roughly the last tenth of the steps (decay 1 - 10 / steps).
+    """
     torch = _torch()
     rng = np.random.default_rng(seed)
     if chw is None:
@@ -385,11 +408,15 @@ def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, se
             net.backward(s.x, s.shape)
             rate = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * k / max(1, steps - 1)))
             net.step(rate)
+            if ema:
+                net.ema(1.0 - 10.0 / max(steps, 20))
             k += 1
             if k % 16 == 0 or k == steps:
                 losses.append((k, float(loss.item())))
                 if log:
                     log(f"step {k}/{steps} loss {losses[-1][1]:.4f} ({time.time() - t0:.0f}s)")
+    if ema:
+        net.apply_ema()
     torch.cuda.synchronize()
     return losses
 

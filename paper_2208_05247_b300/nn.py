@@ -34,6 +34,7 @@ def _lib():
             "nn_copy_channels": ([P, i32, i32, P, i32, i32, i64, i32, i32, P], i32),
             "nn_mse": ([P, i32, P, i32, P, P, i64, P, P], i32),
             "nn_adam": ([P, P, P, P, i64, f32, f32, f32, f32, i32, f32, P], i32),
+            "nn_ema": ([P, P, i64, f32, P], i32),
             "nn_weights_bf16": ([P, P, P, i32, i32, i32, P], i32),
             "nn_pack_inputs": ([P] * 11 + [i32] * 3 + [f64, f64, P], i32),
             "nn_direct_transmittance": ([P, P] + [i32] * 3 + [f64] * 5 + [P, P, P], i32),
@@ -118,6 +119,11 @@ def nn_mse(pred, Cp, target, Cuse, chw, grad, vox, loss, stream=None):
 def nn_adam(W, m, v, grad, lr, step, b1=0.9, b2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
     _check(_lib().nn_adam(_p(W), _p(m), _p(v), _p(grad), W.numel(), lr, b1, b2, eps, step, weight_decay,
                           _s(stream)))
+
+
+def nn_ema(avg, W, decay, stream=None):
+    """avg = decay * avg + (1 - decay) * W (FP32 CUDA tensors of equal size)."""
+    _check(_lib().nn_ema(_p(avg), _p(W), W.numel(), float(decay), _s(stream)))
 
 
 def nn_weights_bf16(W, wt, wd, ksize, Cin, Cout, stream=None):

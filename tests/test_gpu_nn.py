@@ -238,6 +238,13 @@ def test_adam_step():
         v = 0.999 * v + 0.001 * g * g
         W = W - 1e-3 * (m / (1 - 0.9 ** step)) / (np.sqrt(v / (1 - 0.999 ** step)) + 1e-8)
     assert np.allclose(Wd.cpu().numpy(), W, rtol=1e-5, atol=1e-6)
+    # moving average of the parameters
+    avg = f32(np.zeros(1000, np.float32))
+    ref = np.zeros(1000)
+    for d in (0.5, 0.9):
+        nn.nn_ema(avg, Wd, d)
+        ref = d * ref + (1 - d) * Wd.cpu().numpy().astype(np.float64)
+    assert np.allclose(avg.cpu().numpy(), ref, rtol=1e-6, atol=1e-7)
 
 
 def test_direct_transmittance_closed_form_and_oracle():
