@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--no-coupled", action="store_true", help="skip the graph-replay coupled-step leg")
     p.add_argument("--no-birth", action="store_true", help="skip the Sobol-vs-Philox start position leg")
     p.add_argument("--denoise-train", type=int, default=512, help="training scenes of the denoiser leg")
+    p.add_argument("--denoise-epochs", type=int, default=16, help="training epochs of the denoiser leg")
     p.add_argument("--no-autotune", action="store_true",
                    help="use the default launch parameters and the --coarse grid")
     p.add_argument("--coarse", type=int, nargs=3, default=None,
@@ -222,13 +223,14 @@ def denoise_leg(args):
     t_pairs = time.time() - t0
     net = denoise.UNet(seed=0)
     t0 = time.time()
-    losses = denoise.train(net, pairs, epochs=4, lr=1e-3)
+    losses = denoise.train(net, pairs, epochs=args.denoise_epochs, lr=1e-3)
     t_train = time.time() - t0
     del pairs
     res = denoise.evaluate(net, list(range(1512, 1520)), shape, truth_ppc=4096, workers=os.cpu_count() or 8)
     return {"workload": "one quadrature point on cumulus 128x128x128 (dx=dy=50 m, dz=25 m), sza 0/30/60, "
                         "held-out seeds 1512-1519, truth 4096 photons/column",
-            "training": {"scenes": args.denoise_train, "epochs": 4, "pairs_s": t_pairs, "train_s": t_train,
+            "training": {"scenes": args.denoise_train, "epochs": args.denoise_epochs, "pairs_s": t_pairs,
+                         "train_s": t_train, "weights": "moving average over the last tenth of the steps",
                          "loss_first": losses[0][1], "loss_last": losses[-1][1]},
             "plain": res["plain"], "denoised": res["denoised"], "noisy_input": res["noisy_input"],
             "plain_ppc_to_match": {"ghi": res["plain_ppc_to_match_ghi"], "hr": res["plain_ppc_to_match_hr"]},

@@ -534,7 +534,7 @@ def main(argv=None):
     p = argparse.ArgumentParser(description="train and evaluate the 3D U-Net denoiser")
     p.add_argument("--train", type=int, default=512, help="training scenes (seeds 1000...)")
     p.add_argument("--eval", type=int, default=64, help="held-out scenes (seeds after the training ones)")
-    p.add_argument("--epochs", type=int, default=4)
+    p.add_argument("--epochs", type=int, default=16)
     p.add_argument("--lr", type=float, default=1e-3)
     p.add_argument("--shape", type=int, nargs=3, default=(128, 128, 128), help="nz ny nx")
     p.add_argument("--truth-ppc", type=int, default=16384)
