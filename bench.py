@@ -226,11 +226,12 @@ def denoise_leg(args):
     losses = denoise.train(net, pairs, epochs=args.denoise_epochs, lr=1e-3)
     t_train = time.time() - t0
     del pairs
-    res = denoise.evaluate(net, list(range(1512, 1520)), shape, truth_ppc=4096, workers=os.cpu_count() or 8)
+    res = denoise.evaluate(net, list(range(1512, 1528)), shape, truth_ppc=16384, workers=os.cpu_count() or 8)
     return {"workload": "one quadrature point on cumulus 128x128x128 (dx=dy=50 m, dz=25 m), sza 0/30/60, "
-                        "held-out seeds 1512-1519, truth 4096 photons/column",
+                        "held-out seeds 1512-1527, truth 16384 photons/column",
             "training": {"scenes": args.denoise_train, "epochs": args.denoise_epochs, "pairs_s": t_pairs,
                          "train_s": t_train, "weights": "moving average over the last tenth of the steps",
+                         "guards": getattr(net, "train_log", None),
                          "loss_first": losses[0][1], "loss_last": losses[-1][1]},
             "plain": res["plain"], "denoised": res["denoised"], "noisy_input": res["noisy_input"],
             "plain_ppc_to_match": {"ghi": res["plain_ppc_to_match_ghi"], "hr": res["plain_ppc_to_match_hr"]},

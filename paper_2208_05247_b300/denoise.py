@@ -84,6 +84,12 @@ class Conv:
         self.b.copy_(self.be)
         self.refresh()
 
+    def rollback(self):
+        """Back to the averaged weights with fresh Adam moments."""
+        self.apply_ema()
+        for t in (self.mW, self.vW, self.mb, self.vb):
+            t.zero_()
+
     def state(self):
         return {"W": self.W.cpu().numpy(), "b": self.b.cpu().numpy()}
 
@@ -239,6 +245,10 @@ class UNet:
         for c in self.layers():
             c.apply_ema()
 
+    def rollback(self):
+        for c in self.layers():
+            c.rollback()
+
     def state(self):
         return [c.state() for c in self.layers()]
 
@@ -391,6 +401,12 @@ def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, se
 
     With `ema` the returned network holds the moving average of its weights
     over roughly the last tenth of the steps (decay 1 - 10 / steps).
+
+    Two guards keep long runs from collapsing (one 16-epoch run did, while
+    repeats of the same run did not): a step whose loss is non-finite or
+    above 8x the running mean loss is skipped, and if the running mean rises
+    above 4x its lowest value the weights roll back to their moving average
+    with fresh Adam moments. `net.train_log` records both.
     """
     torch = _torch()
     rng = np.random.default_rng(seed)
@@ -400,24 +416,40 @@ def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, se
     losses = []
     k = 0
     t0 = time.time()
+    run, best, skipped, rollbacks = None, None, 0, 0
     for ep in range(epochs):
         for idx in rng.permutation(len(samples)):
             s = samples[idx]
             net.forward(s.x, s.shape)
             loss = net.loss_and_grad(s.target, s.shape, chw)
+            lv = float(loss.item())
+            k += 1
+            if not math.isfinite(lv) or (run is not None and k > 64 and lv > 8.0 * run):
+                skipped += 1
+                continue
+            run = lv if run is None else 0.98 * run + 0.02 * lv
+            if k > 256:
+                best = run if best is None else min(best, run)
+                if ema and run > 4.0 * best:
+                    net.rollback()
+                    rollbacks += 1
+                    run = best
+                    continue
             net.backward(s.x, s.shape)
-            rate = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * k / max(1, steps - 1)))
+            rate = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * (k - 1) / max(1, steps - 1)))
             net.step(rate)
             if ema:
                 net.ema(1.0 - 10.0 / max(steps, 20))
-            k += 1
             if k % 16 == 0 or k == steps:
-                losses.append((k, float(loss.item())))
+                losses.append((k, lv))
                 if log:
-                    log(f"step {k}/{steps} loss {losses[-1][1]:.4f} ({time.time() - t0:.0f}s)")
+                    log(f"step {k}/{steps} loss {lv:.4f} ({time.time() - t0:.0f}s)")
     if ema:
         net.apply_ema()
+    net.train_log = {"skipped_steps": skipped, "rollbacks": rollbacks}
     torch.cuda.synchronize()
+    if not losses:
+        losses.append((k, run if run is not None else float("nan")))
     return losses
 
 
@@ -557,7 +589,7 @@ def main(argv=None):
     del pairs
     res = evaluate(net, list(range(1000 + a.train, 1000 + a.train + a.eval)), shape, truth_ppc=a.truth_ppc,
                    workers=a.workers, plain_ppc=tuple(a.plain_ppc), spectral=a.spectral)
-    res.update({"train_scenes": a.train, "epochs": a.epochs, "hi_ppc": a.hi_ppc, "pairs_s": t_pairs, "train_s": t_train,
+    res.update({"train_scenes": a.train, "epochs": a.epochs, "hi_ppc": a.hi_ppc, "guards": net.train_log, "pairs_s": t_pairs, "train_s": t_train,
                 "loss_first": losses[0][1], "loss_last": losses[-1][1], "params": net.n_params(),
                 "forward_gflop": net.flops(shape) / 1e9})
     print(json.dumps(res), flush=True)
