@@ -68,7 +68,11 @@ int nn_conv3d_fwd(const void *in, const void *wt, const float *bias, void *out_b
                   int H, int W, int Cin, int Cout, int ksize, int relu, void *stream);
 
 /* gw[t][i][o] += sum_p in[p + off(t)][i] gout[p][o]; gb[o] += sum_p gout[p][o]
- * (gb may be NULL). FP32 atomics: zero gw and gb first. Channels multiples of 8. */
+ * (gb may be NULL). FP32 atomics: zero gw and gb first. Channels multiples of 8.
+ * 3x3x3 kernels with channel counts that are multiples of 16 run on tcgen05
+ * (unless NN_CONV_MMA_SYNC is selected): the (tap, input channel) rows and the
+ * voxel reduction are transposed into the tensor core's operand layout in
+ * shared memory by the CTA's threads. */
 int nn_conv3d_wgrad(const void *in, const void *gout, float *gw, float *gb, int N, int D, int H, int W, int Cin,
                     int Cout, int ksize, void *stream);
 

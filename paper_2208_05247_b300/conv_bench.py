@@ -3,13 +3,16 @@
     python -m paper_2208_05247_b300.conv_bench --shape 128 128 128 --cin 32 --cout 32 [--path tcgen05]
     python -m paper_2208_05247_b300.conv_bench --unet 128
     python -m paper_2208_05247_b300.conv_bench --layers 128
+    python -m paper_2208_05247_b300.conv_bench --wgrad 128
 
 Prints one JSON line per kernel: CUDA-event time per launch (after warm-up, on
 the current stream) and the dense FLOP rate 2 * 27 * Cin * Cout * voxels / t.
 With --unet D it times the whole U-Net forward and backward at D^3 instead;
 with --layers D every 3x3x3 layer shape of the U-Net's forward pass and input
 gradients at D^3, with the mma.sync kernel, the per-tap tcgen05 kernel and the
-default tcgen05 choice (halo-tiled where it fits).
+default tcgen05 choice (halo-tiled where it fits); with --wgrad D the weight
+gradient of every 3x3x3 forward layer at D^3 (mma.sync and tcgen05; the same
+2 * 27 * Cin * Cout * voxels FLOPs).
 """
 from __future__ import annotations
 
@@ -49,6 +52,35 @@ def time_layer(shape, cin, cout, path, reps=10, warmup=3, relu=True):
     finally:
         nn.nn_set_conv_path(old)
     return {"kernel": path, "shape": list(shape), "cin": cin, "cout": cout, "us": 1e3 * ms,
+            "tflops": 2.0 * 27 * cin * cout * vox / (ms * 1e-3) / 1e12}
+
+
+def time_wgrad(shape, cin, cout, path, reps=10, warmup=3):
+    import torch
+    vox = int(np.prod(shape))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(vox * cin, device="cuda", generator=g).to(torch.bfloat16)
+    gy = torch.randn(vox * cout, device="cuda", generator=g).to(torch.bfloat16)
+    gw = torch.zeros(27 * cin * cout, dtype=torch.float32, device="cuda")
+    gb = torch.zeros(cout, dtype=torch.float32, device="cuda")
+    old = nn.nn_set_conv_path(PATHS[path])
+    try:
+        for _ in range(warmup):
+            nn.nn_conv3d_wgrad(x, gy, gw, gb, 1, *shape, cin, cout, 3)
+        ms = None
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                nn.nn_conv3d_wgrad(x, gy, gw, gb, 1, *shape, cin, cout, 3)
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / reps
+            ms = t if ms is None else min(ms, t)
+        nn.nn_status()
+    finally:
+        nn.nn_set_conv_path(old)
+    return {"wgrad": path, "shape": list(shape), "cin": cin, "cout": cout, "us": 1e3 * ms,
             "tflops": 2.0 * 27 * cin * cout * vox / (ms * 1e-3) / 1e12}
 
 
@@ -104,10 +136,17 @@ def main(argv=None):
     p.add_argument("--cout", type=int, default=32)
     p.add_argument("--path", choices=sorted(PATHS), default=None, help="one kernel (default: mma.sync and tcgen05)")
     p.add_argument("--reps", type=int, default=20)
+    p.add_argument("--bwd", action="store_true", help="time the weight gradient of --shape instead")
     p.add_argument("--unet", type=int, default=0, help="time the whole U-Net at this edge length instead")
     p.add_argument("--layers", type=int, default=0, help="time every U-Net layer shape at this edge length")
+    p.add_argument("--wgrad", type=int, default=0, help="time every U-Net weight gradient at this edge length")
     a = p.parse_args(argv)
     build.build()
+    if a.wgrad:
+        for shape, cin, cout in unet_layers(a.wgrad)[:11]:
+            for path in ("mma.sync", "tcgen05"):
+                print(json.dumps(time_wgrad(shape, cin, cout, path, reps=a.reps)), flush=True)
+        return
     if a.layers:
         for shape, cin, cout in unet_layers(a.layers):
             for path in ("mma.sync", "tcgen05-tap", "tcgen05"):
@@ -117,6 +156,8 @@ def main(argv=None):
     for path in paths:
         if a.unet:
             r = time_unet(a.unet, path)
+        elif a.bwd:
+            r = time_wgrad(tuple(a.shape), a.cin, a.cout, path, reps=a.reps)
         else:
             r = time_layer(tuple(a.shape), a.cin, a.cout, path, reps=a.reps)
         print(json.dumps(r), flush=True)

@@ -566,6 +566,256 @@ __global__ void __launch_bounds__(kHaloThreads, 1) conv3d_tc_halo_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient on tcgen05: gW[t][i][o] += sum_p in[p + off(t)][i] gout[p][o].
+// As a GEMM the rows (M) are the 27 * Cin (tap, input channel) pairs in the
+// order of gW, the columns (N) the output channels, and the reduction (K) runs
+// over voxels. Both tensors are stored voxel-major with channels contiguous,
+// which is the MN-major operand layout: a TMA box of KV voxels x CK channels
+// (rows of CK * 2 bytes with the matching swizzle) is a stack of tcgen05
+// MN-major swizzle atoms with the voxel as K index, so no thread touches the
+// operands. For every tile of KV voxels the producer loads, per row block of
+// 128 (tap, channel) rows, 128 / CK activation boxes shifted by their tap's
+// offset (zeros outside the volume: the "same" padding) and once the gout box
+// of NT output channels, which the CTA's MG row blocks share; each row block
+// accumulates into its own 128 x NT tensor-memory accumulator. A CTA reduces
+// over a range of voxel tiles and adds its partial sums to gW with FP32
+// atomics.
+//
+// Shared-memory descriptors of an MN-major swizzled operand: the leading byte
+// offset is the distance between swizzle atoms along M (or N), the stride
+// byte offset the distance between groups of 8 K rows.
+// ---------------------------------------------------------------------------
+struct WgradArgs {
+    int N, D, H, W, Cin, Cout;
+    int Wb, Hb, Db, KV;          // voxel box (Wb * Hb * Db = KV voxels = K per stage)
+    int tw, th, td;              // boxes per axis
+    int ntiles, stride;          // voxel tiles; CTA z takes tiles z, z + stride, ...
+    int groups, MG, NT, S;       // 128-row blocks, row blocks per CTA, N tile, stages
+    int CK, CKB;                 // channels per activation / gout box
+    uint32_t stage_bytes, cols;  // bytes per stage, tensor-memory columns per accumulator
+};
+
+__device__ __forceinline__ uint64_t umma_desc_mn(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes,
+                                                 uint64_t layout)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | (layout << 61);
+}
+
+__device__ __forceinline__ uint64_t swizzle_layout(int ck) { return ck == 64 ? 2 : ck == 32 ? 4 : 6; }
+
+constexpr int kWgMaxStages = 8;
+
+__global__ void __launch_bounds__(kThreads) conv3d_wgrad_tc_kernel(const __grid_constant__ CUtensorMap map_x,
+                                                                   const __grid_constant__ CUtensorMap map_g,
+                                                                   float *__restrict__ gw, const WgradArgs P)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    __shared__ __align__(8) unsigned long long bar_full[kWgMaxStages], bar_empty[kWgMaxStages], bar_done;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = P.S, NT = P.NT;
+    const int g0 = blockIdx.x * P.MG;                               // first row block of this CTA
+    const int mg = min(P.MG, P.groups - g0);                        // row blocks held
+    const int n0 = blockIdx.y * NT;
+    // all CTAs sweep the volume together (tile z, z + stride, ...), so the
+    // planes that the z taps read again stay in L2
+    const int t_begin = blockIdx.z;
+    const int nt_local = t_begin < P.ntiles ? (P.ntiles - t_begin + P.stride - 1) / P.stride : 0;
+    const int atoms = 128 / P.CK, chunks = P.Cin / P.CK, batoms = NT / P.CKB;
+    const uint32_t a_atom = (uint32_t)P.KV * P.CK * 2, b_atom = (uint32_t)P.KV * P.CKB * 2;
+    const uint32_t a_block = 128u * P.KV * 2;                       // bytes of one 128-row block
+    const uint32_t bytes = ((uint32_t)mg * 128 + NT) * P.KV * 2;    // bytes landing per stage
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(smem_u32(&bar_full[s]), 1);
+            mbar_init(smem_u32(&bar_empty[s]), 1);
+        }
+        mbar_init(smem_u32(&bar_done), 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(P.MG * P.cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    int issued = 0;
+    if (warp == 0) {
+        // ---- producer: the lanes of warp 0 share a stage's boxes (at most 36) ----
+        // box b < mg * atoms: activation atom (row block b / atoms, tap and
+        // channel chunk of its rows); the rest: gout atoms of NT / batoms channels
+        const int nbox = mg * atoms + batoms;
+        int bc[2], bdx[2], bdy[2], bdz[2], bmap[2];
+        uint32_t boff[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int bx = lane + 32 * q;
+            bc[q] = bdx[q] = bdy[q] = bdz[q] = 0;
+            bmap[q] = -1;                                  // -1: no box for this lane
+            boff[q] = 0;
+            if (bx < mg * atoms) {
+                const int m = bx / atoms, j = bx - m * atoms;
+                int a = (g0 + m) * atoms + j;              // global (tap, chunk) atom
+                int tap = a / chunks;
+                if (tap > 26) { tap = 26; a = 26 * chunks; }   // rows past 27 * Cin: loaded, not stored
+                bc[q] = (a - tap * chunks) * P.CK;
+                bdz[q] = tap / 9 - 1; bdy[q] = (tap / 3) % 3 - 1; bdx[q] = tap % 3 - 1;
+                bmap[q] = 0;
+                boff[q] = (uint32_t)m * a_block + (uint32_t)j * a_atom;
+            } else if (bx < nbox) {
+                const int j = bx - mg * atoms;
+                bc[q] = n0 + j * P.CKB;
+                bmap[q] = 1;
+                boff[q] = (uint32_t)P.MG * a_block + (uint32_t)j * b_atom;
+            }
+        }
+        // first tile's coordinates; later tiles add the stride digit by digit
+        int t = t_begin;
+        int tx = t % P.tw; t /= P.tw;
+        int ty = t % P.th; t /= P.th;
+        int tz = t % P.td;
+        int n = t / P.td;
+        t = P.stride;
+        const int sx = t % P.tw; t /= P.tw;
+        const int sy = t % P.th; t /= P.th;
+        const int sz = t % P.td;
+        const int sn = t / P.td;
+        int s = 0;
+        uint32_t ph = 0;                                   // parity of the stage's next reuse wait
+        for (int i = 0; i < nt_local; ++i) {
+            int ok = 1;
+            if (lane == 0) {
+                if (i >= S && !mbar_wait(smem_u32(&bar_empty[s]), ph ^ 1u)) ok = 0;
+                if (*(volatile int *)&s_abort) ok = 0;
+                if (!ok) s_abort = 1;
+                else mbar_expect_tx(smem_u32(&bar_full[s]), bytes);
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            const uint32_t st = base + (uint32_t)s * P.stage_bytes, fb = smem_u32(&bar_full[s]);
+            const int w0 = tx * P.Wb, h0 = ty * P.Hb, d0 = tz * P.Db;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (bmap[q] == 0)
+                    tma_load_5d(st + boff[q], &map_x, fb, bc[q], w0 + bdx[q], h0 + bdy[q], d0 + bdz[q], n);
+                else if (bmap[q] == 1)
+                    tma_load_5d(st + boff[q], &map_g, fb, bc[q], w0, h0, d0, n);
+            }
+            ++issued;
+            if (++s == S) { s = 0; ph ^= 1u; }
+            int c = 0;
+            tx += sx; if (tx >= P.tw) { tx -= P.tw; c = 1; }
+            ty += sy + c; c = 0; if (ty >= P.th) { ty -= P.th; c = 1; }
+            tz += sz + c; c = 0; if (tz >= P.td) { tz -= P.td; c = 1; }
+            n += sn + c;
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer: KV / 16 products per row block and stage ----
+            // kind::f16, FP32 accumulator, BF16 A and B, both MN-major (bits 15, 16)
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                                   ((uint32_t)(NT >> 3) << 17) | (8u << 24);
+            // descriptors of stage 0; a stage's own differ in the start-address field only
+            const uint64_t da = umma_desc_mn(base, a_atom, 8 * P.CK * 2, swizzle_layout(P.CK));
+            const uint64_t db = umma_desc_mn(base + (uint32_t)P.MG * a_block, b_atom, 8 * P.CKB * 2,
+                                             swizzle_layout(P.CKB));
+            const uint32_t ka = 16 * P.CK * 2 >> 4, kb = 16 * P.CKB * 2 >> 4, mb = a_block >> 4;
+            const int ksteps = P.KV / 16;
+            int s = 0;
+            uint32_t ph = 0;
+            for (int i = 0; i < nt_local; ++i) {
+                if (*(volatile int *)&s_abort || !mbar_wait(smem_u32(&bar_full[s]), ph)) {
+                    s_abort = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint64_t so = (uint64_t)((uint32_t)s * P.stage_bytes >> 4);
+                for (int m = 0; m < mg; ++m)
+                    for (int k = 0; k < ksteps; ++k)
+                        umma_f16(tmem + (uint32_t)m * P.cols, da + so + (uint64_t)(m * mb + k * ka),
+                                 db + so + (uint64_t)(k * kb), idesc, (i | k) != 0);
+                umma_commit(smem_u32(&bar_empty[s]));
+                if (++s == S) { s = 0; ph ^= 1u; }
+            }
+            umma_commit(smem_u32(&bar_done));
+        }
+        __syncwarp();
+    }
+
+    // ---- epilogue: each row block's 128 x NT partial sums into gW ----
+    const bool done = mbar_wait(smem_u32(&bar_done), 0);
+    tc_fence_after();
+    const bool valid = done && nt_local > 0 && !*(volatile int *)&s_abort;
+    const int rows = 27 * P.Cin;
+#pragma unroll 1
+    for (int m = 0; m < mg; ++m) {
+        const int r = (g0 + m) * 128 + warp * 32 + lane;
+#pragma unroll 1
+        for (int cc = 0; cc < NT; cc += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)m * P.cols + (uint32_t)cc, v);
+            if (!valid || r >= rows) continue;
+            float4 *dst = reinterpret_cast<float4 *>(gw + (long long)r * P.Cout + n0 + cc);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 t = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                if (t.x != 0.f || t.y != 0.f || t.z != 0.f || t.w != 0.f) atomicAdd(dst + q, t);
+            }
+        }
+    }
+
+    // ---- after an abort: let this CTA's copies land before its memory goes ----
+    if (threadIdx.x == 0 && *(volatile int *)&s_abort) {
+        for (int i = (issued > S ? issued - S : 0); i < issued; ++i)
+            mbar_wait(smem_u32(&bar_full[i % S]), (i / S) & 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(P.MG * P.cols));
+    }
+}
+
+// gb[o] += sum over voxels of gout[p][o]. Thread t of a block owns the 8
+// channels 8 (t mod Cout/8) .. +7 and every (blockDim / (Cout/8))-th voxel of
+// the block's share; partial sums meet in shared memory, then one global
+// atomic per channel and block.
+__global__ void bias_grad_kernel(const __nv_bfloat16 *__restrict__ gout, float *__restrict__ gb, long long V, int Cout)
+{
+    extern __shared__ float part[];
+    for (int o = threadIdx.x; o < Cout; o += blockDim.x) part[o] = 0.f;
+    __syncthreads();
+    const int cbs = Cout / 8, lanes = blockDim.x / cbs;
+    const int cb = threadIdx.x % cbs, lv = threadIdx.x / cbs;
+    if (lv < lanes) {
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (long long v = (long long)blockIdx.x * lanes + lv; v < V; v += (long long)gridDim.x * lanes) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(gout + v * Cout + cb * 8));
+            const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&q);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] += __bfloat162float(e[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) atomicAdd(&part[cb * 8 + j], acc[j]);
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < Cout; o += blockDim.x)
+        if (part[o] != 0.f) atomicAdd(gb + o, part[o]);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -869,6 +1119,143 @@ int conv3d_fwd(const void *in, const void *wt, const float *bias, void *out_bf16
     if (CK == 64) return dispatch_bn<64>(BN, mx, mw, bias, ob, out_f32, P, (int)ntiles, ny, st, err, errlen);
     if (CK == 32) return dispatch_bn<32>(BN, mx, mw, bias, ob, out_f32, P, (int)ntiles, ny, st, err, errlen);
     return dispatch_bn<16>(BN, mx, mw, bias, ob, out_f32, P, (int)ntiles, ny, st, err, errlen);
+}
+
+// Weight gradient of a 3x3x3 convolution on tcgen05 (Cin, Cout multiples of
+// 16). gw and gb accumulate (FP32).
+bool wgrad_supported(int Cin, int Cout) { return supported(Cin, Cout); }
+
+namespace {
+CUtensorMapSwizzle swizzle_for(int ck)
+{
+    return ck == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : ck == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+}
+}  // namespace
+
+int conv3d_wgrad(const void *in, const void *gout, float *gw, float *gb, int N, int D, int H, int W, int Cin,
+                 int Cout, cudaStream_t st, char *err, size_t errlen)
+{
+    if (!wgrad_supported(Cin, Cout)) {
+        snprintf(err, errlen, "conv3d_wgrad_tc: unsupported channels %d -> %d", Cin, Cout);
+        return NN_E_INVAL;
+    }
+    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(gout) | reinterpret_cast<uintptr_t>(gw)) &
+        15u) {
+        snprintf(err, errlen, "conv3d_wgrad_tc: buffers must be 16-byte aligned");
+        return NN_E_INVAL;
+    }
+    if (Cout / 8 > 256) {
+        snprintf(err, errlen, "conv3d_wgrad_tc: bias gradient takes at most 2048 channels");
+        return NN_E_INVAL;
+    }
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) {
+        snprintf(err, errlen, "conv3d_wgrad_tc: cuTensorMapEncodeTiled unavailable");
+        return NN_E_CUDA;
+    }
+    WgradArgs P{};
+    P.N = N; P.D = D; P.H = H; P.W = W; P.Cin = Cin; P.Cout = Cout;
+    // N tile: the widest of 256, 192, 128, 96, 64, 48, 32, 16 dividing Cout
+    for (int c : {256, 192, 128, 96, 64, 48, 32, 16})
+        if (Cout % c == 0) { P.NT = c; break; }
+    P.CK = Cin % 64 == 0 ? 64 : Cin % 32 == 0 ? 32 : 16;
+    P.CKB = P.NT % 64 == 0 ? 64 : P.NT % 32 == 0 ? 32 : 16;
+    P.cols = tmem_cols(P.NT);
+    P.groups = (27 * Cin + 127) / 128;
+    // Launch plan (measured on the U-Net's layers; TMA issue of many small
+    // boxes, not the tensor core, bounds the narrow layers, so the plan keeps
+    // boxes at 64 voxels where it can and several producers per SM):
+    //   N tile 192-256: two row blocks share each gout box, one CTA per SM;
+    //   N tile 128: one row block, four CTAs per SM;
+    //   narrower: two row blocks, two CTAs per SM.
+    int per_sm;
+    uint32_t budget;                                   // stage-ring bytes per CTA
+    if (P.cols == 256) { P.MG = 2; per_sm = 1; budget = 200 * 1024; }
+    else if (P.NT == 128) { P.MG = 1; per_sm = 4; budget = 40 * 1024; }
+    else { P.MG = 2; per_sm = 2; budget = 96 * 1024; }
+    if (P.MG > P.groups) P.MG = 1;
+    // voxel box of KV voxels (x first, then y, then z): 64 if two stages fit
+    P.KV = (uint32_t)(P.MG * 128 + P.NT) * 64 * 2 * 2 <= budget ? 64 : 32;
+    P.Wb = pow2_at_least(W, P.KV);
+    P.Hb = pow2_at_least(H, P.KV / P.Wb);
+    P.Db = P.KV / (P.Wb * P.Hb);
+    P.tw = (W + P.Wb - 1) / P.Wb;
+    P.th = (H + P.Hb - 1) / P.Hb;
+    P.td = (D + P.Db - 1) / P.Db;
+    const long long ntiles = (long long)N * P.td * P.th * P.tw;
+    if (ntiles > 0x7fffffffLL) {
+        snprintf(err, errlen, "conv3d_wgrad_tc: volume too large");
+        return NN_E_INVAL;
+    }
+    P.ntiles = (int)ntiles;
+    P.stage_bytes = (uint32_t)(P.MG * 128 + P.NT) * P.KV * 2;
+    P.S = (int)std::min<uint32_t>(kWgMaxStages, budget / P.stage_bytes);
+    if (P.S < 2) {
+        snprintf(err, errlen, "conv3d_wgrad_tc: no stage plan for %d -> %d", Cin, Cout);
+        return NN_E_INVAL;
+    }
+    // one wave of CTAs, per_sm on each SM
+    const long long xy = (long long)((P.groups + P.MG - 1) / P.MG) * (Cout / P.NT);
+    long long splits = std::max<long long>(1, (long long)num_sms() * per_sm / xy);
+    splits = std::min<long long>(splits, P.ntiles);
+    P.stride = (int)splits;
+    // Shared memory caps the CTAs per SM at the number whose tensor
+    // memory (MG * cols columns each) fits in 512 columns: one more CTA of
+    // this size would exceed the SM's shared memory.
+    static int sm_smem = 0;
+    if (!sm_smem) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+            sm_smem = 233472;
+    }
+    const int tmem_fit = sm_smem / (512 / (P.MG * (int)P.cols) + 1) + 1;
+    // ... and at per_sm, so that the wave spreads evenly over the SMs
+    const int wave_fit = sm_smem / (per_sm + 1) + 1;
+    const int smem = std::max<int>((int)(P.S * P.stage_bytes) + 1024, std::max(tmem_fit, wave_fit));
+
+    CUtensorMap mx, mg;
+    const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
+    const cuuint64_t gx[5] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)N};
+    const cuuint64_t sx[4] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2,
+                              (cuuint64_t)D * H * W * Cin * 2};
+    const cuuint32_t bx[5] = {(cuuint32_t)P.CK, (cuuint32_t)P.Wb, (cuuint32_t)P.Hb, (cuuint32_t)P.Db, 1};
+    CUresult r1 = enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(in), gx, sx, bx, ones,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(P.CK), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const cuuint64_t gg[5] = {(cuuint64_t)Cout, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)N};
+    const cuuint64_t sg[4] = {(cuuint64_t)Cout * 2, (cuuint64_t)W * Cout * 2, (cuuint64_t)H * W * Cout * 2,
+                              (cuuint64_t)D * H * W * Cout * 2};
+    const cuuint32_t bg[5] = {(cuuint32_t)P.CKB, (cuuint32_t)P.Wb, (cuuint32_t)P.Hb, (cuuint32_t)P.Db, 1};
+    CUresult r2 = enc(&mg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(gout), gg, sg, bg, ones,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(P.CKB), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
+        snprintf(err, errlen, "conv3d_wgrad_tc: tensor map encoding failed (%d, %d)", (int)r1, (int)r2);
+        return NN_E_INVAL;
+    }
+    static bool attr_set = false;
+    cudaError_t e = cudaSuccess;
+    if (!attr_set) {
+        e = allow_max_smem(reinterpret_cast<const void *>(conv3d_wgrad_tc_kernel));
+        attr_set = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) {
+        conv3d_wgrad_tc_kernel<<<dim3((unsigned)((P.groups + P.MG - 1) / P.MG), (unsigned)(Cout / P.NT),
+                                      (unsigned)splits),
+                                 kThreads, smem, st>>>(mx, mg, gw, P);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && gb) {
+        const long long V = (long long)N * D * H * W;
+        bias_grad_kernel<<<num_sms() * 4, 256, Cout * sizeof(float), st>>>((const __nv_bfloat16 *)gout, gb, V, Cout);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "conv3d_wgrad_tc: %s", cudaGetErrorString(e));
+        return NN_E_CUDA;
+    }
+    return NN_OK;
 }
 
 // Read and clear the device-side status word (bit 0: an mbarrier wait timed out).

@@ -28,6 +28,9 @@ bool supported(int Cin, int Cout);
 int conv3d_fwd(const void *in, const void *wt, const float *bias, void *out_bf16, float *out_f32, int N, int D, int H,
                int W, int Cin, int Cout, int relu, cudaStream_t st, char *err, size_t errlen, int variant);
 int take_status(cudaStream_t st, unsigned *out);
+bool wgrad_supported(int Cin, int Cout);
+int conv3d_wgrad(const void *in, const void *gout, float *gw, float *gb, int N, int D, int H, int W, int Cin,
+                 int Cout, cudaStream_t st, char *err, size_t errlen);
 }  // namespace nn_tc
 
 namespace {
@@ -668,6 +671,11 @@ int nn_conv3d_wgrad(const void *in, const void *gout, float *gw, float *gb, int 
         return inval("nn_conv3d_wgrad: bad argument");
     if (Cin % 8 != 0 || Cout % 8 != 0) return inval("nn_conv3d_wgrad: channels must be multiples of 8");
     if (ksize != 1 && ksize != 3) return inval("nn_conv3d_wgrad: ksize must be 1 or 3");
+    const bool aligned = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(gout) |
+                           reinterpret_cast<uintptr_t>(gw)) & 15u) == 0;
+    if (ksize == 3 && g_conv_path != NN_CONV_MMA_SYNC && aligned && nn_tc::wgrad_supported(Cin, Cout))
+        return nn_tc::conv3d_wgrad(in, gout, gw, gb, N, D, H, W, Cin, Cout, (cudaStream_t)stream, g_err,
+                                   sizeof g_err);
     const int taps = ksize == 3 ? 27 : 1;
     const long long M = (long long)N * D * H * W;
     const long long tiles = (long long)taps * ((Cin + 31) / 32) * ((Cout + 31) / 32);

@@ -185,6 +185,38 @@ def test_conv_input_and_weight_gradients(conv_path, path, ksize, shape, Cin, Cou
     assert np.allclose(host(gb), gb_ref, rtol=1e-5, atol=1e-4)
 
 
+@pytest.mark.parametrize("shape,Cin,Cout", [
+    ((1, 5, 6, 7), 16, 16),        # 210 voxels: a ragged last 64-voxel stage
+    ((2, 4, 9, 8), 32, 48),        # two volumes, 48-column tile
+    ((1, 8, 8, 8), 96, 64),        # 2592 (tap, channel) rows: a partial last 128-row block
+    ((1, 4, 5, 6), 384, 128),
+    ((1, 3, 4, 5), 64, 384),       # two 192-column tiles
+    ((1, 16, 16, 16), 32, 256),    # many voxel ranges meeting in the atomics
+])
+def test_weight_gradient_tcgen05(conv_path, shape, Cin, Cout):
+    """The tcgen05 weight gradient accumulates into gw and gb (+=) and agrees
+    with the FP64 reference and with the mma.sync kernel."""
+    rng = np.random.default_rng(11 + Cin + Cout)
+    x = nn_ref.bf16_round(rng.normal(size=shape + (Cin,)))
+    g = nn_ref.bf16_round(rng.normal(size=shape + (Cout,)))
+    W = np.zeros((27, Cin, Cout))
+    _, gW_ref, gb_ref = nn_ref.conv3d_backward(x, W, g, 3)
+    mag_w = nn_ref.conv3d_backward(np.abs(x), W, np.abs(g), 3)[1]
+    out = {}
+    for path in (nn.NN_CONV_TCGEN05, nn.NN_CONV_MMA_SYNC):
+        conv_path(path)
+        gw = torch.full((27 * Cin * Cout,), 0.5, dtype=torch.float32, device="cuda")
+        gb = torch.full((Cout,), -0.25, dtype=torch.float32, device="cuda")
+        nn.nn_conv3d_wgrad(bf(x), bf(g), gw, gb, *shape, Cin, Cout, 3)
+        torch.cuda.synchronize()
+        out[path] = (host(gw).reshape(gW_ref.shape) - 0.5, host(gb) + 0.25)
+        nn.nn_status()                  # raises if a tensor-core wait gave up
+    gw_tc, gb_tc = out[nn.NN_CONV_TCGEN05]
+    assert np.all(np.abs(gw_tc - gW_ref) <= 1e-5 * mag_w + 1e-5)
+    assert np.allclose(gb_tc, gb_ref, rtol=1e-5, atol=1e-4)
+    assert np.all(np.abs(gw_tc - out[nn.NN_CONV_MMA_SYNC][0]) <= 2e-5 * mag_w + 2e-5)
+
+
 def test_pool_upsample_concat_relu_and_loss():
     rng = np.random.default_rng(3)
     x = nn_ref.bf16_round(rng.normal(size=(1, 4, 6, 8, 16)))
