@@ -236,6 +236,7 @@ def denoise_leg(args):
             "plain": res["plain"], "denoised": res["denoised"], "noisy_input": res["noisy_input"],
             "plain_ppc_to_match": {"ghi": res["plain_ppc_to_match_ghi"], "hr": res["plain_ppc_to_match_hr"]},
             "speedup": {"ghi": res["speedup_ghi"], "hr": res["speedup_hr"]},
+            "hybrid_surface": res.get("hybrid"),
             "network": {"params": net.n_params(), "forward_gflop": net.flops(shape) / 1e9}}
 
 

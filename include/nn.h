@@ -123,6 +123,18 @@ int nn_weights_bf16(const float *W, void *wt, void *wd, int ksize, int Cin, int 
 int nn_direct_transmittance(const float *k_gas, const float *k_cld, int D, int H, int W, double dx, double dy,
                             double dz, double sza_deg, double azimuth_deg, float *t3d, float *t2d, void *stream);
 
+/* Pixel-mean direct-beam transmittance at the surface, t2d FP32 [H][W]: the
+ * mean of exp(-integral of (k_gas + k_cld) ds) toward the sun over nsub x nsub
+ * surface points on a midpoint grid of each column (Sec. 2.3: direct radiation
+ * is the never-scattered part, so toa_flux cos(sza) t2d is the expectation of
+ * the traced surface direct irradiance). The march through the fine cells
+ * (periodic in x and y) runs in FP32; one warp per column sums its points in a
+ * fixed order, so the result is deterministic. Optical depths above 30 give 0.
+ * nsub 1..32; NN_E_INVAL otherwise or for a solar zenith angle outside
+ * [0, 90). k_gas, k_cld [D][H][W] and t2d are device buffers. */
+int nn_direct_surface(const float *k_gas, const float *k_cld, int D, int H, int W, double dx, double dy, double dz,
+                      double sza_deg, double azimuth_deg, int nsub, float *t2d, void *stream);
+
 /* Denoiser inputs from a traced field (FP64 [D][H][W] absorption [W m^-3],
  * [H][W] surface direct/diffuse [W m^-2]) and the optics (FP32 [D][H][W]):
  * BF16 [D][H][W][16] with channels 0: 100 A dz / F, 1: direct / F, 2: diffuse

@@ -520,6 +520,56 @@ __global__ void direct_transmittance_kernel(const float *kg, const float *kc, in
     }
 }
 
+// One warp per surface column: lane l marches the sub-points l, l + 32, ...
+// of the column's nsub x nsub midpoint grid toward the sun; the warp sums in
+// a fixed butterfly order.
+__global__ void direct_surface_kernel(const float *kg, const float *kc, int D, int H, int W, float dx, float dy,
+                                      float dz, float vx, float vy, float vz, int nsub, float *t2)
+{
+    const int lane = threadIdx.x & 31;
+    const long long ncol = (long long)H * W;
+    const int max_steps = 4 * (D + H + W) + 64;
+    const float ax = fabsf(vx), ay = fabsf(vy);
+    const float stx = ax > 0.f ? dx / ax : INFINITY, sty = ay > 0.f ? dy / ay : INFINITY, stz = dz / vz;
+    const int sx = vx > 0.f ? 1 : -1, sy = vy > 0.f ? 1 : -1;
+    const int npts = nsub * nsub;
+    for (long long col = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; col < ncol;
+         col += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int ci = (int)(col % W), cj = (int)(col / W);
+        float acc = 0.f;
+        for (int q = lane; q < npts; q += 32) {
+            const float fx = ((q % nsub) + 0.5f) / nsub, fy = ((q / nsub) + 0.5f) / nsub;
+            int i = ci, j = cj, k = 0;
+            float tx = ax > 0.f ? (vx > 0.f ? 1.f - fx : fx) * stx : INFINITY;
+            float ty = ay > 0.f ? (vy > 0.f ? 1.f - fy : fy) * sty : INFINITY;
+            float tz = stz, t = 0.f, tau = 0.f;
+            for (int s = 0; s < max_steps; ++s) {
+                const long long cell = ((long long)k * H + j) * W + i;
+                const float tm = fminf(tx, fminf(ty, tz));
+                tau = fmaf(kg[cell] + kc[cell], tm - t, tau);
+                t = tm;
+                if (tau > 30.f) break;
+                if (tm == tz) {
+                    if (++k >= D) break;
+                    tz += stz;
+                } else if (tm == tx) {
+                    i += sx;
+                    i = i < 0 ? W - 1 : i >= W ? 0 : i;
+                    tx += stx;
+                } else {
+                    j += sy;
+                    j = j < 0 ? H - 1 : j >= H ? 0 : j;
+                    ty += sty;
+                }
+            }
+            acc += tau > 30.f ? 0.f : expf(-tau);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) t2[col] = acc / (float)npts;
+    }
+}
+
 __global__ void pack_inputs_kernel(const double *abs3d, const double *sdir, const double *sdif, const float *kg,
                                    const float *wg, const float *kc, const float *wc, const float *gc,
                                    const float *t3, const float *t2, __nv_bfloat16 *out, int D, int H, int W,
@@ -772,6 +822,21 @@ int nn_direct_transmittance(const float *k_gas, const float *k_cld, int D, int H
         k_gas, k_cld, D, H, W, (float)dx, (float)dy, (float)dz, (float)(std::sin(t) * std::sin(p)),
         (float)(std::sin(t) * std::cos(p)), (float)std::cos(t), t3d, t2d);
     return check_launch("nn_direct_transmittance");
+}
+
+int nn_direct_surface(const float *k_gas, const float *k_cld, int D, int H, int W, double dx, double dy, double dz,
+                      double sza_deg, double azimuth_deg, int nsub, float *t2d, void *stream)
+{
+    if (!k_gas || !k_cld || !t2d || D <= 0 || H <= 0 || W <= 0 || !(dx > 0) || !(dy > 0) || !(dz > 0) ||
+        !(sza_deg >= 0.0 && sza_deg < 90.0) || !std::isfinite(azimuth_deg) || nsub < 1 || nsub > 32)
+        return inval("nn_direct_surface: bad argument");
+    const double t = sza_deg * 3.14159265358979323846 / 180.0, p = azimuth_deg * 3.14159265358979323846 / 180.0;
+    const long long ncol = (long long)H * W;
+    const long long blocks = std::min<long long>((ncol * 32 + 255) / 256, 148LL * 64);
+    direct_surface_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+        k_gas, k_cld, D, H, W, (float)dx, (float)dy, (float)dz, (float)(std::sin(t) * std::sin(p)),
+        (float)(std::sin(t) * std::cos(p)), (float)std::cos(t), nsub, t2d);
+    return check_launch("nn_direct_surface");
 }
 
 int nn_pack_inputs(const double *abs3d, const double *sfc_dir, const double *sfc_dif, const float *k_gas,

@@ -309,13 +309,12 @@ class FieldTracer:
         self.ncell, self.ncol = nx * ny * nz, nx * ny
         self.optics = [torch.empty(self.ncell, dtype=torch.float32, device=dev) for _ in range(5)]
         self.alb = torch.empty(self.ncol, dtype=torch.float32, device=dev)
-        # optional input channels 6 and 7: deterministic direct-beam transmittance.
-        # Measured on the 512-scene configuration they lowered the GHI error a
-        # little (47.8 vs 54.9 W m^-2) but raised the heating-rate error (0.38 vs
-        # 0.22 K/day), so they are off by default.
+        # optional input channels 6 and 7: deterministic direct-beam transmittance
+        # of each voxel (column centre) and the pixel-mean one at the surface.
         self.direct_features = direct_features
         self.t3d = torch.empty(self.ncell, dtype=torch.float32, device=dev)
         self.t2d = torch.empty(self.ncol, dtype=torch.float32, device=dev)
+        self.t2s = torch.empty(self.ncol, dtype=torch.float32, device=dev)
         self.dx, self.dy = dx, dy
 
     def load(self, scene):
@@ -353,6 +352,8 @@ class FieldTracer:
             # deterministic direct-beam transmittance of the optics (input channels 6, 7)
             nn.nn_direct_transmittance(self.optics[0], self.optics[2], nz, ny, nx, self.dx, self.dy, self.dz, sza,
                                        0.0, self.t3d, self.t2d)
+            nn.nn_direct_surface(self.optics[0], self.optics[2], nz, ny, nx, self.dx, self.dy, self.dz, sza, 0.0, 8,
+                                 self.t2d)
         nn.nn_pack_inputs(lo[0], lo[1], lo[2], *self.optics, x, nz, ny, nx, self.dz, F,
                           t3d=self.t3d if self.direct_features else None,
                           t2d=self.t2d if self.direct_features else None)
@@ -362,6 +363,17 @@ class FieldTracer:
             nn.nn_pack_targets(hi[0], hi[1], hi[2], lo[0], lo[1], lo[2], tgt, nz, ny, nx, self.dz, F)
         return Sample(x, tgt, self.shape, F, self.dz)
 
+    def direct_surface(self, sza, nsub=8):
+        """Expected surface direct irradiance [W m^-2], device FP64 [ny*nx]:
+        toa_flux cos(sza) times the pixel-mean Beer-Lambert transmittance over
+        nsub x nsub surface points per column (one quadrature point only)."""
+        if self.spectral:
+            raise ValueError("direct_surface covers the single quadrature point")
+        nz, ny, nx = self.shape
+        nn.nn_direct_surface(self.optics[0], self.optics[2], nz, ny, nx, self.dx, self.dy, self.dz, sza, 0.0, nsub,
+                             self.t2s)
+        return self.t2s.double() * (1000.0 * math.cos(math.radians(sza)))
+
     def close(self):
         self.t.close()
 
@@ -369,11 +381,11 @@ class FieldTracer:
 SZAS = (0.0, 30.0, 60.0)
 
 
-def make_pairs(seeds, shape, lo_ppc=4, hi_ppc=1024, workers=8, spectral=False):
+def make_pairs(seeds, shape, lo_ppc=4, hi_ppc=1024, workers=8, spectral=False, direct_features=False):
     """Training pairs (low-photon input, correction target) traced on the GPU."""
     nz, ny, nx = shape
     scs = make_scenes(seeds, nx, ny, nz, workers)
-    ft = FieldTracer(shape, spectral=spectral)
+    ft = FieldTracer(shape, spectral=spectral, direct_features=direct_features)
     out = []
     for seed, sc in zip(seeds, scs):
         sza = SZAS[seed % 3]
@@ -473,6 +485,11 @@ def heating_factor(nz, dz):
     return 86400.0 / (1.225 * np.exp(-zc / 8000.0) * 1004.0)
 
 
+def torch_rms(a, b):
+    """RMS difference of two device tensors."""
+    return ((a - b) ** 2).mean().sqrt().item()
+
+
 def _errors(fields, truth, hf, shape):
     nz, ny, nx = shape
     a = fields[0].cpu().numpy().reshape(nz, ny, nx)
@@ -484,7 +501,7 @@ def _errors(fields, truth, hf, shape):
 
 
 def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), truth_ppc=16384, workers=8,
-             repeats=3, spectral=False):
+             repeats=3, spectral=False, direct_nsub=8, direct_features=False):
     """Time-to-RMSE of denoised low-photon runs against the plain tracer.
 
     For each held-out scene: a truth run at `truth_ppc`, plain runs at each
@@ -494,16 +511,31 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), trut
     (RMSE is proportional to N^-1/2, Sec. 3.2); the speed-up is the time the
     fitted plain tracer needs to reach the denoised RMSE divided by the
     denoised wall time.
+
+    For one quadrature point it also reports a hybrid surface estimate: the
+    expected direct irradiance from the pixel-mean Beer-Lambert transmittance
+    (`direct_nsub`^2 points per column, nn_direct_surface) plus the denoised
+    diffuse irradiance, timed as the denoised run plus the direct solve. Two
+    speed-ups are given for it: against the plain tracer, and against a plain
+    tracer whose direct part is replaced by the same exact direct beam (which
+    isolates what the network adds to the diffuse field). Direct and diffuse
+    RMS errors are reported separately.
     """
     torch = _torch()
     nz, ny, nx = shape
     scs = make_scenes(seeds, nx, ny, nz, workers)
-    ft = FieldTracer(shape, spectral=spectral)
+    ft = FieldTracer(shape, spectral=spectral, direct_features=direct_features)
     hf = heating_factor(nz, ft.dz)
     stream = torch.cuda.current_stream()
     acc = {p: [0.0, 0.0, 0.0] for p in plain_ppc}
     den = [0.0, 0.0, 0.0]
     noisy = [0.0, 0.0]
+    hybrid = not spectral
+    hyb = [0.0, 0.0]                         # hybrid GHI error^2, direct-solve ms
+    comp = {}                                # direct and diffuse RMS errors^2, summed over scenes
+
+    def add(key, a, b):
+        comp[key] = comp.get(key, 0.0) + torch_rms(a, b) ** 2
 
     def timed(fn):
         best = None
@@ -522,10 +554,17 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), trut
         sza = SZAS[seed % 3]
         ft.load(sc)
         truth = tuple(t.clone() for t in ft.trace(sza, truth_ppc, 7 * seed + 1))
+        if hybrid:
+            sdx, dms = timed(lambda: ft.direct_surface(sza, direct_nsub))
+            hyb[1] += dms
+            add("exact_dir", sdx, truth[1])
         for p in plain_ppc:
             f, ms = timed(lambda: ft.trace(sza, p, 7 * seed + 2 + p))
             e1, e2 = _errors(f, truth, hf, shape)
             acc[p][0] += e1 ** 2; acc[p][1] += e2 ** 2; acc[p][2] += ms
+            if hybrid:
+                add("plain%d_dir" % p, f[1], truth[1])
+                add("plain%d_dif" % p, f[2], truth[2])
 
         def run():
             lo = ft.trace(sza, lo_ppc, 7 * seed + 3)
@@ -535,6 +574,12 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), trut
         den[0] += e1 ** 2; den[1] += e2 ** 2; den[2] += ms
         n1, n2 = _errors(lo, truth, hf, shape)
         noisy[0] += n1 ** 2; noisy[1] += n2 ** 2
+        if hybrid:
+            hyb[0] += torch_rms(sdx + fd[2], truth[1] + truth[2]) ** 2
+            add("den_dir", fd[1], truth[1])
+            add("den_dif", fd[2], truth[2])
+            add("noisy_dir", lo[1], truth[1])
+            add("noisy_dif", lo[2], truth[2])
     ft.close()
     n = len(seeds)
     plain = {p: {"rmse_ghi": math.sqrt(v[0] / n), "rmse_hr": math.sqrt(v[1] / n), "ms": v[2] / n}
@@ -556,6 +601,21 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), trut
         res["plain_ppc_to_match_" + name] = ppc_match
         res["plain_ms_to_match_" + name] = t_match
         res["speedup_" + name] = t_match / res["denoised"]["ms"]
+    if hybrid:
+        h_ms = res["denoised"]["ms"] + hyb[1] / n
+        h_err = math.sqrt(hyb[0] / n)
+        res["hybrid"] = {"direct_nsub": direct_nsub, "rmse_ghi": h_err, "ms": h_ms, "direct_ms": hyb[1] / n,
+                         "rmse_components": {k: math.sqrt(v / n) for k, v in comp.items()}}
+        a = float(np.exp(np.mean([math.log(plain[p]["rmse_ghi"] * math.sqrt(p)) for p in plain_ppc])))
+        res["hybrid"]["speedup_ghi"] = (t0 + t1 * (a / h_err) ** 2) / h_ms
+        # The plain tracer given the same exact direct beam: both GHI errors then
+        # share the direct term, so they differ only in the diffuse part; the
+        # plain diffuse RMSE is fitted as a / sqrt(ppc) and its time includes
+        # the direct solve.
+        ad = float(np.exp(np.mean([math.log(math.sqrt(comp["plain%d_dif" % p] / n) * math.sqrt(p))
+                                   for p in plain_ppc])))
+        d_err = math.sqrt(comp["den_dif"] / n)
+        res["hybrid"]["speedup_ghi_vs_plain_exact_direct"] = (t0 + t1 * (ad / d_err) ** 2 + hyb[1] / n) / h_ms
     return res
 
 
@@ -575,21 +635,30 @@ def main(argv=None):
     p.add_argument("--spectral", action="store_true",
                    help="broadband fields: all quadrature points of the g-point table in one batched launch")
     p.add_argument("--workers", type=int, default=16)
+    p.add_argument("--direct-features", action="store_true",
+                   help="input channels 6, 7: deterministic direct-beam transmittance (voxel, pixel-mean surface)")
+    p.add_argument("--no-direct-loss", action="store_true",
+                   help="train without the surface-direct term (the hybrid estimate takes the exact direct beam)")
     p.add_argument("--out", default=None, help="write the result JSON here")
     a = p.parse_args(argv)
     shape = tuple(a.shape)
     t0 = time.time()
     pairs = make_pairs(list(range(1000, 1000 + a.train)), shape, hi_ppc=a.hi_ppc, workers=a.workers,
-                       spectral=a.spectral)
+                       spectral=a.spectral, direct_features=a.direct_features)
     t_pairs = time.time() - t0
     net = UNet(seed=0)
+    chw = channel_weights(pairs)
+    if a.no_direct_loss:
+        chw[1] = 0.0
     t0 = time.time()
-    losses = train(net, pairs, epochs=a.epochs, lr=a.lr, log=lambda s: print(s, flush=True))
+    losses = train(net, pairs, epochs=a.epochs, lr=a.lr, chw=chw, log=lambda s: print(s, flush=True))
     t_train = time.time() - t0
     del pairs
     res = evaluate(net, list(range(1000 + a.train, 1000 + a.train + a.eval)), shape, truth_ppc=a.truth_ppc,
-                   workers=a.workers, plain_ppc=tuple(a.plain_ppc), spectral=a.spectral)
-    res.update({"train_scenes": a.train, "epochs": a.epochs, "hi_ppc": a.hi_ppc, "guards": net.train_log, "pairs_s": t_pairs, "train_s": t_train,
+                   workers=a.workers, plain_ppc=tuple(a.plain_ppc), spectral=a.spectral,
+                   direct_features=a.direct_features)
+    res.update({"train_scenes": a.train, "epochs": a.epochs, "hi_ppc": a.hi_ppc,
+                "direct_features": a.direct_features, "direct_loss": not a.no_direct_loss, "guards": net.train_log, "pairs_s": t_pairs, "train_s": t_train,
                 "loss_first": losses[0][1], "loss_last": losses[-1][1], "params": net.n_params(),
                 "forward_gflop": net.flops(shape) / 1e9})
     print(json.dumps(res), flush=True)

@@ -38,6 +38,7 @@ def _lib():
             "nn_weights_bf16": ([P, P, P, i32, i32, i32, P], i32),
             "nn_pack_inputs": ([P] * 11 + [i32] * 3 + [f64, f64, P], i32),
             "nn_direct_transmittance": ([P, P] + [i32] * 3 + [f64] * 5 + [P, P, P], i32),
+            "nn_direct_surface": ([P, P] + [i32] * 3 + [f64] * 5 + [i32, P, P], i32),
             "nn_pack_targets": ([P] * 7 + [i32] * 3 + [f64, f64, P], i32),
             "nn_unpack": ([P, P, i32, P, P, P] + [i32] * 3 + [f64, f64, P], i32),
         }
@@ -139,6 +140,11 @@ def nn_pack_inputs(abs3d, sfc_dir, sfc_dif, k_gas, ssa_gas, k_cld, ssa_cld, g_cl
 def nn_direct_transmittance(k_gas, k_cld, D, H, W, dx, dy, dz, sza_deg, azimuth_deg, t3d, t2d, stream=None):
     _check(_lib().nn_direct_transmittance(_p(k_gas), _p(k_cld), D, H, W, float(dx), float(dy), float(dz),
                                           float(sza_deg), float(azimuth_deg), _p(t3d), _p(t2d), _s(stream)))
+
+
+def nn_direct_surface(k_gas, k_cld, D, H, W, dx, dy, dz, sza_deg, azimuth_deg, nsub, t2d, stream=None):
+    _check(_lib().nn_direct_surface(_p(k_gas), _p(k_cld), D, H, W, float(dx), float(dy), float(dz), float(sza_deg),
+                                    float(azimuth_deg), int(nsub), _p(t2d), _s(stream)))
 
 
 def nn_pack_targets(abs_hi, sdir_hi, sdif_hi, abs_lo, sdir_lo, sdif_lo, out, D, H, W, dz, flux, stream=None):

@@ -55,3 +55,6 @@ def test_trained_denoiser_beats_the_noisy_input_on_held_out_scenes():
     # what the network gains over the plain 4-photon field (the method without it)
     assert d["rmse_ghi"] < 0.9 * n["rmse_ghi"], res
     assert d["rmse_hr"] < 0.6 * n["rmse_hr"], res
+    # the exact pixel-mean direct beam is far closer to the truth than the 4-photon tally
+    c = res["hybrid"]["rmse_components"]
+    assert c["exact_dir"] < 0.3 * c["noisy_dir"], res["hybrid"]

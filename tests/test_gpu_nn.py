@@ -311,6 +311,42 @@ def test_direct_transmittance_closed_form_and_oracle():
         assert np.allclose(host(t2).reshape(sc.ny, sc.nx), want, rtol=1e-4, atol=1e-6), np.abs(host(t2) - want.ravel()).max()
 
 
+def test_direct_surface_pixel_mean_matches_the_oracle():
+    """Pixel-mean direct-beam transmittance at the surface (Sec. 2.3): exact in
+    a layered slab, equal to the oracle's FP64 march over the same nsub x nsub
+    surface points through a 3D cloud field, and at nsub = 1 the same as the
+    column-centre value of nn_direct_transmittance."""
+    import oracle
+    from paper_2208_05247_b300 import scenes
+    D, H, W, dz = 5, 4, 6, 50.0
+    k = np.array([2e-3, 0.0, 1e-2, 5e-4, 3e-3], dtype=np.float32)
+    kg = np.broadcast_to(k[:, None, None], (D, H, W)).astype(np.float32)
+    kc = np.zeros_like(kg)
+    t2 = torch.empty(H * W, dtype=torch.float32, device="cuda")
+    nn.nn_direct_surface(f32(kg), f32(kc), D, H, W, 25.0, 30.0, dz, 35.0, 70.0, 3, t2)
+    want = np.exp(-k.astype(np.float64).sum() * dz / np.cos(np.deg2rad(35.0)))
+    assert np.allclose(host(t2), want, rtol=2e-6, atol=0)
+    sc = scenes.ellipsoid_scene(seed=0)
+    for sza, az, nsub in ((30.0, 0.0, 4), (55.0, 228.1, 5), (10.0, 90.0, 8)):
+        t2 = torch.empty(sc.ncol, dtype=torch.float32, device="cuda")
+        nn.nn_direct_surface(f32(sc.k_gas), f32(sc.k_cld), sc.nz, sc.ny, sc.nx, sc.dx, sc.dy, sc.dz, sza, az, nsub,
+                             t2)
+        want = oracle.direct_beam(sc, sza, az, nsub=nsub)
+        got = host(t2).reshape(sc.ny, sc.nx)
+        assert np.allclose(got, want, rtol=1e-4, atol=1e-6), np.abs(got - want).max()
+    t1 = torch.empty(sc.ncol, dtype=torch.float32, device="cuda")
+    t3 = torch.empty(sc.ncell, dtype=torch.float32, device="cuda")
+    tc = torch.empty(sc.ncol, dtype=torch.float32, device="cuda")
+    nn.nn_direct_surface(f32(sc.k_gas), f32(sc.k_cld), sc.nz, sc.ny, sc.nx, sc.dx, sc.dy, sc.dz, 40.0, 10.0, 1, t1)
+    nn.nn_direct_transmittance(f32(sc.k_gas), f32(sc.k_cld), sc.nz, sc.ny, sc.nx, sc.dx, sc.dy, sc.dz, 40.0, 10.0,
+                               t3, tc)
+    assert torch.equal(t1, tc)
+    for bad in (0, 33):
+        with pytest.raises(nn.NnError):
+            nn.nn_direct_surface(f32(sc.k_gas), f32(sc.k_cld), sc.nz, sc.ny, sc.nx, sc.dx, sc.dy, sc.dz, 40.0, 10.0,
+                                 bad, t1)
+
+
 def test_pack_and_unpack_round_trip():
     """Inputs are the noisy fields scaled by the incoming flux; the denoised
     fields add the predicted corrections back, the surface ones averaged over
