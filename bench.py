@@ -65,7 +65,7 @@ def parse():
     p.add_argument("--no-coupled", action="store_true", help="skip the graph-replay coupled-step leg")
     p.add_argument("--no-birth", action="store_true", help="skip the Sobol-vs-Philox start position leg")
     p.add_argument("--denoise-train", type=int, default=512, help="training scenes of the denoiser leg")
-    p.add_argument("--denoise-epochs", type=int, default=16, help="training epochs of the denoiser leg")
+    p.add_argument("--denoise-epochs", type=int, default=32, help="training epochs of the denoiser leg")
     p.add_argument("--no-autotune", action="store_true",
                    help="use the default launch parameters and the --coarse grid")
     p.add_argument("--coarse", type=int, nargs=3, default=None,
@@ -223,7 +223,9 @@ def denoise_leg(args):
     t_pairs = time.time() - t0
     net = denoise.UNet(seed=0)
     t0 = time.time()
-    losses = denoise.train(net, pairs, epochs=args.denoise_epochs, lr=1e-3)
+    # no surface-direct term in the loss: the product takes the exact direct beam
+    losses = denoise.train(net, pairs, epochs=args.denoise_epochs, lr=1e-3,
+                           chw=denoise.channel_weights(pairs, direct=False))
     t_train = time.time() - t0
     del pairs
     res = denoise.evaluate(net, list(range(1512, 1528)), shape, truth_ppc=16384, workers=os.cpu_count() or 8)
@@ -236,7 +238,7 @@ def denoise_leg(args):
             "plain": res["plain"], "denoised": res["denoised"], "noisy_input": res["noisy_input"],
             "plain_ppc_to_match": {"ghi": res["plain_ppc_to_match_ghi"], "hr": res["plain_ppc_to_match_hr"]},
             "speedup": {"ghi": res["speedup_ghi"], "hr": res["speedup_hr"]},
-            "hybrid_surface": res.get("hybrid"),
+            "surface": res.get("surface"),
             "network": {"params": net.n_params(), "forward_gflop": net.flops(shape) / 1e9}}
 
 

@@ -363,16 +363,19 @@ class FieldTracer:
             nn.nn_pack_targets(hi[0], hi[1], hi[2], lo[0], lo[1], lo[2], tgt, nz, ny, nx, self.dz, F)
         return Sample(x, tgt, self.shape, F, self.dz)
 
-    def direct_surface(self, sza, nsub=8):
+    def direct_surface(self, sza, nsub=8, stream=None):
         """Expected surface direct irradiance [W m^-2], device FP64 [ny*nx]:
         toa_flux cos(sza) times the pixel-mean Beer-Lambert transmittance over
-        nsub x nsub surface points per column (one quadrature point only)."""
+        nsub x nsub surface points per column (one quadrature point only).
+        Runs on `stream` (a torch stream) if given, else on the current one."""
+        torch = _torch()
         if self.spectral:
             raise ValueError("direct_surface covers the single quadrature point")
         nz, ny, nx = self.shape
-        nn.nn_direct_surface(self.optics[0], self.optics[2], nz, ny, nx, self.dx, self.dy, self.dz, sza, 0.0, nsub,
-                             self.t2s)
-        return self.t2s.double() * (1000.0 * math.cos(math.radians(sza)))
+        with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream()):
+            nn.nn_direct_surface(self.optics[0], self.optics[2], nz, ny, nx, self.dx, self.dy, self.dz, sza, 0.0,
+                                 nsub, self.t2s, torch.cuda.current_stream())
+            return self.t2s.double() * (1000.0 * math.cos(math.radians(sza)))
 
     def close(self):
         self.t.close()
@@ -397,15 +400,21 @@ def make_pairs(seeds, shape, lo_ppc=4, hi_ppc=1024, workers=8, spectral=False, d
     return out
 
 
-def channel_weights(samples, device="cuda"):
-    """1 / variance of each target channel over the samples (balances the loss)."""
+def channel_weights(samples, device="cuda", direct=True):
+    """1 / variance of each target channel over the samples (balances the loss).
+    direct=False drops the surface-direct channel from the loss: the denoised
+    product then takes the exact direct beam (FieldTracer.direct_surface), and
+    the network's capacity goes to absorption and diffuse irradiance."""
     torch = _torch()
     v = np.zeros(NUSE)
     for s in samples:
         t = s.target.view(-1, NUSE).double()
         v += (t * t).mean(0).cpu().numpy()
     v /= len(samples)
-    return torch.tensor((1.0 / np.maximum(v, 1e-12)).astype(np.float32), device=device)
+    w = 1.0 / np.maximum(v, 1e-12)
+    if not direct:
+        w[1] = 0.0
+    return torch.tensor(w.astype(np.float32), device=device)
 
 
 def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, seed=0, ema=True):
@@ -501,7 +510,7 @@ def _errors(fields, truth, hf, shape):
 
 
 def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), truth_ppc=16384, workers=8,
-             repeats=3, spectral=False, direct_nsub=8, direct_features=False):
+             repeats=3, spectral=False, direct_nsub=8, direct_features=False, exact_direct=True):
     """Time-to-RMSE of denoised low-photon runs against the plain tracer.
 
     For each held-out scene: a truth run at `truth_ppc`, plain runs at each
@@ -512,14 +521,15 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), trut
     fitted plain tracer needs to reach the denoised RMSE divided by the
     denoised wall time.
 
-    For one quadrature point it also reports a hybrid surface estimate: the
-    expected direct irradiance from the pixel-mean Beer-Lambert transmittance
-    (`direct_nsub`^2 points per column, nn_direct_surface) plus the denoised
-    diffuse irradiance, timed as the denoised run plus the direct solve. Two
-    speed-ups are given for it: against the plain tracer, and against a plain
-    tracer whose direct part is replaced by the same exact direct beam (which
-    isolates what the network adds to the diffuse field). Direct and diffuse
-    RMS errors are reported separately.
+    Surface direct irradiance of the denoised product (one quadrature point,
+    `exact_direct`): the expected value from the pixel-mean Beer-Lambert
+    transmittance (`direct_nsub`^2 points per column, nn_direct_surface),
+    included in the timed region; the network supplies absorption and
+    diffuse irradiance. Otherwise all three come from the network. `surface` reports
+    direct and diffuse RMS errors separately, the network's own surface-direct
+    error, and the GHI speed-up against a plain tracer whose direct part is
+    the same exact direct beam (which isolates what the network adds to the
+    diffuse field).
     """
     torch = _torch()
     nz, ny, nx = shape
@@ -530,8 +540,8 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), trut
     acc = {p: [0.0, 0.0, 0.0] for p in plain_ppc}
     den = [0.0, 0.0, 0.0]
     noisy = [0.0, 0.0]
-    hybrid = not spectral
-    hyb = [0.0, 0.0]                         # hybrid GHI error^2, direct-solve ms
+    hybrid = exact_direct and not spectral
+    dms_sum = 0.0
     comp = {}                                # direct and diffuse RMS errors^2, summed over scenes
 
     def add(key, a, b):
@@ -556,7 +566,7 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), trut
         truth = tuple(t.clone() for t in ft.trace(sza, truth_ppc, 7 * seed + 1))
         if hybrid:
             sdx, dms = timed(lambda: ft.direct_surface(sza, direct_nsub))
-            hyb[1] += dms
+            dms_sum += dms
             add("exact_dir", sdx, truth[1])
         for p in plain_ppc:
             f, ms = timed(lambda: ft.trace(sza, p, 7 * seed + 2 + p))
@@ -568,15 +578,18 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), trut
 
         def run():
             lo = ft.trace(sza, lo_ppc, 7 * seed + 3)
-            return denoise(net, ft.pack(lo, sza)), lo
-        (fd, lo), ms = timed(run)
+            fnet = denoise(net, ft.pack(lo, sza))
+            if hybrid:
+                return (fnet[0], ft.direct_surface(sza, direct_nsub), fnet[2]), fnet, lo
+            return fnet, fnet, lo
+        (fd, fnet, lo), ms = timed(run)
         e1, e2 = _errors(fd, truth, hf, shape)
         den[0] += e1 ** 2; den[1] += e2 ** 2; den[2] += ms
         n1, n2 = _errors(lo, truth, hf, shape)
         noisy[0] += n1 ** 2; noisy[1] += n2 ** 2
         if hybrid:
-            hyb[0] += torch_rms(sdx + fd[2], truth[1] + truth[2]) ** 2
-            add("den_dir", fd[1], truth[1])
+            add("network_ghi", fnet[1] + fnet[2], truth[1] + truth[2])
+            add("network_dir", fnet[1], truth[1])
             add("den_dif", fd[2], truth[2])
             add("noisy_dir", lo[1], truth[1])
             add("noisy_dif", lo[2], truth[2])
@@ -601,13 +614,12 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), trut
         res["plain_ppc_to_match_" + name] = ppc_match
         res["plain_ms_to_match_" + name] = t_match
         res["speedup_" + name] = t_match / res["denoised"]["ms"]
+    res["surface"] = {"direct": "network"}
     if hybrid:
-        h_ms = res["denoised"]["ms"] + hyb[1] / n
-        h_err = math.sqrt(hyb[0] / n)
-        res["hybrid"] = {"direct_nsub": direct_nsub, "rmse_ghi": h_err, "ms": h_ms, "direct_ms": hyb[1] / n,
-                         "rmse_components": {k: math.sqrt(v / n) for k, v in comp.items()}}
-        a = float(np.exp(np.mean([math.log(plain[p]["rmse_ghi"] * math.sqrt(p)) for p in plain_ppc])))
-        res["hybrid"]["speedup_ghi"] = (t0 + t1 * (a / h_err) ** 2) / h_ms
+        res["surface"] = {"direct": "exact pixel-mean Beer-Lambert, %d x %d points per column" % (direct_nsub,
+                                                                                                  direct_nsub),
+                          "direct_solve_ms_alone": dms_sum / n,
+                          "rmse": {k: math.sqrt(v / n) for k, v in comp.items()}}
         # The plain tracer given the same exact direct beam: both GHI errors then
         # share the direct term, so they differ only in the diffuse part; the
         # plain diffuse RMSE is fitted as a / sqrt(ppc) and its time includes
@@ -615,7 +627,12 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), trut
         ad = float(np.exp(np.mean([math.log(math.sqrt(comp["plain%d_dif" % p] / n) * math.sqrt(p))
                                    for p in plain_ppc])))
         d_err = math.sqrt(comp["den_dif"] / n)
-        res["hybrid"]["speedup_ghi_vs_plain_exact_direct"] = (t0 + t1 * (ad / d_err) ** 2 + hyb[1] / n) / h_ms
+        res["surface"]["speedup_ghi_vs_plain_exact_direct"] = (
+            (t0 + t1 * (ad / d_err) ** 2 + dms_sum / n) / res["denoised"]["ms"])
+        # the network's own surface-direct estimate, for comparison
+        an = float(np.exp(np.mean([math.log(plain[p]["rmse_ghi"] * math.sqrt(p)) for p in plain_ppc])))
+        e_net = math.sqrt(comp["network_ghi"] / n)
+        res["surface"]["network_only_speedup_ghi"] = (t0 + t1 * (an / e_net) ** 2) / res["denoised"]["ms"]
     return res
 
 
@@ -626,7 +643,7 @@ def main(argv=None):
     p = argparse.ArgumentParser(description="train and evaluate the 3D U-Net denoiser")
     p.add_argument("--train", type=int, default=512, help="training scenes (seeds 1000...)")
     p.add_argument("--eval", type=int, default=64, help="held-out scenes (seeds after the training ones)")
-    p.add_argument("--epochs", type=int, default=16)
+    p.add_argument("--epochs", type=int, default=32)
     p.add_argument("--lr", type=float, default=1e-3)
     p.add_argument("--shape", type=int, nargs=3, default=(128, 128, 128), help="nz ny nx")
     p.add_argument("--truth-ppc", type=int, default=16384)
@@ -637,8 +654,9 @@ def main(argv=None):
     p.add_argument("--workers", type=int, default=16)
     p.add_argument("--direct-features", action="store_true",
                    help="input channels 6, 7: deterministic direct-beam transmittance (voxel, pixel-mean surface)")
-    p.add_argument("--no-direct-loss", action="store_true",
-                   help="train without the surface-direct term (the hybrid estimate takes the exact direct beam)")
+    p.add_argument("--direct-loss", action="store_true",
+                   help="train on the surface-direct channel too and take the network's surface direct "
+                        "(default: the exact direct beam, and no direct term in the loss)")
     p.add_argument("--out", default=None, help="write the result JSON here")
     a = p.parse_args(argv)
     shape = tuple(a.shape)
@@ -647,18 +665,16 @@ def main(argv=None):
                        spectral=a.spectral, direct_features=a.direct_features)
     t_pairs = time.time() - t0
     net = UNet(seed=0)
-    chw = channel_weights(pairs)
-    if a.no_direct_loss:
-        chw[1] = 0.0
+    chw = channel_weights(pairs, direct=a.direct_loss)
     t0 = time.time()
     losses = train(net, pairs, epochs=a.epochs, lr=a.lr, chw=chw, log=lambda s: print(s, flush=True))
     t_train = time.time() - t0
     del pairs
     res = evaluate(net, list(range(1000 + a.train, 1000 + a.train + a.eval)), shape, truth_ppc=a.truth_ppc,
                    workers=a.workers, plain_ppc=tuple(a.plain_ppc), spectral=a.spectral,
-                   direct_features=a.direct_features)
+                   direct_features=a.direct_features, exact_direct=not a.direct_loss)
     res.update({"train_scenes": a.train, "epochs": a.epochs, "hi_ppc": a.hi_ppc,
-                "direct_features": a.direct_features, "direct_loss": not a.no_direct_loss, "guards": net.train_log, "pairs_s": t_pairs, "train_s": t_train,
+                "direct_features": a.direct_features, "direct_loss": a.direct_loss, "guards": net.train_log, "pairs_s": t_pairs, "train_s": t_train,
                 "loss_first": losses[0][1], "loss_last": losses[-1][1], "params": net.n_params(),
                 "forward_gflop": net.flops(shape) / 1e9})
     print(json.dumps(res), flush=True)
