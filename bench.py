@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--no-coupled", action="store_true", help="skip the graph-replay coupled-step leg")
     p.add_argument("--no-birth", action="store_true", help="skip the Sobol-vs-Philox start position leg")
     p.add_argument("--denoise-train", type=int, default=512, help="training scenes of the denoiser leg")
+    p.add_argument("--no-l2-probe", action="store_true", help="skip the L2 read-bandwidth probe")
     p.add_argument("--denoise-epochs", type=int, default=32, help="training epochs of the denoiser leg")
     p.add_argument("--no-autotune", action="store_true",
                    help="use the default launch parameters and the --coarse grid")
@@ -424,6 +425,17 @@ def run_ours(args):
             "traffic": profiled_traffic(), "peak_source": peak_src,
             "kernel": "trace_kernel<double>", "kernel_ms": 1e3 * tk,
             "algorithmic_bytes_per_launch": alg_bytes}
+    # the same algorithmic bytes against this GPU's L2 read bandwidth, measured
+    # here (outside the timed region) by the library's read probe: the
+    # transport kernel's working set is L2-resident
+    l2roof = None
+    if not args.no_l2_probe:
+        from paper_2208_05247_b300 import mem_probe
+        rows = mem_probe.sweep((48, 1024), target_bytes=4 << 30, repeats=3)
+        l2roof = {"bound": "l2", "achieved": achieved, "peak": rows[0]["gbs"], "unit": "GB/s",
+                  "frac": achieved / rows[0]["gbs"], "dram_read_gbs": rows[1]["gbs"],
+                  "peak_source": "rt_probe_read in this run: L2-cached 16-byte reads of a 48 MB buffer "
+                                 "(1024 MB for the DRAM figure)"}
 
     # end to end through the C ABI with host buffers: every step copies its
     # inputs in from pinned host memory and its fields out to pinned host
@@ -487,7 +499,7 @@ def run_ours(args):
             "events_per_step": events_all, "real_scatter_fraction": st["scatters"] / max(1, events),
             "trace_kernel_ms": 1e3 * tk, "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps, "time_to_rmse": dn, "coupled_step": cstep,
-            "sobol_birth": births}
+            "sobol_birth": births, "l2_roofline": l2roof}
     print(json.dumps(line), flush=True)
     t.close()
     if dist is not None:

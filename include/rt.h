@@ -391,6 +391,15 @@ int rt_debug_sobol(uint64_t k0, int n, uint32_t sx, uint32_t sy, uint32_t *out);
  * vector at angle acos(mu[i]) from d and azimuth phi[i] about it (host arrays). */
 int rt_debug_turn(const float d[3], const float *mu, const float *phi, float *out, int n);
 
+/* Memory-system probe (measurement of the GPU, not part of the method): one
+ * launch reads `bytes` of device buffer buf `reps` times over with 16-byte
+ * loads cached in L2 only (ld.global.cg), on `stream`; the caller times it.
+ * Swept over buffer sizes it gives the L2 read bandwidth below the L2
+ * capacity and the DRAM bandwidth above it. bytes: a positive multiple of 16;
+ * buf 16-byte aligned; sink: one device word, written only so that the
+ * loads are not removed. RT_E_INVAL otherwise. */
+int rt_probe_read(const void *buf, uint64_t bytes, int reps, unsigned *sink, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1224,6 +1224,38 @@ int rt_debug_sobol(uint64_t k0, int n, uint32_t sx, uint32_t sy, uint32_t *out)
     return RT_OK;
 }
 
+namespace {
+// Grid-stride 16-byte reads cached in L2 only; the XOR of everything read
+// decides a store that never happens in practice but keeps the loads live.
+__global__ void probe_read_kernel(const uint4 *__restrict__ p, uint64_t n16, int reps, unsigned *sink)
+{
+    uint32_t acc = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r)
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+            const uint4 v = __ldcg(p + i);
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+    if (acc == 0x9e3779b9u) atomicAdd(sink, 1u);
+}
+}  // namespace
+
+int rt_probe_read(const void *buf, uint64_t bytes, int reps, unsigned *sink, void *stream)
+{
+    if (!buf || !sink || bytes == 0 || bytes % 16 || reps <= 0 || (reinterpret_cast<uintptr_t>(buf) & 15u))
+        return fail(RT_E_INVAL, "rt_probe_read: bad argument");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t n16 = bytes / 16;
+    const uint64_t blocks = std::min<uint64_t>((uint64_t)(sms > 0 ? sms : 148) * 8, (n16 + 255) / 256);
+    probe_read_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<const uint4 *>(buf), n16, reps,
+                                                                         sink);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(RT_E_CUDA, "rt_probe_read: %s", cudaGetErrorString(e));
+    return RT_OK;
+}
+
 int rt_debug_turn(const float d[3], const float *mu, const float *phi, float *out, int n)
 {
     if (!d || !mu || !phi || !out || n <= 0) return fail(RT_E_INVAL, "rt_debug_turn: bad argument");

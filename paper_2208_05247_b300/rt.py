@@ -107,6 +107,7 @@ def library() -> ctypes.CDLL:
             "rt_debug_sample": ([i32, ctypes.c_float, u64, u64, P], i32),
             "rt_debug_turn": ([P, P, P, P, i32], i32),
             "rt_debug_sobol": ([u64, i32, ctypes.c_uint32, ctypes.c_uint32, P], i32),
+            "rt_probe_read": ([P, u64, i32, P, P], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -377,6 +378,12 @@ def rt_debug_sobol(k0: int, n: int, sx: int = 0, sy: int = 0) -> np.ndarray:
     out = np.empty((n, 2), dtype=np.uint32)
     _check(library().rt_debug_sobol(int(k0), int(n), int(sx), int(sy), out.ctypes.data))
     return out
+
+
+def rt_probe_read(buf, nbytes: int, reps: int, sink, stream=None):
+    """Read nbytes of the device buffer buf reps times (L2-cached 16-byte loads)."""
+    sptr = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(library().rt_probe_read(buf.data_ptr(), int(nbytes), int(reps), sink.data_ptr(), sptr))
 
 
 def rt_debug_turn(d, mu, phi) -> np.ndarray:
