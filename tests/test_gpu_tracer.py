@@ -207,6 +207,75 @@ def test_energy_ledger_closes(c0_parity):
         assert s["photons"] == 2 ** 22
 
 
+# --- conservation and symmetry pins ---------------------------------------------------
+
+def test_gpu_conservative_black_surface_and_white_surface():
+    """omega = 1 everywhere: weights never drop in the atmosphere, so nothing
+    is absorbed there. Over a black surface every photon ends at the surface or
+    the top; over a white one every photon leaves through the top (R = 1).
+    Both hold to rounding, not only statistically (Sec. 2.3); the rounding is
+    that of the FP32 product of weight and per-call photon energy that every
+    tally adds (about 1e-8 relative), far below the sampling noise (~1e-3)."""
+    sc = scenes.ellipsoid_scene(seed=0)
+    sc.ssa_gas[:] = 1.0
+    sc.ssa_cld[sc.k_cld > 0] = 1.0
+    F = 1000.0 * np.cos(np.deg2rad(30.0))
+    sc.albedo[:] = 0.0
+    with rt.Tracer.from_scene(sc) as t:
+        t.trace(30.0, 0.0, 1000.0, 1_000_000, 41)
+        f, st = t.fields(split=True), t.stats()
+    assert np.all(f["abs_dir"] == 0) and np.all(f["abs_dif"] == 0)
+    assert st["energy_atm_abs"] == 0 and st["capped"] == 0
+    arrived = f["sfc_dir"].mean() + f["sfc_dif"].mean()
+    assert np.isclose(arrived + f["toa_up"].mean(), F, rtol=1e-6)
+    sc.albedo[:] = 1.0
+    with rt.Tracer.from_scene(sc) as t:
+        t.trace(30.0, 0.0, 1000.0, 1_000_000, 42)
+        f, st = t.fields(split=True), t.stats()
+    assert st["energy_atm_abs"] == 0 and st["energy_sfc_abs"] == 0 and st["capped"] == 0
+    assert np.isclose(f["toa_up"].mean(), F, rtol=1e-6)
+
+
+def test_gpu_horizontally_homogeneous_scene_is_translation_invariant():
+    """A layered scene with scattering: every column sees the same expectation,
+    so column means differ from the domain mean only by sampling noise."""
+    sc = scenes.layered_scene(12, 10, 8, 60.0, 60.0, 80.0, k_gas=2e-4, ssa_gas=0.9,
+                              k_cld=[0, 0, 0.01, 0.02, 0.01, 0, 0, 0], ssa_cld=0.99, g_cld=0.8, albedo=0.3)
+    g, _ = gpu_batches(sc, 40.0, 75.0, 1000.0, 399_960, range(300, 324))     # 3333 photons per column
+    for field in ("sfc_dir", "sfc_dif", "toa_up"):
+        a = g[field]                                   # [B][ny][nx]
+        m = a.mean(0)
+        se = a.std(0, ddof=1) / np.sqrt(a.shape[0])
+        z = (m - m.mean()) / se
+        # chi^2 of the column means about the domain mean: consistent with noise
+        chi2 = float((z ** 2).sum())
+        dof = z.size - 1
+        assert chi2 < dof + 5 * np.sqrt(2 * dof), (field, chi2, dof)
+        assert np.abs(z).max() < 6.5, (field, np.abs(z).max())
+
+
+def test_gpu_overhead_sun_commutes_with_swapping_x_and_y():
+    """With the sun overhead the transport has no preferred horizontal axis:
+    tracing the x-y transposed scene gives the transposed fields (cell-wise
+    parity statistic between two independent GPU runs)."""
+    sc = scenes.ellipsoid_scene(seed=3)
+    sw = copy.deepcopy(sc)
+    for name in ("k_gas", "ssa_gas", "k_cld", "ssa_cld", "g_cld"):
+        setattr(sw, name, np.ascontiguousarray(np.swapaxes(getattr(sc, name), 1, 2)))
+    sw.albedo = np.ascontiguousarray(sc.albedo.T)
+    sw.nx, sw.ny, sw.dx, sw.dy = sc.ny, sc.nx, sc.dy, sc.dx
+    a, _ = gpu_batches(sc, 0.0, 0.0, 1000.0, 2 ** 20, range(700, 716))
+    b, _ = gpu_batches(sw, 0.0, 0.0, 1000.0, 2 ** 20, range(800, 816))
+    # independent pilot batches choose the well-sampled cells
+    ap, _ = gpu_batches(sc, 0.0, 0.0, 1000.0, 2 ** 20, range(900, 908))
+    bp, _ = gpu_batches(sw, 0.0, 0.0, 1000.0, 2 ** 20, range(950, 958))
+    for field in FIELDS:
+        bt = np.swapaxes(b[field], -1, -2)
+        rep = refs.parity_report(bt, a[field], pilot=(np.swapaxes(bp[field], -1, -2), ap[field]))
+        assert rep["frac_over"] <= rep["bound"], (field, rep["frac_over"], rep["bound"])
+        assert abs(rep["domain_rel"]) < 4 * rep["domain_rel_se"] + 1e-9, (field, rep["domain_rel"])
+
+
 # --- reproducibility, launch-geometry and partition invariance -----------------------
 
 def _run(sc, seed, N, **opts):
