@@ -385,6 +385,145 @@ __global__ void up2_bwd_kernel(const __nv_bfloat16 *gout, __nv_bfloat16 *gin, in
     }
 }
 
+// ---- 8-channel (16-byte) variants of the resampling and copy kernels ----
+// Used when every channel count and offset is a multiple of 8 and the buffers
+// are 16-byte aligned. One thread handles 8 channels of one coarse voxel (of
+// one voxel for the copy), so the index arithmetic runs once per 16 bytes
+// instead of once per element; I is the index type (32-bit when the counts
+// fit). Per channel the arithmetic and its order are those of the scalar
+// kernels above, so the results are bit-identical.
+struct bf8 { __nv_bfloat162 h[4]; };
+
+__device__ __forceinline__ void bf8_to_f(const uint4 &q, float (&f)[8])
+{
+    const bf8 b = *reinterpret_cast<const bf8 *>(&q);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float2 t = __bfloat1622float2(b.h[j]);
+        f[2 * j] = t.x;
+        f[2 * j + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ uint4 f_to_bf8(const float (&f)[8])
+{
+    bf8 b;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b.h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+    return *reinterpret_cast<const uint4 *>(&b);
+}
+
+// coarse voxel (b, z, y, x) of i / G over a [N][d][h][w] grid
+template <typename I>
+__device__ __forceinline__ void coarse_index(I v, int d, int h, int w, I &b, int &z, int &y, int &x)
+{
+    x = (int)(v % (I)w); v /= (I)w;
+    y = (int)(v % (I)h); v /= (I)h;
+    z = (int)(v % (I)d);
+    b = v / (I)d;
+}
+
+template <typename I>
+__global__ void pool2_fwd_vec_kernel(const uint4 *in, uint4 *out, int N, int d, int h, int w, int G)
+{
+    const I n = (I)N * d * h * w * G;
+    for (I i = (I)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (I)gridDim.x * blockDim.x) {
+        const int g = (int)(i % (I)G);
+        I b; int z, y, x;
+        coarse_index<I>(i / (I)G, d, h, w, b, z, y, x);
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int e = 0; e < 8; ++e) {
+            const I src = ((b * (2 * d) + 2 * z + (e >> 2)) * (2 * h) + 2 * y + ((e >> 1) & 1)) * (2 * w) + 2 * x + (e & 1);
+            float f[8];
+            bf8_to_f(in[src * G + g], f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s[j] += f[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s[j] *= 0.125f;
+        out[i] = f_to_bf8(s);
+    }
+}
+
+template <typename I>
+__global__ void pool2_bwd_vec_kernel(const uint4 *gout, uint4 *gin, int N, int d, int h, int w, int G)
+{
+    const I n = (I)N * d * h * w * G;
+    for (I i = (I)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (I)gridDim.x * blockDim.x) {
+        const int g = (int)(i % (I)G);
+        I b; int z, y, x;
+        coarse_index<I>(i / (I)G, d, h, w, b, z, y, x);
+        float f[8];
+        bf8_to_f(gout[i], f);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) f[j] *= 0.125f;
+        const uint4 q = f_to_bf8(f);
+        for (int e = 0; e < 8; ++e) {
+            const I dst = ((b * (2 * d) + 2 * z + (e >> 2)) * (2 * h) + 2 * y + ((e >> 1) & 1)) * (2 * w) + 2 * x + (e & 1);
+            gin[dst * G + g] = q;
+        }
+    }
+}
+
+template <typename I>
+__global__ void up2_fwd_vec_kernel(const uint4 *in, uint4 *out, int N, int d, int h, int w, int G, int Gdst, int g0)
+{
+    const I n = (I)N * d * h * w * G;
+    for (I i = (I)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (I)gridDim.x * blockDim.x) {
+        const int g = (int)(i % (I)G);
+        I b; int z, y, x;
+        coarse_index<I>(i / (I)G, d, h, w, b, z, y, x);
+        const uint4 q = in[i];
+        for (int e = 0; e < 8; ++e) {
+            const I dst = ((b * (2 * d) + 2 * z + (e >> 2)) * (2 * h) + 2 * y + ((e >> 1) & 1)) * (2 * w) + 2 * x + (e & 1);
+            out[dst * Gdst + g0 + g] = q;
+        }
+    }
+}
+
+template <typename I>
+__global__ void up2_bwd_vec_kernel(const uint4 *gout, uint4 *gin, int N, int d, int h, int w, int G, int Gsrc, int g0)
+{
+    const I n = (I)N * d * h * w * G;
+    for (I i = (I)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (I)gridDim.x * blockDim.x) {
+        const int g = (int)(i % (I)G);
+        I b; int z, y, x;
+        coarse_index<I>(i / (I)G, d, h, w, b, z, y, x);
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int e = 0; e < 8; ++e) {
+            const I src = ((b * (2 * d) + 2 * z + (e >> 2)) * (2 * h) + 2 * y + ((e >> 1) & 1)) * (2 * w) + 2 * x + (e & 1);
+            float f[8];
+            bf8_to_f(gout[src * Gsrc + g0 + g], f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s[j] += f[j];
+        }
+        gin[i] = f_to_bf8(s);
+    }
+}
+
+template <typename I>
+__global__ void copy_channels_vec_kernel(const uint4 *src, int Gs, int s0, uint4 *dst, int Gd, int d0, I vox, int G,
+                                         int accumulate)
+{
+    const I n = vox * (I)G;
+    for (I i = (I)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (I)gridDim.x * blockDim.x) {
+        const I v = i / (I)G;
+        const int g = (int)(i - v * (I)G);
+        const uint4 x = src[v * Gs + s0 + g];
+        uint4 &y = dst[v * Gd + d0 + g];
+        if (accumulate) {
+            float a[8], c[8];
+            bf8_to_f(y, a);
+            bf8_to_f(x, c);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) a[j] += c[j];
+            y = f_to_bf8(a);
+        } else {
+            y = x;
+        }
+    }
+}
+
 // copy C channels between tensors with channel strides Csrc / Cdst and offsets
 __global__ void copy_channels_kernel(const __nv_bfloat16 *src, int Csrc, int s0, __nv_bfloat16 *dst, int Cdst, int d0,
                                      long long vox, int C, int accumulate)
@@ -638,6 +777,10 @@ __global__ void unpack_kernel(const __nv_bfloat16 *in, const float *pred, int Cp
 
 int grid1d(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 148 * 16)); }
 
+bool al16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+// the 8-channel kernels index with 32 bits when every index they form fits
+bool fits32(long long elems16) { return elems16 < (1LL << 31); }
+
 thread_local char g_err[256] = "";
 
 int check_launch(const char *what)
@@ -751,6 +894,16 @@ int nn_pool2_fwd(const void *in, void *out, int N, int D, int H, int W, int C, v
 {
     if (!in || !out || D % 2 || H % 2 || W % 2) return inval("nn_pool2_fwd: bad argument");
     const long long n = (long long)N * (D / 2) * (H / 2) * (W / 2) * C;
+    if (C % 8 == 0 && al16(in) && al16(out)) {
+        const long long big = (long long)N * D * H * W * (C / 8);
+        if (fits32(big))
+            pool2_fwd_vec_kernel<uint32_t><<<grid1d(n / 8), 256, 0, (cudaStream_t)stream>>>(
+                (const uint4 *)in, (uint4 *)out, N, D / 2, H / 2, W / 2, C / 8);
+        else
+            pool2_fwd_vec_kernel<long long><<<grid1d(n / 8), 256, 0, (cudaStream_t)stream>>>(
+                (const uint4 *)in, (uint4 *)out, N, D / 2, H / 2, W / 2, C / 8);
+        return check_launch("nn_pool2_fwd");
+    }
     pool2_fwd_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)in, (__nv_bfloat16 *)out, N, D,
                                                                   H, W, C);
     return check_launch("nn_pool2_fwd");
@@ -760,6 +913,15 @@ int nn_pool2_bwd(const void *gout, void *gin, int N, int D, int H, int W, int C,
 {
     if (!gout || !gin || D % 2 || H % 2 || W % 2) return inval("nn_pool2_bwd: bad argument");
     const long long n = (long long)N * D * H * W * C;
+    if (C % 8 == 0 && al16(gout) && al16(gin)) {
+        if (fits32(n / 8))
+            pool2_bwd_vec_kernel<uint32_t><<<grid1d(n / 64), 256, 0, (cudaStream_t)stream>>>(
+                (const uint4 *)gout, (uint4 *)gin, N, D / 2, H / 2, W / 2, C / 8);
+        else
+            pool2_bwd_vec_kernel<long long><<<grid1d(n / 64), 256, 0, (cudaStream_t)stream>>>(
+                (const uint4 *)gout, (uint4 *)gin, N, D / 2, H / 2, W / 2, C / 8);
+        return check_launch("nn_pool2_bwd");
+    }
     pool2_bwd_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)gout, (__nv_bfloat16 *)gin, N,
                                                                   D, H, W, C);
     return check_launch("nn_pool2_bwd");
@@ -769,6 +931,16 @@ int nn_up2_fwd(const void *in, void *out, int N, int d, int h, int w, int C, int
 {
     if (!in || !out || c0 < 0 || c0 + C > Cdst) return inval("nn_up2_fwd: bad argument");
     const long long n = (long long)N * 8 * d * h * w * C;
+    if (C % 8 == 0 && Cdst % 8 == 0 && c0 % 8 == 0 && al16(in) && al16(out)) {
+        const long long big = (long long)N * 8 * d * h * w * (Cdst / 8);
+        if (fits32(big))
+            up2_fwd_vec_kernel<uint32_t><<<grid1d(n / 64), 256, 0, (cudaStream_t)stream>>>(
+                (const uint4 *)in, (uint4 *)out, N, d, h, w, C / 8, Cdst / 8, c0 / 8);
+        else
+            up2_fwd_vec_kernel<long long><<<grid1d(n / 64), 256, 0, (cudaStream_t)stream>>>(
+                (const uint4 *)in, (uint4 *)out, N, d, h, w, C / 8, Cdst / 8, c0 / 8);
+        return check_launch("nn_up2_fwd");
+    }
     up2_fwd_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)in, (__nv_bfloat16 *)out, N, d, h,
                                                                 w, C, Cdst, c0);
     return check_launch("nn_up2_fwd");
@@ -778,6 +950,16 @@ int nn_up2_bwd(const void *gout, void *gin, int N, int d, int h, int w, int C, i
 {
     if (!gout || !gin || c0 < 0 || c0 + C > Csrc) return inval("nn_up2_bwd: bad argument");
     const long long n = (long long)N * d * h * w * C;
+    if (C % 8 == 0 && Csrc % 8 == 0 && c0 % 8 == 0 && al16(gout) && al16(gin)) {
+        const long long big = (long long)N * 8 * d * h * w * (Csrc / 8);
+        if (fits32(big))
+            up2_bwd_vec_kernel<uint32_t><<<grid1d(n / 8), 256, 0, (cudaStream_t)stream>>>(
+                (const uint4 *)gout, (uint4 *)gin, N, d, h, w, C / 8, Csrc / 8, c0 / 8);
+        else
+            up2_bwd_vec_kernel<long long><<<grid1d(n / 8), 256, 0, (cudaStream_t)stream>>>(
+                (const uint4 *)gout, (uint4 *)gin, N, d, h, w, C / 8, Csrc / 8, c0 / 8);
+        return check_launch("nn_up2_bwd");
+    }
     up2_bwd_kernel<<<grid1d(n), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)gout, (__nv_bfloat16 *)gin, N, d,
                                                                 h, w, C, Csrc, c0);
     return check_launch("nn_up2_bwd");
@@ -787,6 +969,16 @@ int nn_copy_channels(const void *src, int Csrc, int s0, void *dst, int Cdst, int
                      int accumulate, void *stream)
 {
     if (!src || !dst || s0 < 0 || d0 < 0 || s0 + C > Csrc || d0 + C > Cdst) return inval("nn_copy_channels: bad argument");
+    if (C % 8 == 0 && Csrc % 8 == 0 && Cdst % 8 == 0 && s0 % 8 == 0 && d0 % 8 == 0 && al16(src) && al16(dst)) {
+        const long long big = vox * (std::max(Csrc, Cdst) / 8);
+        if (fits32(big))
+            copy_channels_vec_kernel<uint32_t><<<grid1d(vox * C / 8), 256, 0, (cudaStream_t)stream>>>(
+                (const uint4 *)src, Csrc / 8, s0 / 8, (uint4 *)dst, Cdst / 8, d0 / 8, (uint32_t)vox, C / 8, accumulate);
+        else
+            copy_channels_vec_kernel<long long><<<grid1d(vox * C / 8), 256, 0, (cudaStream_t)stream>>>(
+                (const uint4 *)src, Csrc / 8, s0 / 8, (uint4 *)dst, Cdst / 8, d0 / 8, vox, C / 8, accumulate);
+        return check_launch("nn_copy_channels");
+    }
     copy_channels_kernel<<<grid1d(vox * C), 256, 0, (cudaStream_t)stream>>>(
         (const __nv_bfloat16 *)src, Csrc, s0, (__nv_bfloat16 *)dst, Cdst, d0, vox, C, accumulate);
     return check_launch("nn_copy_channels");

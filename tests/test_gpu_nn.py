@@ -257,6 +257,60 @@ def test_pool_upsample_concat_relu_and_loss():
     assert np.allclose(host(grad).reshape(500, 16), g_ref, rtol=2 ** -8, atol=1e-9)
 
 
+def test_resampling_vector_and_scalar_paths_are_bit_identical():
+    """With channel counts and offsets that are multiples of 8 and 16-byte
+    aligned buffers the resampling and copy kernels move 8 channels per thread;
+    otherwise one element per thread. Both do the same per-channel arithmetic
+    in the same order, so the same data gives the same bits either way (the
+    scalar path is forced here by a buffer offset of one element)."""
+    rng = np.random.default_rng(5)
+    N, D, H, W, C, Cdst, c0 = 1, 4, 6, 8, 24, 40, 16
+
+    def dev(a, shift):
+        # a device BF16 copy of a, starting `shift` elements into a larger buffer
+        t = torch.zeros(a.size + 8, dtype=torch.bfloat16, device="cuda")
+        t[shift:shift + a.size] = bf(a).ravel()
+        return t[shift:shift + a.size], t
+
+    def run(shift):
+        x = nn_ref.bf16_round(rng_x)
+        outs = []
+        xi, _ = dev(x, shift)
+        p, _ = dev(np.zeros(N * 2 * 3 * 4 * C), shift)
+        nn.nn_pool2_fwd(xi, p, N, D, H, W, C)
+        outs.append(p.clone())
+        gp, _ = dev(nn_ref.bf16_round(rng_gp), shift)
+        gx, _ = dev(np.zeros(x.size), shift)
+        nn.nn_pool2_bwd(gp, gx, N, D, H, W, C)
+        outs.append(gx.clone())
+        y, _ = dev(nn_ref.bf16_round(rng_y), shift)
+        cat, _ = dev(nn_ref.bf16_round(rng_cat), shift)
+        nn.nn_up2_fwd(y, cat, N, 2, 3, 4, C, Cdst, c0)
+        outs.append(cat.clone())
+        gy, _ = dev(np.zeros(rng_y.size), shift)
+        nn.nn_up2_bwd(cat, gy, N, 2, 3, 4, C, Cdst, c0)
+        outs.append(gy.clone())
+        acc, _ = dev(nn_ref.bf16_round(rng_acc), shift)
+        nn.nn_copy_channels(cat, Cdst, 8, acc, 32, 8, D * H * W, 24, 1)
+        outs.append(acc.clone())
+        torch.cuda.synchronize()
+        return outs
+
+    rng_x = rng.normal(size=(N, D, H, W, C))
+    rng_gp = rng.normal(size=(N, 2, 3, 4, C))
+    rng_y = rng.normal(size=(N, 2, 3, 4, C))
+    rng_cat = rng.normal(size=(N, D, H, W, Cdst))
+    rng_acc = rng.normal(size=(N, D, H, W, 32))
+    vec, sca = run(0), run(1)
+    for a, b in zip(vec, sca):
+        assert torch.equal(a, b)
+    # and the values are the reference ones
+    assert np.allclose(host(vec[0]).reshape(N, 2, 3, 4, C), nn_ref.pool2(nn_ref.bf16_round(rng_x)), rtol=2 ** -8,
+                       atol=1e-3)
+    up = nn_ref.up2(nn_ref.bf16_round(rng_y))
+    assert np.array_equal(host(vec[2]).reshape(N, D, H, W, Cdst)[..., c0:c0 + C], up)
+
+
 def test_adam_step():
     rng = np.random.default_rng(5)
     W = rng.normal(size=1000).astype(np.float32)
