@@ -23,6 +23,12 @@
 // mbarrier is bounded; on time-out the CTA records an error, waits (bounded)
 // for its own copies and products in flight, frees its tensor memory and
 // returns.
+//
+// The weight gradient (conv3d_wgrad) is the GEMM with the (tap, input
+// channel) pairs as M, output channels as N and voxels as K. Activations and
+// output gradients are voxel-major, which is the MN-major operand layout for
+// that GEMM, so its TMA boxes feed tcgen05.mma directly (see the kernel's
+// own comment).
 #include <algorithm>
 #include <cstdint>
 #include <cstdio>
