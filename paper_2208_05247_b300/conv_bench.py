@@ -4,6 +4,7 @@
     python -m paper_2208_05247_b300.conv_bench --unet 128
     python -m paper_2208_05247_b300.conv_bench --layers 128
     python -m paper_2208_05247_b300.conv_bench --wgrad 128
+    python -m paper_2208_05247_b300.conv_bench --unet-forward 128
 
 Prints one JSON line per kernel: CUDA-event time per launch (after warm-up, on
 the current stream) and the dense FLOP rate 2 * 27 * Cin * Cout * voxels / t.
@@ -12,7 +13,8 @@ with --layers D every 3x3x3 layer shape of the U-Net's forward pass and input
 gradients at D^3, with the mma.sync kernel, the per-tap tcgen05 kernel and the
 default tcgen05 choice (halo-tiled where it fits); with --wgrad D the weight
 gradient of every 3x3x3 forward layer at D^3 (mma.sync and tcgen05; the same
-2 * 27 * Cin * Cout * voxels FLOPs).
+2 * 27 * Cin * Cout * voxels FLOPs); with --unet-forward D three untimed and
+one timed forward pass of the U-Net (default kernels; for launch lists).
 """
 from __future__ import annotations
 
@@ -113,6 +115,25 @@ def time_unet(d, path, reps=3):
             "forward_tflops": net.flops(shape) / (fwd / reps * 1e-3) / 1e12}
 
 
+def unet_forward(d):
+    """Three untimed forward passes and one timed one (CUDA events)."""
+    import torch
+    from . import denoise
+    net = denoise.UNet(seed=0)
+    shape = (d, d, d)
+    x = torch.randn(d ** 3 * denoise.CIN, device="cuda").to(torch.bfloat16)
+    for _ in range(3):
+        net.forward(x, shape)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    net.forward(x, shape)
+    b.record()
+    torch.cuda.synchronize()
+    nn.nn_status()
+    return {"unet_forward": d, "ms": a.elapsed_time(b)}
+
+
 def unet_layers(d):
     """(shape, Cin, Cout) of the U-Net's 3x3x3 forward convolutions and input
     gradients at d^3 (an input gradient is a convolution with Cin and Cout swapped)."""
@@ -140,8 +161,12 @@ def main(argv=None):
     p.add_argument("--unet", type=int, default=0, help="time the whole U-Net at this edge length instead")
     p.add_argument("--layers", type=int, default=0, help="time every U-Net layer shape at this edge length")
     p.add_argument("--wgrad", type=int, default=0, help="time every U-Net weight gradient at this edge length")
+    p.add_argument("--unet-forward", type=int, default=0, help="3 untimed + 1 timed U-Net forward at this edge length")
     a = p.parse_args(argv)
     build.build()
+    if a.unet_forward:
+        print(json.dumps(unet_forward(a.unet_forward)), flush=True)
+        return
     if a.wgrad:
         for shape, cin, cout in unet_layers(a.wgrad)[:11]:
             for path in ("mma.sync", "tcgen05"):
