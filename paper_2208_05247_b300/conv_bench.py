@@ -5,6 +5,7 @@
     python -m paper_2208_05247_b300.conv_bench --layers 128
     python -m paper_2208_05247_b300.conv_bench --wgrad 128
     python -m paper_2208_05247_b300.conv_bench --unet-forward 128
+    python -m paper_2208_05247_b300.conv_bench --pack 128
 
 Prints one JSON line per kernel: CUDA-event time per launch (after warm-up, on
 the current stream) and the dense FLOP rate 2 * 27 * Cin * Cout * voxels / t.
@@ -14,7 +15,8 @@ gradients at D^3, with the mma.sync kernel, the per-tap tcgen05 kernel and the
 default tcgen05 choice (halo-tiled where it fits); with --wgrad D the weight
 gradient of every 3x3x3 forward layer at D^3 (mma.sync and tcgen05; the same
 2 * 27 * Cin * Cout * voxels FLOPs); with --unet-forward D three untimed and
-one timed forward pass of the U-Net (default kernels; for launch lists).
+one timed forward pass of the U-Net (default kernels; for launch lists); with
+--pack D the input packing and output unpacking of the denoiser at D^3.
 """
 from __future__ import annotations
 
@@ -134,6 +136,37 @@ def unet_forward(d):
     return {"unet_forward": d, "ms": a.elapsed_time(b)}
 
 
+def time_pack(d, reps=20):
+    """CUDA-event time of nn_pack_inputs and nn_unpack at d^3 (best of 3 blocks)."""
+    import torch
+    from . import denoise
+    n3, n2 = d ** 3, d ** 2
+    g = torch.Generator(device="cuda").manual_seed(0)
+    r = lambda n, dt=torch.float32: torch.rand(n, device="cuda", generator=g).to(dt)   # noqa: E731
+    abs3d, sdir, sdif = r(n3, torch.float64), r(n2, torch.float64), r(n2, torch.float64)
+    opt = [r(n3) for _ in range(5)]
+    x = torch.empty(n3 * denoise.CIN, dtype=torch.bfloat16, device="cuda")
+    pred = r(n3 * denoise.COUT)
+    o3, o1, o2 = r(n3, torch.float64), r(n2, torch.float64), r(n2, torch.float64)
+    out = {}
+    for name, fn in (("pack_ms", lambda: nn.nn_pack_inputs(abs3d, sdir, sdif, *opt, x, d, d, d, 25.0, 866.0)),
+                     ("unpack_ms", lambda: nn.nn_unpack(x, pred, denoise.COUT, o3, o1, o2, d, d, d, 25.0, 866.0))):
+        for _ in range(3):
+            fn()
+        best = None
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / reps
+            best = t if best is None else min(best, t)
+        out[name] = best
+    return {"pack": d, **out}
+
+
 def unet_layers(d):
     """(shape, Cin, Cout) of the U-Net's 3x3x3 forward convolutions and input
     gradients at d^3 (an input gradient is a convolution with Cin and Cout swapped)."""
@@ -162,8 +195,12 @@ def main(argv=None):
     p.add_argument("--layers", type=int, default=0, help="time every U-Net layer shape at this edge length")
     p.add_argument("--wgrad", type=int, default=0, help="time every U-Net weight gradient at this edge length")
     p.add_argument("--unet-forward", type=int, default=0, help="3 untimed + 1 timed U-Net forward at this edge length")
+    p.add_argument("--pack", type=int, default=0, help="time the denoiser's input packing and unpacking at this edge")
     a = p.parse_args(argv)
     build.build()
+    if a.pack:
+        print(json.dumps(time_pack(a.pack)), flush=True)
+        return
     if a.unet_forward:
         print(json.dumps(unet_forward(a.unet_forward)), flush=True)
         return

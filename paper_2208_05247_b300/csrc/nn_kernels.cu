@@ -762,16 +762,27 @@ __global__ void unpack_kernel(const __nv_bfloat16 *in, const float *pred, int Cp
         abs3d[v] = (double)a * F / (100.0 * dz);
     }
     // every layer of a column is trained to predict the same surface
-    // correction; their mean is the surface estimate
+    // correction; their mean is the surface estimate. One warp per column:
+    // lane l sums layers l, l + 32, ...; the warp adds the partial sums in a
+    // fixed order (blockDim is a multiple of 32, so every warp is whole).
     const long long nc = (long long)H * W;
-    GRID_LOOP(c, nc) {
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nc; c += nwarps) {
         float s1 = 0.f, s2 = 0.f;
-        for (int k = 0; k < D; ++k) {
+        for (int k = lane; k < D; k += 32) {
             s1 += pred[(k * nc + c) * Cp + 1];
             s2 += pred[(k * nc + c) * Cp + 2];
         }
-        sdir[c] = (double)(__bfloat162float(in[c * 16 + 1]) + s1 / D) * F;
-        sdif[c] = (double)(__bfloat162float(in[c * 16 + 2]) + s2 / D) * F;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            sdir[c] = (double)(__bfloat162float(in[c * 16 + 1]) + s1 / D) * F;
+            sdif[c] = (double)(__bfloat162float(in[c * 16 + 2]) + s2 / D) * F;
+        }
     }
 }
 
