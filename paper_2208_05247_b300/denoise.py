@@ -494,6 +494,22 @@ def heating_factor(nz, dz):
     return 86400.0 / (1.225 * np.exp(-zc / 8000.0) * 1004.0)
 
 
+def plain_time_fit(plain_ppc, ms):
+    """Least-squares line time = t0 + t1 * ppc through the plain runs' times."""
+    t1, t0 = np.polyfit(np.asarray(plain_ppc, dtype=np.float64), np.asarray(ms, dtype=np.float64), 1)
+    return float(t0), float(t1)
+
+
+def plain_ppc_to_match(plain_ppc, rmse, target):
+    """Photons/column at which the plain tracer's RMSE reaches `target`.
+
+    The plain RMSE is modelled as a / sqrt(ppc) (Sec. 3.2: Monte Carlo error
+    falls as N^-1/2) with a the geometric mean of rmse * sqrt(ppc) over the
+    runs; the answer is (a / target)^2."""
+    a = float(np.exp(np.mean([math.log(e * math.sqrt(p)) for p, e in zip(plain_ppc, rmse)])))
+    return (a / target) ** 2
+
+
 def torch_rms(a, b):
     """RMS difference of two device tensors."""
     return ((a - b) ** 2).mean().sqrt().item()
@@ -603,12 +619,10 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), trut
                         "ms": den[2] / n},
            "noisy_input": {"rmse_ghi": math.sqrt(noisy[0] / n), "rmse_hr": math.sqrt(noisy[1] / n)}}
     # plain tracer: RMSE = a / sqrt(ppc) (fixed slope -1/2) and time = t0 + t1 ppc
-    pp = np.array(plain_ppc, dtype=np.float64)
-    t1, t0 = np.polyfit(pp, [plain[p]["ms"] for p in plain_ppc], 1)
-    res["plain_time_fit_ms"] = {"t0": float(t0), "per_ppc": float(t1)}
+    t0, t1 = plain_time_fit(plain_ppc, [plain[p]["ms"] for p in plain_ppc])
+    res["plain_time_fit_ms"] = {"t0": t0, "per_ppc": t1}
     for key in ("rmse_ghi", "rmse_hr"):
-        a = float(np.exp(np.mean([math.log(plain[p][key] * math.sqrt(p)) for p in plain_ppc])))
-        ppc_match = (a / res["denoised"][key]) ** 2
+        ppc_match = plain_ppc_to_match(plain_ppc, [plain[p][key] for p in plain_ppc], res["denoised"][key])
         t_match = t0 + t1 * ppc_match
         name = key.split("_")[1]
         res["plain_ppc_to_match_" + name] = ppc_match
@@ -624,15 +638,14 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024), trut
         # share the direct term, so they differ only in the diffuse part; the
         # plain diffuse RMSE is fitted as a / sqrt(ppc) and its time includes
         # the direct solve.
-        ad = float(np.exp(np.mean([math.log(math.sqrt(comp["plain%d_dif" % p] / n) * math.sqrt(p))
-                                   for p in plain_ppc])))
-        d_err = math.sqrt(comp["den_dif"] / n)
+        p_dif = plain_ppc_to_match(plain_ppc, [math.sqrt(comp["plain%d_dif" % p] / n) for p in plain_ppc],
+                                   math.sqrt(comp["den_dif"] / n))
         res["surface"]["speedup_ghi_vs_plain_exact_direct"] = (
-            (t0 + t1 * (ad / d_err) ** 2 + dms_sum / n) / res["denoised"]["ms"])
+            (t0 + t1 * p_dif + dms_sum / n) / res["denoised"]["ms"])
         # the network's own surface-direct estimate, for comparison
-        an = float(np.exp(np.mean([math.log(plain[p]["rmse_ghi"] * math.sqrt(p)) for p in plain_ppc])))
-        e_net = math.sqrt(comp["network_ghi"] / n)
-        res["surface"]["network_only_speedup_ghi"] = (t0 + t1 * (an / e_net) ** 2) / res["denoised"]["ms"]
+        p_net = plain_ppc_to_match(plain_ppc, [plain[p]["rmse_ghi"] for p in plain_ppc],
+                                   math.sqrt(comp["network_ghi"] / n))
+        res["surface"]["network_only_speedup_ghi"] = (t0 + t1 * p_net) / res["denoised"]["ms"]
     return res
 
 

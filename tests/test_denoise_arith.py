@@ -1,0 +1,40 @@
+"""The time-to-RMSE arithmetic behind the denoiser speed-ups (CPU only):
+the plain tracer's RMSE is modelled as a / sqrt(ppc) (Monte Carlo error falls
+as N^-1/2, Sec. 3.2) and its wall time as t0 + t1 * ppc."""
+import math
+
+import numpy as np
+
+from paper_2208_05247_b300 import denoise
+
+PPC = (4, 16, 64, 256, 1024)
+
+
+def test_exact_model_is_recovered():
+    a, t0, t1 = 417.0, 2.6, 0.0167
+    rmse = [a / math.sqrt(p) for p in PPC]
+    ms = [t0 + t1 * p for p in PPC]
+    f0, f1 = denoise.plain_time_fit(PPC, ms)
+    assert math.isclose(f0, t0, rel_tol=1e-9) and math.isclose(f1, t1, rel_tol=1e-9)
+    for target in (200.0, 13.0, 8.0, 0.5):
+        assert math.isclose(denoise.plain_ppc_to_match(PPC, rmse, target), (a / target) ** 2, rel_tol=1e-12)
+
+
+def test_prefactor_is_the_geometric_mean():
+    """Run-to-run scatter whose factors multiply to one leaves a unchanged."""
+    a = 7.25
+    f = [1.1, 1 / 1.1, 1.0, 1.05, 1 / 1.05]
+    rmse = [a / math.sqrt(p) * k for p, k in zip(PPC, f)]
+    assert math.isclose(denoise.plain_ppc_to_match(PPC, rmse, 0.0785), (a / 0.0785) ** 2, rel_tol=1e-12)
+    # halving the target error needs four times the photons
+    r1 = denoise.plain_ppc_to_match(PPC, rmse, 0.2)
+    assert math.isclose(denoise.plain_ppc_to_match(PPC, rmse, 0.1), 4 * r1, rel_tol=1e-12)
+
+
+def test_time_fit_is_least_squares():
+    rng = np.random.default_rng(0)
+    ms = [2.6 + 0.0167 * p + e for p, e in zip(PPC, rng.normal(0, 0.05, len(PPC)))]
+    t0, t1 = denoise.plain_time_fit(PPC, ms)
+    A = np.stack([np.ones(len(PPC)), np.array(PPC, float)], 1)
+    want = np.linalg.lstsq(A, np.array(ms), rcond=None)[0]
+    assert np.allclose([t0, t1], want, rtol=1e-10, atol=1e-12)
