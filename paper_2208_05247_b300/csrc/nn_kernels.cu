@@ -709,10 +709,13 @@ __global__ void direct_surface_kernel(const float *kg, const float *kc, int D, i
     }
 }
 
+// s_abs = 100 dz / F and s_sfc = 1 / F come from the host: FP64 divisions
+// are slow on this GPU, and a product with the reciprocal moves the value by
+// at most an FP64 ulp or two before it is rounded to FP32 and BF16.
 __global__ void pack_inputs_kernel(const double *abs3d, const double *sdir, const double *sdif, const float *kg,
                                    const float *wg, const float *kc, const float *wc, const float *gc,
                                    const float *t3, const float *t2, __nv_bfloat16 *out, int D, int H, int W,
-                                   double dz, double F)
+                                   float dz, double s_abs, double s_sfc)
 {
     const long long n = (long long)D * H * W;
     GRID_LOOP(v, n) {
@@ -720,10 +723,10 @@ __global__ void pack_inputs_kernel(const double *abs3d, const double *sdir, cons
         const float ke = kg[v] + kc[v];
         const float ks = kg[v] * wg[v] + kc[v] * wc[v];
         float ch[16];
-        ch[0] = (float)(100.0 * abs3d[v] * dz / F);
-        ch[1] = (float)(sdir[col] / F);
-        ch[2] = (float)(sdif[col] / F);
-        ch[3] = logf(ke * (float)dz + 1e-4f) / 5.0f;
+        ch[0] = (float)(abs3d[v] * s_abs);
+        ch[1] = (float)(sdir[col] * s_sfc);
+        ch[2] = (float)(sdif[col] * s_sfc);
+        ch[3] = logf(ke * dz + 1e-4f) / 5.0f;
         ch[4] = ke > 0.f ? ks / ke : 1.0f;
         ch[5] = gc[v];
         ch[6] = t3 ? t3[v] : 0.f;
@@ -736,30 +739,31 @@ __global__ void pack_inputs_kernel(const double *abs3d, const double *sdir, cons
 
 __global__ void pack_targets_kernel(const double *abs_hi, const double *sdir_hi, const double *sdif_hi,
                                     const double *abs_lo, const double *sdir_lo, const double *sdif_lo,
-                                    float *out, int D, int H, int W, double dz, double F)
+                                    float *out, int D, int H, int W, double s_abs, double s_sfc)
 {
     const long long n = (long long)D * H * W;
     GRID_LOOP(v, n) {
         const long long col = v % ((long long)H * W);
         // the noisy value exactly as the input channel holds it (BF16-rounded)
-        const float lo0 = __bfloat162float(__float2bfloat16_rn((float)(100.0 * abs_lo[v] * dz / F)));
-        const float lo1 = __bfloat162float(__float2bfloat16_rn((float)(sdir_lo[col] / F)));
-        const float lo2 = __bfloat162float(__float2bfloat16_rn((float)(sdif_lo[col] / F)));
-        out[v * 3 + 0] = (float)(100.0 * abs_hi[v] * dz / F) - lo0;
-        out[v * 3 + 1] = (float)(sdir_hi[col] / F) - lo1;
-        out[v * 3 + 2] = (float)(sdif_hi[col] / F) - lo2;
+        const float lo0 = __bfloat162float(__float2bfloat16_rn((float)(abs_lo[v] * s_abs)));
+        const float lo1 = __bfloat162float(__float2bfloat16_rn((float)(sdir_lo[col] * s_sfc)));
+        const float lo2 = __bfloat162float(__float2bfloat16_rn((float)(sdif_lo[col] * s_sfc)));
+        out[v * 3 + 0] = (float)(abs_hi[v] * s_abs) - lo0;
+        out[v * 3 + 1] = (float)(sdir_hi[col] * s_sfc) - lo1;
+        out[v * 3 + 2] = (float)(sdif_hi[col] * s_sfc) - lo2;
     }
 }
 
 // denoised fields: noisy input channel + predicted correction, back to
 // physical units; surface fields from the mean correction over each column
+// s_out = F / (100 dz) from the host (see pack_inputs_kernel)
 __global__ void unpack_kernel(const __nv_bfloat16 *in, const float *pred, int Cp, double *abs3d, double *sdir,
-                              double *sdif, int D, int H, int W, double dz, double F)
+                              double *sdif, int D, int H, int W, double s_out, double F)
 {
     const long long n = (long long)D * H * W;
     GRID_LOOP(v, n) {
         const float a = __bfloat162float(in[v * 16 + 0]) + pred[v * Cp + 0];
-        abs3d[v] = (double)a * F / (100.0 * dz);
+        abs3d[v] = (double)a * s_out;
     }
     // every layer of a column is trained to predict the same surface
     // correction; their mean is the surface estimate. One warp per column:
@@ -1051,7 +1055,7 @@ int nn_pack_inputs(const double *abs3d, const double *sfc_dir, const double *sfc
         return inval("nn_pack_inputs: bad argument");
     pack_inputs_kernel<<<grid1d((long long)D * H * W), 256, 0, (cudaStream_t)stream>>>(
         abs3d, sfc_dir, sfc_dif, k_gas, ssa_gas, k_cld, ssa_cld, g_cld, t3d, t2d, (__nv_bfloat16 *)out, D, H, W,
-        dz, flux);
+        (float)dz, 100.0 * dz / flux, 1.0 / flux);
     return check_launch("nn_pack_inputs");
 }
 
@@ -1062,7 +1066,7 @@ int nn_pack_targets(const double *abs_hi, const double *sdir_hi, const double *s
     if (!abs_hi || !sdir_hi || !sdif_hi || !abs_lo || !sdir_lo || !sdif_lo || !out || !(flux > 0))
         return inval("nn_pack_targets: bad argument");
     pack_targets_kernel<<<grid1d((long long)D * H * W), 256, 0, (cudaStream_t)stream>>>(
-        abs_hi, sdir_hi, sdif_hi, abs_lo, sdir_lo, sdif_lo, out, D, H, W, dz, flux);
+        abs_hi, sdir_hi, sdif_hi, abs_lo, sdir_lo, sdif_lo, out, D, H, W, 100.0 * dz / flux, 1.0 / flux);
     return check_launch("nn_pack_targets");
 }
 
@@ -1071,7 +1075,7 @@ int nn_unpack(const void *in, const float *pred, int Cp, double *abs3d, double *
 {
     if (!in || !pred || !abs3d || !sfc_dir || !sfc_dif || Cp < 3 || !(flux > 0)) return inval("nn_unpack: bad argument");
     unpack_kernel<<<grid1d((long long)D * H * W), 256, 0, (cudaStream_t)stream>>>(
-        (const __nv_bfloat16 *)in, pred, Cp, abs3d, sfc_dir, sfc_dif, D, H, W, dz, flux);
+        (const __nv_bfloat16 *)in, pred, Cp, abs3d, sfc_dir, sfc_dif, D, H, W, flux / (100.0 * dz), flux);
     return check_launch("nn_unpack");
 }
 
