@@ -40,9 +40,10 @@ METRIC = "photon collision events/s & wall time to target RMS GHI/heating error,
 UNIT = "events/s"
 SZA, AZ, F0 = 30.0, 0.0, 1000.0
 SEED = 20220926
-COARSE = (4, 4, 4)
+COARSE = (2, 2, 2)
 # Algorithmic bytes of the transport kernel: 16 B optics record + 16 B FP64
-# tally read-modify-write per majorant event, 4 B majorant per coarse crossing.
+# tally read-modify-write per majorant event, 4 B majorant box word per walk
+# step (the "crossings" counter).
 BYTES_PER_EVENT, BYTES_PER_CROSSING = 32, 4
 # derive, albedo check, majorant, column keys + column order (launch order),
 # transport, 4 field sums, heating rate
@@ -203,10 +204,19 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args, 1),
+            "data": "synthetic",
+            "config": dict(workload_config(args, 1),
+                           sample=f"bounded sample: each step traces {ppc} photon/column ({ppc * scene.ncol} "
+                                  f"photons) of this workload with the FP64 analog oracle, not "
+                                  f"{args.ppc} photons/column",
+                           photons_per_step_traced=ppc * scene.ncol),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-                             "photons_per_s": photons / secs},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                             "photons_per_s": photons / secs,
+                             "note": "events are the oracle's real (analog) collisions; the GPU arm counts "
+                                     "majorant events, null collisions included, so photons_per_s is the "
+                                     "like-for-like rate"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                    "photons_per_s": photons / secs}}
     print(json.dumps(line), flush=True)
 
 

@@ -113,13 +113,27 @@ typedef struct {
     int birth;                   /* RT_BIRTH_*; default RT_BIRTH_PHILOX */
     int schedule;                /* RT_SCHEDULE_*; applies from the next rt_build_accel;
                                     default RT_SCHEDULE_THICK_FIRST */
+    int box_levels;              /* majorant boxes (see rt_build_accel): 0..4 dilation levels,
+                                    i.e. box radii up to 0, 1, 3, 7 or 15 coarse cells; 0 = every
+                                    walk step crosses one coarse cell; applies from the next
+                                    rt_build_accel; default 4 */
+    float box_tau;               /* largest majorant optical depth across a box diagonal; 0 selects
+                                    the default 0.5; applies from the next rt_build_accel */
+    int tally_aggregate;         /* 1: in single-scene launches, lanes of a warp that flush
+                                    absorption into the same cell sum their FP32 partials first and
+                                    issue one FP64 atomic (fewer atomics; results then reproduce
+                                    across launch shapes to FP32 rounding only); 0 (default): one
+                                    atomic per photon and cell, reproducible to FP64 rounding */
+    int refill_min;              /* lanes of a warp whose photons ended that it gathers before it
+                                    starts new photons (births run with only those lanes active);
+                                    0 = 8 */
 } rt_options;
 
 typedef struct {
     uint64_t photons;            /* photons traced since the last reset */
     uint64_t events;             /* majorant events (real scatterings + null collisions) */
     uint64_t scatters;           /* real scattering events */
-    uint64_t crossings;          /* coarse-cell face crossings */
+    uint64_t crossings;          /* walk steps that crossed a box face (see rt_build_accel) */
     uint64_t surface_hits;
     uint64_t roulette_kills;
     uint64_t capped;             /* photons stopped by the step cap */
@@ -180,7 +194,20 @@ int rt_set_surface(rt_handle h, const float *albedo, int mem);
  * cells hold the largest extinction of the fine cells they cover, used as the
  * null-collision coefficient, without recursion). cx, cy, cz are the coarsening
  * factors (fine cells per coarse cell); the last coarse cell along an axis
- * covers the remainder. 0,0,0 selects 4,4,4 clipped to the grid. */
+ * covers the remainder. 0,0,0 selects the library default, 2,2,2 clipped to
+ * the grid (the fastest factors measured on the 256 x 256 x 128 cumulus scene;
+ * the caller-side autotuner in the Python package picks factors for other
+ * scenes by timing trial launches).
+ *
+ * With rt_options.box_levels > 0 the grid also gets majorant boxes: each coarse
+ * cell carries the cube of coarse cells within radius r of it (r one of 0, 1,
+ * 3, 7, 15; periodic in x and y, clipped at the surface and the top) and the
+ * largest extinction in that cube, with r the largest radius whose maximum
+ * times the cube's diagonal stays below rt_options.box_tau. A walk step from
+ * that cell crosses the whole cube with the cube's maximum as its majorant:
+ * still an upper bound everywhere on the step, so the null-collision estimator
+ * keeps its expectation, while a step through clear air replaces up to 31
+ * coarse-cell crossings. */
 int rt_build_accel(rt_handle h, int cx, int cy, int cz);
 
 /* Trace `photons` photons of one spectral quadrature point and ADD their
@@ -358,9 +385,9 @@ int rt_step_destroy(rt_step s);
  * a status word and the majorant grid live in one fixed device array of
  * 4 MiB + 256 B inside the library, which every GPU that loads the library
  * holds until the process exits. The majorant grid must fit in it: at most
- * 1,048,576 coarse cells, otherwise RT_E_INVAL. The first call on a device
- * looks the array's device address up once (cudaGetSymbolAddress); make that
- * first call before any stream capture. All calls on a device share the array
+ * 1,048,576 coarse cells, otherwise RT_E_INVAL. Every call looks the array's
+ * device address up in the current context (cudaGetSymbolAddress) and
+ * synchronises `stream` before it returns. All calls on a device share the array
  * and it keeps the last call's contents (each call clears what must start at
  * zero), so calls whose work overlaps on the GPU race: serialise them.
  * Errors: RT_E_INVAL (sizes, pointers, angles, too many coarse cells, invalid

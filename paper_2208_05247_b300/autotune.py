@@ -1,8 +1,8 @@
 """Launch-parameter autotuner for the transport kernel.
 
-Chooses the coarse-grid factors (majorant resolution), the event-batching
-threshold, the bound on face-crossing sweeps, the refill chunk and the block
-shape by coordinate descent. Each candidate is timed with CUDA events on the
+Chooses the coarse-grid factors (majorant resolution), the majorant-box
+levels, the event-batching threshold, the bound on walk sweeps, the refill
+threshold and chunk and the block shape by coordinate descent. Each candidate is timed with CUDA events on the
 tracer's stream: majorant build plus one trace of the given photons.
 
 Candidates are ranked by PHOTONS per second, not events per second: a coarser
@@ -14,11 +14,13 @@ from __future__ import annotations
 import itertools
 
 
-COARSE = [(2, 2, 2), (4, 4, 2), (4, 4, 4), (8, 8, 4), (4, 4, 8), (8, 8, 8), (16, 16, 4), (16, 16, 8)]
-THRESHOLDS = [8, 16, 24, 28, 32]
-MAX_INNER = [2, 4, 8, 16, 32, 64]
+COARSE = [(2, 2, 2), (2, 2, 1), (4, 4, 2), (4, 4, 4), (8, 8, 4), (8, 8, 8)]
+BOX_LEVELS = [0, 2, 3, 4]
+THRESHOLDS = [8, 12, 16, 20, 24]
+MAX_INNER = [8, 16, 64]
+REFILL_MIN = [1, 4, 8, 16]
 CHUNKS = [32, 64, 128]
-BLOCKS = [(256, 0), (128, 0), (256, 2), (256, 3)]
+BLOCKS = [(256, 0), (128, 0), (256, 4)]
 
 
 def _valid_coarse(c, t):
@@ -54,8 +56,8 @@ def autotune(tracer, sza, az, flux, photons, seed=1, repeats=2, verbose=False):
     measurement as dicts (photons/s, events/s, ms).
     """
     table = []
-    cur = {"coarse": (4, 4, 4), "ready_threshold": 16, "max_inner": 16, "refill_chunk": 32,
-           "block_size": 256, "blocks_per_sm": 0}
+    cur = {"coarse": (2, 2, 2), "box_levels": 4, "ready_threshold": 16, "max_inner": 64, "refill_min": 8,
+           "refill_chunk": 128, "block_size": 256, "blocks_per_sm": 0}
 
     def measure(cfg):
         opts = {k: v for k, v in cfg.items() if k != "coarse"}
@@ -70,8 +72,10 @@ def autotune(tracer, sza, az, flux, photons, seed=1, repeats=2, verbose=False):
     best = measure(cur)
     stages = [
         ("coarse", [c for c in COARSE if _valid_coarse(c, tracer)]),
+        ("box_levels", BOX_LEVELS),
         ("ready_threshold", THRESHOLDS),
         ("max_inner", MAX_INNER),
+        ("refill_min", REFILL_MIN),
         ("refill_chunk", CHUNKS),
         ("block", BLOCKS),
     ]
@@ -94,8 +98,8 @@ def autotune(tracer, sza, az, flux, photons, seed=1, repeats=2, verbose=False):
                 continue
             if row["photons_per_s"] > best["photons_per_s"]:
                 best = row
-    final = {k: best[k] for k in ("coarse", "ready_threshold", "max_inner", "refill_chunk", "block_size",
-                                  "blocks_per_sm")}
+    final = {k: best[k] for k in ("coarse", "box_levels", "ready_threshold", "max_inner", "refill_min",
+                                  "refill_chunk", "block_size", "blocks_per_sm")}
     tracer.set_options(**{k: v for k, v in final.items() if k != "coarse"})
     tracer.build_accel(*final["coarse"])
     return final, table

@@ -1,6 +1,7 @@
 // rt_api.cu -- host side of the C ABI declared in include/rt.h: handle
 // lifecycle, input validation, device buffers and kernel launches.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -38,9 +39,12 @@ int fail(int code, const char *fmt, ...)
     } while (0)
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr uint32_t kDefaultMaxSteps = 10000000u;
-constexpr int kDefaultReadyThreshold = 16;
-constexpr int kDefaultMaxInner = 16;
+using rt::kDefaultBoxLevels;
+using rt::kDefaultBoxTau;
+using rt::kDefaultMaxInner;
+using rt::kDefaultMaxSteps;
+using rt::kDefaultReadyThreshold;
+using rt::kDefaultRefillMin;
 constexpr uint64_t kOrderMinPhotonsPerColumn = 64;
 
 template <typename T>
@@ -92,6 +96,13 @@ struct rt_scene {
     float *kmax = nullptr;
     int cx = 0, cy = 0, cz = 0, NX = 0, NY = 0, NZ = 0;
     size_t kmax_cap = 0;
+
+    // majorant boxes (box words per coarse cell) and the scratch of their build;
+    // batched launches: {gas, cloud} box words and two more scratch arrays
+    uint32_t *box = nullptr;
+    uint2 *box2 = nullptr;
+    float *bw[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t box_cap = 0, box2_cap = 0;
 
     // launch order of the columns (RT_SCHEDULE_THICK_FIRST) and its sort keys
     uint32_t *order = nullptr;
@@ -321,14 +332,47 @@ int device_status(rt_handle h)
     return RT_OK;
 }
 
+// Majorant boxes of the current majorant grid (single-scene words).
+cudaError_t build_boxes_of(rt_handle h, cudaStream_t st)
+{
+    return rt::build_boxes(h->kmax, h->box, h->bw[0], h->bw[1], h->NX, h->NY, h->NZ, h->cx * h->dx, h->cy * h->dy,
+                           h->cz * h->dz, h->opt.box_levels, h->opt.box_tau > 0 ? h->opt.box_tau : kDefaultBoxTau,
+                           h->nx % h->cx == 0 && h->ny % h->cy == 0, st);
+}
+
+// Box buffers for n coarse cells (two scratch arrays, four with the split ones).
+int ensure_boxes(rt_handle h, size_t n, bool split)
+{
+    int rc;
+    if (n > h->box_cap) {
+        cudaFree(h->box);
+        cudaFree(h->bw[0]);
+        cudaFree(h->bw[1]);
+        h->box = nullptr; h->bw[0] = h->bw[1] = nullptr;
+        h->box_cap = 0;
+        if ((rc = dev_alloc(&h->box, n)) || (rc = dev_alloc(&h->bw[0], n)) || (rc = dev_alloc(&h->bw[1], n))) return rc;
+        h->box_cap = n;
+    }
+    if (split && n > h->box2_cap) {
+        cudaFree(h->box2);
+        cudaFree(h->bw[2]);
+        cudaFree(h->bw[3]);
+        h->box2 = nullptr; h->bw[2] = h->bw[3] = nullptr;
+        h->box2_cap = 0;
+        if ((rc = dev_alloc(&h->box2, n)) || (rc = dev_alloc(&h->bw[2], n)) || (rc = dev_alloc(&h->bw[3], n))) return rc;
+        h->box2_cap = n;
+    }
+    return RT_OK;
+}
+
 template <typename T>
 rt::SceneDev<T> scene_desc(rt_handle h, T *base, bool batch)
 {
     rt::SceneDev<T> S{};
     S.rec = batch ? h->rec2 : h->rec;
     S.gcl = h->gcl;
-    S.kmax = h->kmax;
-    S.kmax2 = h->kmax2;
+    S.box = h->box;
+    S.box2 = h->box2;
     S.alb = h->alb;
     S.tal = tallies_of(base, h->ncell, h->ncol);
     S.scr = h->scr;
@@ -341,6 +385,14 @@ rt::SceneDev<T> scene_desc(rt_handle h, T *base, bool batch)
     S.inv_dx = (float)(1.0 / h->dx); S.inv_dy = (float)(1.0 / h->dy); S.inv_dz = (float)(1.0 / h->dz);
     S.Lx = (float)(h->nx * h->dx); S.Ly = (float)(h->ny * h->dy); S.H = (float)(h->nz * h->dz);
     S.cdx = (float)(h->cx * h->dx); S.cdy = (float)(h->cy * h->dy); S.cdz = (float)(h->cz * h->dz);
+    S.inv_cdx = (float)(1.0 / (h->cx * h->dx));
+    S.inv_cdy = (float)(1.0 / (h->cy * h->dy));
+    S.inv_cdz = (float)(1.0 / (h->cz * h->dz));
+    const bool rx = h->nx % h->cx != 0, ry = h->ny % h->cy != 0;   // a shorter last coarse cell
+    S.xcap = rx ? S.Lx : INFINITY;
+    S.ycap = ry ? S.Ly : INFINITY;
+    S.fxcap = rx ? h->nx : INT_MAX;
+    S.fycap = ry ? h->ny : INT_MAX;
     return S;
 }
 
@@ -371,6 +423,39 @@ void fill_launch(rt_handle h, rt::TraceArgs<T> &A)
     A.chunk = (uint32_t)(h->opt.refill_chunk > 0 ? h->opt.refill_chunk : 32);
     A.ready_threshold = h->opt.ready_threshold > 0 ? h->opt.ready_threshold : kDefaultReadyThreshold;
     A.max_inner = h->opt.max_inner > 0 ? h->opt.max_inner : kDefaultMaxInner;
+    A.refill_min = h->opt.refill_min > 0 ? h->opt.refill_min : kDefaultRefillMin;
+}
+
+// The single-scene transport kernel of the handle's options: with or without
+// the grouped absorption flush.
+template <typename T>
+const void *single_kernel(rt_handle h)
+{
+    return h->opt.tally_aggregate ? reinterpret_cast<const void *>(rt::trace_kernel<T, rt::kOpticsRecord, true>)
+                                  : reinterpret_cast<const void *>(rt::trace_kernel<T, rt::kOpticsRecord, false>);
+}
+
+// Blocks per SM of a single-scene launch: the option, else as many as fit.
+template <typename T>
+int single_blocks_per_sm(rt_handle h, int block, int *bps)
+{
+    *bps = h->opt.blocks_per_sm;
+    if (*bps <= 0) {
+        RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, single_kernel<T>(h), block, 0));
+        *bps = std::max(1, *bps);
+    }
+    return RT_OK;
+}
+
+template <typename T>
+int launch_single(rt_handle h, const rt::TraceArgs<T> &A, int grid, int block, cudaStream_t st)
+{
+    if (h->opt.tally_aggregate)
+        rt::trace_kernel<T, rt::kOpticsRecord, true><<<grid, block, 0, st>>>(A);
+    else
+        rt::trace_kernel<T, rt::kOpticsRecord, false><<<grid, block, 0, st>>>(A);
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
 }
 
 template <typename T>
@@ -389,14 +474,10 @@ int launch_trace(rt_handle h, T *base, double sza, double az, double toa_flux, d
     set_order(h, A, begin, count);
 
     const int block = h->opt.block_size > 0 ? h->opt.block_size : 256;
-    int bps = h->opt.blocks_per_sm;
-    if (bps <= 0) {
-        RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rt::trace_kernel<T, false>, block, 0));
-        bps = std::max(1, bps);
-    }
+    int bps = 0, rc = single_blocks_per_sm<T>(h, block, &bps);
+    if (rc) return rc;
     RT_CUDA(cudaMemsetAsync(&h->scr->queue_head, 0, sizeof(unsigned long long), h->stream));
-    rt::trace_kernel<T, false><<<h->num_sms * bps, block, 0, h->stream>>>(A);
-    RT_CUDA(cudaGetLastError());
+    if ((rc = launch_single<T>(h, A, h->num_sms * bps, block, h->stream))) return rc;
     const double mu0 = std::cos(sza * kPi / 180.0);
     h->energy_in += toa_flux * mu0 * h->nx * h->dx * h->ny * h->dy * ((double)count / (double)total);
     return RT_OK;
@@ -443,16 +524,16 @@ int launch_batch(rt_handle home, const std::vector<rt_handle> &scenes, const std
     const int block = home->opt.block_size > 0 ? home->opt.block_size : 256;
     const size_t smem = bytes_s + bytes_j;
     if (smem > 48 * 1024)
-        RT_CUDA(cudaFuncSetAttribute(rt::trace_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        RT_CUDA(cudaFuncSetAttribute(rt::trace_kernel<T, rt::kOpticsSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     int bps = home->opt.blocks_per_sm;
     int fit = 0;
-    RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, rt::trace_kernel<T, true>, block, smem));
+    RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, rt::trace_kernel<T, rt::kOpticsSplit>, block, smem));
     if (fit <= 0) return fail(RT_E_INVAL, "rt_trace_batch: descriptors of %d jobs do not fit in shared memory",
                               (int)jobs.size());
     if (bps <= 0 || bps > fit) bps = fit;
     RT_CUDA(cudaMemsetAsync(&home->scr->queue_head, 0, sizeof(unsigned long long), home->stream));
-    rt::trace_kernel<T, true><<<home->num_sms * bps, block, smem, home->stream>>>(A);
+    rt::trace_kernel<T, rt::kOpticsSplit><<<home->num_sms * bps, block, smem, home->stream>>>(A);
     RT_CUDA(cudaGetLastError());
     return RT_OK;
 }
@@ -482,6 +563,7 @@ int record_step(rt_handle h, const rt_step_desc *d, rt_step s, cudaStream_t cs, 
     rt::build_majorant<<<grid_for(nc), 256, 0, cs>>>(h->rec, h->kmax, h->nx, h->ny, h->nz, h->cx, h->cy, h->cz,
                                                      h->NX, h->NY, h->NZ);
     RT_CUDA(cudaGetLastError());
+    RT_CUDA(build_boxes_of(h, cs));
     if (h->order_ok) {
         int rc = order_columns(h, cs);
         if (rc) return rc;
@@ -499,8 +581,8 @@ int record_step(rt_handle h, const rt_step_desc *d, rt_step s, cudaStream_t cs, 
     if constexpr (std::is_same<T, double>::value) s->a64 = A;
     else s->a32 = A;
     const int block = h->opt.block_size > 0 ? h->opt.block_size : 256;
-    rt::trace_kernel<T, false><<<h->num_sms * bps, block, 0, cs>>>(A);
-    RT_CUDA(cudaGetLastError());
+    int rc = launch_single<T>(h, A, h->num_sms * bps, block, cs);
+    if (rc) return rc;
     cudaStreamCaptureStatus st;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
@@ -602,6 +684,10 @@ rt_handle rt_create(int nx, int ny, int nz, double dx, double dy, double dz)
     h->opt.pcld_mode = RT_PCLD_SCATTERING;
     h->opt.tally_precision = RT_TALLY_FP64;
     h->opt.schedule = RT_SCHEDULE_THICK_FIRST;
+    h->opt.box_levels = kDefaultBoxLevels;
+    h->opt.box_tau = kDefaultBoxTau;
+    h->opt.tally_aggregate = 0;
+    h->opt.refill_min = kDefaultRefillMin;
     return h;
 }
 
@@ -619,6 +705,9 @@ int rt_destroy(rt_handle h)
     cudaFree(h->desc);
     cudaFree(h->alb);
     cudaFree(h->kmax);
+    cudaFree(h->box);
+    cudaFree(h->box2);
+    for (float *b : h->bw) cudaFree(b);
     cudaFree(h->order);
     cudaFree(h->okey);
     cudaFree(h->stage);
@@ -666,10 +755,21 @@ int rt_set_options(rt_handle h, const rt_options *o)
         return fail(RT_E_INVAL, "rt_set_options: unknown birth mode");
     if (o->schedule != RT_SCHEDULE_IDS && o->schedule != RT_SCHEDULE_THICK_FIRST)
         return fail(RT_E_INVAL, "rt_set_options: unknown schedule");
+    if (o->box_levels < 0 || o->box_levels > rt::kBoxLevels)
+        return fail(RT_E_INVAL, "rt_set_options: box_levels must be in [0, %d]", rt::kBoxLevels);
+    if (!(o->box_tau >= 0.0f) || !(o->box_tau <= 1e6f))
+        return fail(RT_E_INVAL, "rt_set_options: box_tau must be finite and >= 0");
+    if (o->refill_min < 0 || o->refill_min > 32)
+        return fail(RT_E_INVAL, "rt_set_options: refill_min must be in [0, 32]");
+    if (o->tally_aggregate != 0 && o->tally_aggregate != 1)
+        return fail(RT_E_INVAL, "rt_set_options: tally_aggregate must be 0 or 1");
     if (o->blocks_per_sm > 0) {
         int fit = 0;
         const int block = o->block_size > 0 ? o->block_size : 256;
-        RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, rt::trace_kernel<double, false>, block, 0));
+        RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &fit, o->tally_aggregate ? reinterpret_cast<const void *>(rt::trace_kernel<double, rt::kOpticsRecord, true>)
+                                     : reinterpret_cast<const void *>(rt::trace_kernel<double, rt::kOpticsRecord, false>),
+            block, 0));
         if (o->blocks_per_sm > fit)
             return fail(RT_E_INVAL, "rt_set_options: %d blocks/SM do not fit (max %d)", o->blocks_per_sm, fit);
     }
@@ -788,9 +888,9 @@ int rt_build_accel(rt_handle h, int cx, int cy, int cz)
     if (rc) return rc;
     if (!h->optics_ok) return fail(RT_E_STATE, "rt_build_accel: set valid optics first");
     if (cx == 0 && cy == 0 && cz == 0) {
-        cx = std::min(4, h->nx);
-        cy = std::min(4, h->ny);
-        cz = std::min(4, h->nz);
+        cx = std::min(rt::kDefaultCoarse, h->nx);
+        cy = std::min(rt::kDefaultCoarse, h->ny);
+        cz = std::min(rt::kDefaultCoarse, h->nz);
     }
     if (cx <= 0 || cy <= 0 || cz <= 0 || cx > h->nx || cy > h->ny || cz > h->nz)
         return fail(RT_E_INVAL, "rt_build_accel: coarsening factors must be in [1, n] per axis");
@@ -808,6 +908,8 @@ int rt_build_accel(rt_handle h, int cx, int cy, int cz)
     rt::build_majorant<<<grid_for(nc), 256, 0, h->stream>>>(h->rec, h->kmax, h->nx, h->ny, h->nz, cx, cy, cz,
                                                             NX, NY, NZ);
     RT_CUDA(cudaGetLastError());
+    if ((rc = ensure_boxes(h, nc, h->split_ok))) return rc;
+    RT_CUDA(build_boxes_of(h, h->stream));
     h->order_ok = false;
     if (h->opt.schedule == RT_SCHEDULE_THICK_FIRST) {
         if ((rc = ensure_order(h))) return rc;
@@ -826,6 +928,10 @@ int rt_build_accel(rt_handle h, int cx, int cy, int cz)
         rt::build_majorant_split<<<grid_for(nc), 256, 0, h->stream>>>(h->rec2, h->kmax2, h->nx, h->ny, h->nz, cx,
                                                                       cy, cz, NX, NY, NZ);
         RT_CUDA(cudaGetLastError());
+        RT_CUDA(rt::build_boxes2(h->kmax2, h->box2, h->bw[0], h->bw[1], h->bw[2], h->bw[3], NX, NY, NZ, cx * h->dx,
+                                 cy * h->dy, cz * h->dz, h->opt.box_levels,
+                                 h->opt.box_tau > 0 ? h->opt.box_tau : kDefaultBoxTau,
+                                 h->nx % cx == 0 && h->ny % cy == 0, h->stream));
         h->accel2_ok = true;
     }
     h->accel_ok = true;
@@ -989,8 +1095,8 @@ int rt_step_create(rt_handle h, const rt_step_desc *d, rt_step *out)
     };
     cudaError_t e = cudaSuccess;
     if (bps <= 0) {
-        e = s->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rt::trace_kernel<double, false>, block, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rt::trace_kernel<float, false>, block, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, s->fp64 ? single_kernel<double>(h) : single_kernel<float>(h),
+                                                          block, 0);
         bps = std::max(1, bps);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);

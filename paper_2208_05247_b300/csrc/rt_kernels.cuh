@@ -4,18 +4,28 @@
 //   derive_optics   per-cell record {k_abs, k_sca, k_sca*P(cloud|scatter), g}
 //                   from the five gas/cloud fields, with validation
 //   build_majorant  coarse-grid maximum of k_ext (the null-collision coefficient)
+//   box_*           majorant boxes: per coarse cell a cube of low optical depth
+//                   that one walk step may cross
 //   trace_kernel    persistent photon transport with warp-level refill:
-//                   null-collision tracking over the coarse grid, weights,
+//                   null-collision tracking over the majorant boxes, weights,
 //                   roulette, Lambertian surface, FP32 partial -> FP64 tallies
 //   fields kernels  FP64 normalisation of the tallies into output fields
+//
+// Everything here has internal linkage: the files that include this header
+// each compile their own copy of the kernels they launch.
 #pragma once
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <utility>
+
 #include <cuda_runtime.h>
 
 #include "rt_device.cuh"
 
 namespace rt {
+namespace {   // internal linkage: each .cu file that includes this header has its own copy
 
 constexpr int kStatusBudget = 1;
 constexpr int kStatusInput = 2;                        // an rt_step launch found invalid inputs
@@ -41,22 +51,34 @@ struct Tallies {
 constexpr int kMaxBatchScenes = 16;
 constexpr int kMaxBatchJobs = 512;
 
+// How a launch reads the optics of a cell at an event.
+enum : int {
+    kOpticsRecord = 0,   // single scene: derived record {k_abs, k_sca, k_sca*P(cloud), g}
+    kOpticsSplit = 1,    // batched: {k_abs,gas, k_sca,gas, k_abs,cloud, k_sca,cloud} and cloud g,
+                         // gas scaled per quadrature point
+    kOpticsFields = 2    // the five input fields themselves (no derived record in memory)
+};
+
 // One scene as the transport kernel sees it.
 template <typename T>
 struct SceneDev {
-    const float4 *rec;     // single-scene launches: {k_abs, k_sca, k_sca*P(cloud), g} per cell;
-                           // batched launches: {k_abs,gas, k_sca,gas, k_abs,cloud, k_sca,cloud}
-    const float *gcl;      // batched launches: cloud asymmetry per cell
-    const float *kmax;     // single-scene: max k_ext per coarse cell
-    const float2 *kmax2;   // batched: {max gas k_ext, max cloud k_ext} per coarse cell
+    const float4 *rec;     // kOpticsRecord / kOpticsSplit record per cell
+    const float *gcl;      // kOpticsSplit and kOpticsFields: cloud asymmetry per cell
+    const float *f_kg, *f_wg, *f_kc, *f_wc;   // kOpticsFields: gas/cloud extinction and albedo
+    const uint32_t *box;   // majorant box word per coarse cell (single scene)
+    const uint2 *box2;     // batched: {gas, cloud} majorant box words per coarse cell
     const float *alb;      // [ny][nx]
     Tallies<T> tal;
     Scratch *scr;
     int nx, ny, nz, NX, NY, NZ, cx, cy, cz, pcld_mode;
     float dx, dy, dz, inv_dx, inv_dy, inv_dz, Lx, Ly, H;
     float cdx, cdy, cdz;   // coarse cell size [m] (the last cell may be smaller)
+    float inv_cdx, inv_cdy, inv_cdz;
     int birth;             // start positions: 0 Philox uniforms, 1 scrambled Sobol
-    int pad_[3];
+    // face caps: with a shorter last coarse cell along x (or y) the face at NX
+    // is the domain edge (xcap = Lx, fxcap = nx); otherwise +inf / INT_MAX
+    float xcap, ycap;
+    int fxcap, fycap;
 };
 
 // One traced job: a scene, a sun position, an energy per photon and a range of
@@ -90,7 +112,8 @@ struct TraceArgs {
     uint32_t max_steps;
     uint32_t chunk;
     int ready_threshold;           // lanes that must be ready before an interaction sweep
-    int max_inner;                 // bound on face-crossing sweeps per interaction sweep
+    int max_inner;                 // bound on walk sweeps per interaction sweep
+    int refill_min;                // dead lanes a warp gathers before it refills
     // single-scene launches of whole photon rounds: queue index q takes photon
     // (order_k0 + q mod order_ppc) * ncol + order[q div order_ppc], i.e. all
     // photons of one column in turn, columns in the order of `order`
@@ -98,6 +121,29 @@ struct TraceArgs {
     uint32_t order_ppc;
     unsigned long long order_k0;
 };
+
+// ---------------------------------------------------------------------------
+// a1 for one cell, shared by the derivation kernel and the launches that read
+// the five input fields directly: explicit roundings (no contraction into
+// fused multiply-adds), so both give the same bits.
+// ---------------------------------------------------------------------------
+struct CellOptics {
+    float kabs, ksca, kscl;   // absorption, scattering, scattering by cloud
+};
+
+__device__ __forceinline__ CellOptics cell_optics(float kg, float wg, float kc, float wc, int pcld_mode)
+{
+    const float ksg = __fmul_rn(kg, wg), ksc = __fmul_rn(kc, wc);
+    CellOptics o;
+    o.ksca = __fadd_rn(ksg, ksc);
+    o.kabs = __fadd_rn(__fmul_rn(kg, __fsub_rn(1.0f, wg)), __fmul_rn(kc, __fsub_rn(1.0f, wc)));
+    o.kscl = ksc;
+    if (pcld_mode == 1) {
+        const float ke = __fadd_rn(kg, kc);
+        o.kscl = ke > 0.0f ? __fmul_rn(o.ksca, __fdiv_rn(kc, ke)) : 0.0f;
+    }
+    return o;
+}
 
 // ---------------------------------------------------------------------------
 // a1: optics record. k_abs = k_g (1 - w_g) + k_c (1 - w_c); k_sca = k_g w_g + k_c w_c;
@@ -117,12 +163,8 @@ __global__ void derive_optics(const float *__restrict__ kg, const float *__restr
                         (b >= 0.0f) && (b <= 1.0f) && (d >= 0.0f) && (d <= 1.0f) &&
                         (fabsf(g) < 1.0f);
         if (!ok) atomicOr(bad, 1);
-        const float ksg = a * b, ksc = c * d;
-        const float ksca = ksg + ksc;
-        const float kabs = fmaf(a, 1.0f - b, c * (1.0f - d));
-        float zc = ksc;
-        if (pcld_mode == 1) zc = (a + c > 0.0f) ? ksca * (c / (a + c)) : 0.0f;
-        rec[i] = make_float4(kabs, ksca, zc, g);
+        const CellOptics o = cell_optics(a, b, c, d, pcld_mode);
+        rec[i] = make_float4(o.kabs, o.ksca, o.kscl, g);
     }
 }
 
@@ -296,19 +338,119 @@ __global__ void build_majorant_split(const float4 *__restrict__ rec2, float2 *__
 }
 
 // ---------------------------------------------------------------------------
-// Tally accumulation: FP32 partial times the per-call energy, added into the
-// FP64 (or, for the precision study, FP32) global accumulator.
+// Majorant boxes (a2, a4). A walk that crosses one coarse cell per step spends
+// most of its steps in clear air, where tens of crossings add up to an optical
+// depth of a few hundredths. Every coarse cell therefore also carries a box:
+// the cube of coarse cells within Chebyshev radius r of it (periodic in x and
+// y, clipped at the surface and the domain top) and the largest extinction in
+// that cube. A photon in the cell crosses the whole cube in one step with the
+// cube's maximum as its majorant. The bound is >= the extinction everywhere on
+// the step, and it may be chosen anew at every step from the photon's current
+// position (thinning with a piecewise-constant dominating rate, Sec. 2.3's
+// null collisions), so the estimator is unchanged in expectation. r is the
+// largest of 0, 1, 3, 7, 15 for which the cube's maximum times the cube's
+// diagonal stays below box_tau: a step through a box adds at most about
+// box_tau null collisions, while in clear air it replaces up to 2r + 1
+// crossings.
+//
+// Box word: the float bits of the cube maximum with the low four mantissa
+// bits replaced by r. Read back with those bits set to one, the majorant is
+// >= the cube maximum (at most 15 units in the last place above it).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void tally_add(double *p, float v, double scale)
+constexpr int kBoxLevels = 4;                    // radii 1, 3, 7, 15 (dilation by 1, 2, 4, 8)
+constexpr int kDefaultCoarse = 2;                // coarsening factor per axis selected by 0,0,0
+// launch defaults shared by rt_create's options and rt_trace_noalloc
+constexpr uint32_t kDefaultMaxSteps = 10000000u;
+constexpr int kDefaultReadyThreshold = 16;
+constexpr int kDefaultMaxInner = 16;
+constexpr int kDefaultRefillMin = 8;
+constexpr int kDefaultBoxLevels = 4;
+constexpr float kDefaultBoxTau = 0.5f;
+
+__device__ __forceinline__ uint32_t box_word(float k, int r) { return (__float_as_uint(k) & ~0xFu) | (uint32_t)r; }
+__device__ __forceinline__ float box_kmaj(uint32_t w) { return __uint_as_float(w | 0xFu); }
+__device__ __forceinline__ int box_radius(uint32_t w) { return (int)(w & 0xFu); }
+
+// radius 0: every box is its own coarse cell
+__global__ void box_init(const float *__restrict__ kmax, float *__restrict__ cur, uint32_t *__restrict__ box, int n)
 {
-    // the partial is FP32 already; scaling it in FP32 keeps the thin FP64 pipe
-    // to the one conversion the FP64 accumulator needs
-    atomicAdd(p, (double)(v * (float)scale));
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const float k = kmax[q];
+        cur[q] = k;
+        box[q] = box_word(k, 0);
+    }
 }
-__device__ __forceinline__ void tally_add(float *p, float v, double scale)
+
+__global__ void box_init2(const float2 *__restrict__ kmax2, float *__restrict__ curg, float *__restrict__ curc,
+                          uint2 *__restrict__ box2, int n)
 {
-    atomicAdd(p, v * (float)scale);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const float2 m = kmax2[q];
+        curg[q] = m.x;
+        curc[q] = m.y;
+        box2[q] = make_uint2(box_word(m.x, 0), __float_as_uint(m.y) | 0xFu);
+    }
 }
+
+// One axis of a running-maximum filter of radius rho over the coarse grid:
+// axis 0 (x) and 1 (y) periodic, axis 2 (z) clipped. Callers keep rho < NX, NY.
+__global__ void box_dilate(const float *__restrict__ in, float *__restrict__ out, int NX, int NY, int NZ, int axis,
+                           int rho)
+{
+    const int n = NX * NY * NZ;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const int I = q % NX, J = (q / NX) % NY, K = q / (NX * NY);
+        float m = in[q];
+        if (axis == 0) {
+            const int row = q - I;
+            for (int d = 1; d <= rho; ++d) {
+                const int a = I + d >= NX ? I + d - NX : I + d, b = I - d < 0 ? I - d + NX : I - d;
+                m = fmaxf(m, fmaxf(in[row + a], in[row + b]));
+            }
+        } else if (axis == 1) {
+            const int base = q - J * NX;
+            for (int d = 1; d <= rho; ++d) {
+                const int a = J + d >= NY ? J + d - NY : J + d, b = J - d < 0 ? J - d + NY : J - d;
+                m = fmaxf(m, fmaxf(in[base + a * NX], in[base + b * NX]));
+            }
+        } else {
+            const int base = q - K * NX * NY;
+            for (int k = max(K - rho, 0); k <= min(K + rho, NZ - 1); ++k) m = fmaxf(m, in[base + k * NX * NY]);
+        }
+        out[q] = m;
+    }
+}
+
+// Cells whose box still has radius r_prev take radius r_new where the dilated
+// maximum m is at most `limit` = box_tau / ((2 r_new + 1) * cell diagonal).
+__global__ void box_select(const float *__restrict__ m, uint32_t *__restrict__ box, int n, int r_prev, int r_new,
+                           float limit)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const uint32_t w = box[q];
+        if (box_radius(w) == r_prev && m[q] <= limit) box[q] = box_word(m[q], r_new);
+    }
+}
+
+// Batched launches: the radius follows from gas (at scale 1) plus cloud; the
+// gas and cloud maxima of the box are kept apart for the per-job gas scale.
+__global__ void box_select2(const float *__restrict__ mg, const float *__restrict__ mc, uint2 *__restrict__ box2,
+                            int n, int r_prev, int r_new, float limit)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const uint2 w = box2[q];
+        if (box_radius(w.x) == r_prev && mg[q] + mc[q] <= limit)
+            box2[q] = make_uint2(box_word(mg[q], r_new), __float_as_uint(mc[q]) | 0xFu);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tally accumulation (a5, a9, a10): an FP32 partial of photon weight, times
+// the job's energy per unit weight in FP64, added to the FP64 (or, for the
+// precision study, FP32) global accumulator.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tally_add(double *p, float v, double scale) { atomicAdd(p, (double)v * scale); }
+__device__ __forceinline__ void tally_add(float *p, float v, double scale) { atomicAdd(p, (float)((double)v * scale)); }
 
 __device__ __forceinline__ unsigned long long warp_sum_u32(uint32_t v)
 {
@@ -322,42 +464,104 @@ __device__ __forceinline__ double warp_sum_f64(double v)
     return v;
 }
 
+// Flush of the absorption partials of the lanes with `fl` set (every lane of
+// the warp calls it). With `aggregate`, lanes that flush the same (cell,
+// direct/diffuse) are grouped (__match_any_sync); the group's lowest lane adds
+// the members' partials in lane order and issues the one atomic. Otherwise
+// every flushing lane issues its own. Grouping depends on which photons share
+// a warp, so aggregated sums are reproducible across launch shapes only to
+// FP32 rounding; unaggregated ones to the order of FP64 additions.
+template <typename T, bool AGG>
+__device__ __forceinline__ void flush_partials(bool fl, T *t_dir, T *t_dif, int cell, bool dir, float acc,
+                                               double scale)
+{
+    if constexpr (!AGG) {
+        if (fl) tally_add((dir ? t_dir : t_dif) + cell, acc, scale);
+        return;
+    }
+    const unsigned flm = __ballot_sync(0xffffffffu, fl);
+    if (!flm) return;
+    const unsigned lane = threadIdx.x & 31u;
+    const uint32_t key = fl ? ((uint32_t)cell << 1 | (uint32_t)dir) : 0xFFFFFFFFu;
+    const unsigned grp = __match_any_sync(0xffffffffu, key) & flm;
+    const int leader = grp ? __ffs(grp) - 1 : (int)lane;
+    unsigned rest = grp & ~(1u << leader);
+    float sum = acc;
+    while (__any_sync(0xffffffffu, rest != 0u)) {
+        const int src = rest ? __ffs(rest) - 1 : (int)lane;
+        const float v = __shfl_sync(0xffffffffu, acc, src);
+        if (rest) sum += v;
+        rest &= rest - 1u;
+    }
+    if (fl && (int)lane == leader) tally_add((dir ? t_dir : t_dif) + cell, sum, scale);
+}
+
+// ---------------------------------------------------------------------------
+// Geometry of the periodic coarse grid. Boxes of radius r > 0 exist only when
+// the coarse cells along x and y all have one size (box_grid_uniform), so a
+// coarse face e along x, for any integer e, lies at e * cdx, and the fine cell
+// beyond it has index e * cx (both in the periodic extension of the domain).
+// With a shorter last coarse cell the radius is 0 everywhere, faces are those
+// of the cell itself (e in [0, NX]) and the face at NX is the domain edge:
+// min(e * cdx, xcap) with xcap = Lx (fine index min(e * cx, fxcap), fxcap =
+// nx), the caps being +inf and INT_MAX otherwise. z is not periodic: a face
+// at min(e * cdz, H).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float wrap_coord(float p, float L) { return p < 0.f ? p + L : (p >= L ? p - L : p); }
+
 // ---------------------------------------------------------------------------
 // a3-a11: persistent transport kernel.
 //
 // Every warp loops until the photon queue is empty. One iteration has three
 // phases, each warp-synchronous:
 //
-//  1. refill: lanes whose photon ended take new photon ids (one atomicAdd per
-//     warp for a chunk of ids, handed out by ballot rank) and are born at the
-//     domain top along the sun beam;
-//  2. advance: lanes without a pending interaction cross faces of their coarse
-//     cell (subtracting k_max * l from the remaining optical depth) until the
-//     free path ends inside a cell (an event), the photon reaches the surface
-//     or leaves the top. The sweep repeats until `ready_threshold` lanes are
-//     ready (or none is left to advance, or `max_inner` sweeps), so the costly
-//     interaction code below runs with most lanes active;
-//  3. interact: ready lanes handle their event, surface hit or exit.
+//  1. refill: once at least refill_min lanes hold no photon (births run with
+//     only those lanes active), they flush the ended photons' absorption
+//     partials and take new photon ids (one atomicAdd per warp for a chunk of
+//     ids, handed out by ballot rank); a new photon is born at the domain top
+//     along the sun beam;
+//  2. walk: lanes without a pending interaction take box steps (subtracting
+//     k_box * l from the remaining optical depth) until the free path ends
+//     inside a box (an event), the photon reaches the surface or leaves the
+//     top. Sweeps repeat until `ready_threshold` lanes are ready (or none is
+//     left to walk, or `max_inner` sweeps), so the costly interaction code
+//     runs with most lanes active;
+//  3. interact: ready lanes handle their event, surface hit or exit; lanes
+//     whose absorption partial moved to another cell flush the old one.
 //
-// The walk over the coarse grid is parametric: along a straight segment from
-// origin o with direction u, tn[a] is the distance to the next face on axis a;
-// a crossing updates only the crossed axis. x and y wrap periodically (the
-// origin shifts by the domain length).
+// A walk step starts at the photon's position o in coarse cell (I,J,K) with
+// box radius r: the distance to the box face ahead along each axis, the
+// nearest of the three, and either the event inside the box or the move to
+// the neighbouring coarse cell across that face (x and y wrap periodically).
+// The crossed axis takes its index from the face. The others take the cell of
+// the position, but moved from the start cell only in the direction of travel
+// and within the box: a position on a face then stays in the cell the photon
+// moves into (the plain cell of the position can put it back behind a face it
+// crossed, and two axes can then undo each other's steps forever).
 //
 // Events (Sec. 2.3, weights after Iwabuchi 2006): at every majorant event the
-// cell absorbs w k_abs/k_max (heating tally) and w shrinks by the same amount;
-// the photon then scatters with probability k_sca/(k_max - k_abs), by cloud
+// cell absorbs w k_abs/k_maj (heating tally) and w shrinks by the same amount;
+// the photon then scatters with probability k_sca/(k_maj - k_abs), by cloud
 // (HG) or gas (Rayleigh), or has a null collision; below w = 0.5 roulette ends
 // it with probability 1 - w or resets w = 1. The surface adds w to the direct
 // or diffuse irradiance of its column, multiplies w by the albedo and reflects
 // Lambertian. Leaving the top adds w to the upward flux of its column.
+// Events and surface hits share one code path.
 //
 // Random numbers: block b of photon p is Philox(ctr = (p lo, p hi, b, slot)).
-// Birth uses block 0 (x, y, first free path); each event or surface hit uses
-// the next block (choice, mu, phi, next free path) and slot 1 of the same
-// block for roulette.
+// Birth uses block 0 (x, y, first free path, diffuse choice); each event or
+// surface hit uses the next block: (choice, mu, phi, next free path) at an
+// event, (roulette, mu, phi, next free path) at the surface. Roulette after a
+// null event uses the event's unused second word; after a scattering, word 0
+// of slot 1 of the same block.
+//
+// Counters: per photon (events, scatterings, box steps) into per-block shared
+// totals when the photon ends; per block into the launch scratch at the end.
 // ---------------------------------------------------------------------------
 enum : int { kNone = 0, kEvent = 1, kSurface = 2, kTop = 3, kCap = 4 };
+// per-scene block counters: surface hits, roulette kills, capped photons,
+// photons, events, scatterings, box steps, largest event count of a photon
+enum : int { kCntSurface = 0, kCntKills, kCntCapped, kCntPhotons, kCntEvents, kCntScatters, kCntSteps, kCntMax, kCnt };
 
 // Scene and job fields of the lane's photon: kernel parameters in single-scene
 // launches, shared memory in batched ones (folded at compile time).
@@ -366,33 +570,44 @@ enum : int { kNone = 0, kEvent = 1, kSurface = 2, kTop = 3, kCap = 4 };
 
 // Scrambled Sobol start point k of column col (Sec. 2.3): the column's two
 // scramble words come from Philox counter (col, 0, 0, 2) under the job's key.
-// Kept out of line: it runs once per photon, and inlining it into the refill
-// phase made the batched kernel spill.
+// Kept out of line: it runs once per photon.
 __device__ __noinline__ uint2 sobol_start(uint32_t k, uint32_t col, uint32_t k0, uint32_t k1)
 {
     const uint4 h = philox4x32_10(make_uint4(col, 0u, 0u, 2u), k0, k1);
     return make_uint2(sobol_dim1(k) ^ h.x, sobol_dim2(k) ^ h.y);
 }
 
-template <typename T, bool BATCH>
-__global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ TraceArgs<T> A)
+constexpr int kMaxWarpsPerBlock = 8;          // blocks of up to 256 threads
+
+// Five blocks of 256 threads per SM (register budget 48 per thread).
+// AGG (single-scene launches with rt_options.tally_aggregate) compiles the
+// grouped flush as a separate instantiation.
+template <typename T, int MODE, bool AGG = false>
+__global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ TraceArgs<T> A)
 {
+    constexpr bool BATCH = MODE == kOpticsSplit;
+    static_assert(!(AGG && BATCH), "batched launches flush per lane (jobs differ in energy)");
     constexpr unsigned kFull = 0xffffffffu;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned below = (1u << lane) - 1u;
+    const int wid = threadIdx.x >> 5;
 
     // batched launches: scene and job descriptors in dynamic shared memory
     extern __shared__ __align__(16) unsigned char s_dyn[];
     SceneDev<T> *s_scenes = reinterpret_cast<SceneDev<T> *>(s_dyn);
     JobDev *s_jobs = reinterpret_cast<JobDev *>(s_dyn + (BATCH ? A.nscenes : 0) * sizeof(SceneDev<T>));
-    // rare counters and the energy ledger per scene: surface hits, roulette
-    // kills, capped | created, destroyed, capped energy; batched launches also
-    // keep photons, events, scatters and crossings per scene here
     constexpr int NS = BATCH ? kMaxBatchScenes : 1;
-    __shared__ unsigned long long s_cnt[NS][7];
-    __shared__ double s_led[NS][3];
-    for (int q = threadIdx.x; q < NS * 7; q += blockDim.x) s_cnt[q / 7][q % 7] = 0;
+    __shared__ unsigned long long s_cnt[NS][kCnt];
+    __shared__ double s_led[NS][3];          // roulette created, destroyed, capped energy
+    // each warp's share of the photon queue: next and end index, queue empty
+    __shared__ unsigned long long s_pool[kMaxWarpsPerBlock][2];
+    __shared__ int s_exh[kMaxWarpsPerBlock];
+    for (int q = threadIdx.x; q < NS * kCnt; q += blockDim.x) s_cnt[q / kCnt][q % kCnt] = 0;
     for (int q = threadIdx.x; q < NS * 3; q += blockDim.x) s_led[q / 3][q % 3] = 0.0;
+    if (lane == 0) {
+        s_pool[wid][0] = s_pool[wid][1] = 0;
+        s_exh[wid] = 0;
+    }
     if (BATCH) {
         const int4 *src = reinterpret_cast<const int4 *>(A.scenes);
         int4 *dst = reinterpret_cast<int4 *>(s_scenes);
@@ -404,60 +619,77 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
     __syncthreads();
 
     int sid = 0, jid = 0;                     // scene and job of the lane's photon
-    float ox = 0.f, oy = 0.f, oz = 0.f;       // origin of the current straight segment
+    float ox = 0.f, oy = 0.f, oz = 0.f;       // photon position at the start of the walk step
     float ux = 0.f, uy = 0.f, uz = -1.f;      // direction
     float ivx = 0.f, ivy = 0.f, ivz = 0.f;    // 1/u per axis (used only on axes that move)
-    float tnx = 0.f, tny = 0.f, tnz = 0.f;    // distance from o to the next face per axis
-    float tcur = 0.f;                         // distance from o to the photon
-    float w = 0.f, tau = 0.f, kmaj = 0.f;
-    int I = 0, J = 0, K = 0;
+    float w = 0.f, kmaj = 0.f;                // weight, box majorant
+    float tau = 0.f;                          // optical depth left; once an event is found,
+                                              // its distance from o
+    int I = 0, J = 0, K = 0, r = 0;           // coarse cell and its box radius
     unsigned long long gid = 0;
-    uint32_t blk = 0, steps = 0, nev = 0, nsc = 0, ncr = 0;
+    uint32_t blk = 0, nev = 0, ncr = 0, nsc = 0;   // Philox block; events, box steps, scatterings
     bool alive = false, direct = false;
     int ready = kNone;
-    int pcell = -1;
+    int pcell = -1;                           // absorption partial: cell, direct flag, FP32 sum
     bool pdir = false;
     float pacc = 0.f;
 
-    uint32_t c_ph = 0, c_ev = 0, c_sc = 0, c_cr = 0, c_max = 0;
-
-    unsigned long long pool_next = 0, pool_end = 0;
-    bool exhausted = false;
-
-    auto load_kmaj = [&]() -> float {
-        const size_t q = ((size_t)K * RT_SC(NY) + J) * RT_SC(NX) + I;
+    auto load_box = [&]() {
+        const int q = (K * RT_SC(NY) + J) * RT_SC(NX) + I;
         if constexpr (BATCH) {
-            const float2 m = __ldg(RT_SC(kmax2) + q);
-            return fmaf(RT_JB(gas_scale), m.x, m.y);
+            const uint2 b = __ldg(RT_SC(box2) + q);
+            r = box_radius(b.x);
+            kmaj = fmaf(RT_JB(gas_scale), box_kmaj(b.x), box_kmaj(b.y));
         } else {
-            return __ldg(RT_SC(kmax) + q);
+            const uint32_t b = __ldg(RT_SC(box) + q);
+            r = box_radius(b);
+            kmaj = box_kmaj(b);
         }
     };
-    auto flush = [&]() {
-        if (pcell >= 0)
-            tally_add((pdir ? RT_SC(tal.abs_dir) : RT_SC(tal.abs_dif)) + pcell, pacc, RT_JB(scale3));
-        pcell = -1;
+    // coarse cell of a position inside the periodic domain
+    auto locate = [&](float px, float py, float pz) {
+        I = min(max((int)(px * RT_SC(inv_cdx)), 0), RT_SC(NX) - 1);
+        J = min(max((int)(py * RT_SC(inv_cdy)), 0), RT_SC(NY) - 1);
+        K = min(max((int)(pz * RT_SC(inv_cdz)), 0), RT_SC(NZ) - 1);
     };
-
-    // distances to the next coarse faces from origin o along u, for cell (I,J,K).
-    // An axis along which the photon does not move gets an infinite distance and
-    // is never crossed, so its reciprocal is never used.
-    auto start_segment = [&]() {
-        tcur = 0.f;
-        ivx = __frcp_rn(ux); ivy = __frcp_rn(uy); ivz = __frcp_rn(uz);
-        tnx = ux > 0.f ? (fminf((float)(I + 1) * RT_SC(cdx), RT_SC(Lx)) - ox) * ivx
-            : ux < 0.f ? ((float)I * RT_SC(cdx) - ox) * ivx : INFINITY;
-        tny = uy > 0.f ? (fminf((float)(J + 1) * RT_SC(cdy), RT_SC(Ly)) - oy) * ivy
-            : uy < 0.f ? ((float)J * RT_SC(cdy) - oy) * ivy : INFINITY;
-        tnz = uz > 0.f ? (fminf((float)(K + 1) * RT_SC(cdz), RT_SC(H)) - oz) * ivz
-            : uz < 0.f ? ((float)K * RT_SC(cdz) - oz) * ivz : INFINITY;
-        tnx = fmaxf(tnx, 0.f); tny = fmaxf(tny, 0.f); tnz = fmaxf(tnz, 0.f);
+    auto set_recip = [&]() {
+        ivx = __fdividef(1.0f, ux);
+        ivy = __fdividef(1.0f, uy);
+        ivz = __fdividef(1.0f, uz);
+    };
+    auto flush = [&](bool fl, int cell, bool dir, float acc) {
+        flush_partials<T, AGG>(fl, RT_SC(tal.abs_dir), RT_SC(tal.abs_dif), cell, dir, acc, RT_JB(scale3));
+    };
+    auto end_photon = [&]() {
+        // the absorption partial stays with the lane until its next refill
+        alive = false;
+        atomicAdd(&s_cnt[sid][kCntPhotons], 1ull);
+        atomicAdd(&s_cnt[sid][kCntEvents], (unsigned long long)nev);
+        atomicAdd(&s_cnt[sid][kCntScatters], (unsigned long long)nsc);
+        atomicAdd(&s_cnt[sid][kCntSteps], (unsigned long long)ncr);
+        atomicMax(&s_cnt[sid][kCntMax], (unsigned long long)nev);
+    };
+    auto roulette = [&](float xi) -> bool {   // true: the photon dies
+        if (xi > w) {
+            atomicAdd(&s_led[sid][1], (double)w * RT_JB(energy));
+            atomicAdd(&s_cnt[sid][kCntKills], 1ull);
+            return true;
+        }
+        atomicAdd(&s_led[sid][0], (double)(1.0f - w) * RT_JB(energy));
+        w = 1.f;
+        return false;
     };
 
     for (;;) {
         // ---------------- 1. refill ----------------
         const unsigned dead = __ballot_sync(kFull, !alive);
-        if (dead) {
+        if (dead && (dead == kFull ||
+                     ((!s_exh[wid] || s_pool[wid][0] < s_pool[wid][1]) && __popc(dead) >= A.refill_min))) {
+            // the ended photons' absorption partials, before the lanes take new ones
+            flush(!alive && pcell >= 0, pcell, pdir, pacc);
+            if (!alive) pcell = -1;
+            unsigned long long pool_next = s_pool[wid][0], pool_end = s_pool[wid][1];
+            bool exhausted = s_exh[wid] != 0;
             const unsigned ndead = __popc(dead);
             const unsigned rank = __popc(dead & below);
             const unsigned long long avail = pool_end - pool_next;
@@ -484,6 +716,13 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
                     }
                 }
             }
+            __syncwarp();
+            if (lane == 0) {
+                s_pool[wid][0] = pool_next;
+                s_pool[wid][1] = pool_end;
+                s_exh[wid] = exhausted;
+            }
+            __syncwarp();
             if (mine != ~0ull) {
                 // ---- a11: which job (batched launches: binary search of job starts) ----
                 if constexpr (BATCH) {
@@ -506,9 +745,9 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
                 const unsigned long long ncol = RT_JB(ncol);
                 const unsigned col = (gid >> 32) ? (unsigned)(gid % ncol) : (uint32_t)gid % (uint32_t)ncol;
                 const int ci = (int)(col % (unsigned)RT_SC(nx)), cj = (int)(col / (unsigned)RT_SC(nx));
-                const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), 0u, 0u),
-                                              RT_JB(key0), RT_JB(key1));
-                uint32_t bx = r.x, by = r.y;
+                const uint4 rb = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), 0u, 0u),
+                                               RT_JB(key0), RT_JB(key1));
+                uint32_t bx = rb.x, by = rb.y;
                 if (RT_SC(birth)) {
                     // photon k = gid / ncol of its column takes the column's k-th
                     // Sobol point, shifted by that column's scramble words
@@ -517,12 +756,14 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
                     bx = p.x;
                     by = p.y;
                 }
+                // position inside the column (the product can round up to the
+                // column's far edge; the cell index comes from the column)
                 ox = ((float)ci + u01(bx)) * RT_SC(dx);
                 oy = ((float)cj + u01(by)) * RT_SC(dy);
                 oz = RT_SC(H);
                 ux = RT_JB(sx); uy = RT_JB(sy); uz = RT_JB(sz);
                 direct = true;
-                if (RT_JB(diffuse) > 0.f && u01(r.w) < RT_JB(diffuse)) {
+                if (RT_JB(diffuse) > 0.f && u01(rb.w) < RT_JB(diffuse)) {
                     // diffuse share of the top boundary: isotropic downwelling
                     // radiance, i.e. cosine-weighted downward directions (Sec. 2.3)
                     const uint4 d = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), 0u, 1u),
@@ -531,237 +772,258 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
                     uz = -uz;
                     direct = false;
                 }
-                tau = -__logf(u01(r.z));
+                set_recip();
+                tau = -__logf(u01(rb.z));
                 w = 1.f;
                 alive = true;
                 ready = kNone;
-                I = ci / RT_SC(cx); J = cj / RT_SC(cy); K = RT_SC(NZ) - 1;
-                kmaj = load_kmaj();
-                start_segment();
-                blk = 1; steps = 0; nev = 0; nsc = 0; ncr = 0;
-                ++c_ph;
+                I = min(ci / RT_SC(cx), RT_SC(NX) - 1);
+                J = min(cj / RT_SC(cy), RT_SC(NY) - 1);
+                K = RT_SC(NZ) - 1;
+                load_box();
+                blk = 1; nev = 0; ncr = 0; nsc = 0;
             }
             if (!__any_sync(kFull, alive)) break;
         }
 
-        // ---------------- 2. advance (a4) ----------------
+        // ---------------- 2. walk (a4) ----------------
         for (int it = 0; it < A.max_inner; ++it) {
             const bool pend = alive && ready == kNone;
             const unsigned pm = __ballot_sync(kFull, pend);
             if (!pm) break;
             if (it > 0 && __popc(__ballot_sync(kFull, ready != kNone)) >= A.ready_threshold) break;
             if (!pend) continue;
-            if (++steps > A.max_steps) { ready = kCap; continue; }
+            if (ncr + nev >= A.max_steps) { ready = kCap; continue; }
+            const int NX = RT_SC(NX), NY = RT_SC(NY), NZ = RT_SC(NZ);
+            const int ex = ux > 0.f ? I + r + 1 : I - r;
+            const int ey = uy > 0.f ? J + r + 1 : J - r;
+            const int ez = uz > 0.f ? min(K + r + 1, NZ) : max(K - r, 0);
+            const float tx = ux != 0.f ? (fminf((float)ex * RT_SC(cdx), RT_SC(xcap)) - ox) * ivx : INFINITY;
+            const float ty = uy != 0.f ? (fminf((float)ey * RT_SC(cdy), RT_SC(ycap)) - oy) * ivy : INFINITY;
+            const float tz = uz != 0.f ? (fminf((float)ez * RT_SC(cdz), RT_SC(H)) - oz) * ivz : INFINITY;
             float tm;
             int ax;
-            if (tnx <= tny && tnx <= tnz) { tm = tnx; ax = 0; }
-            else if (tny <= tnz) { tm = tny; ax = 1; }
-            else { tm = tnz; ax = 2; }
-            const float dt = fmaxf(tm - tcur, 0.f);
-            if (kmaj * dt > tau) {
-                tcur += __fdividef(tau, kmaj);     // the free path ends in this coarse cell
+            if (tz <= tx && tz <= ty) { tm = tz; ax = 2; }
+            else if (tx <= ty) { tm = tx; ax = 0; }
+            else { tm = ty; ax = 1; }
+            tm = fmaxf(tm, 0.f);
+            if (kmaj * tm > tau) {
+                tau = __fdividef(tau, kmaj);      // the free path ends inside this box, tau from o
                 ready = kEvent;
                 continue;
             }
-            tau = fmaf(-kmaj, dt, tau);
-            tcur = tm;
-            ++c_cr;
-            if (BATCH) ++ncr;
+            tau = fmaf(-kmaj, tm, tau);
+            ++ncr;
+            float px = fmaf(ux, tm, ox), py = fmaf(uy, tm, oy), pz = fmaf(uz, tm, oz);
+            if (ax == 2) {
+                if (uz < 0.f) {
+                    if (ez == 0) { ready = kSurface; ox = px; oy = py; oz = 0.f; continue; }
+                    K = ez - 1;
+                } else {
+                    if (ez == NZ) { ready = kTop; ox = px; oy = py; oz = RT_SC(H); continue; }
+                    K = ez;
+                }
+                pz = (float)ez * RT_SC(cdz);
+            } else if (r > 0) {
+                K = min(max((int)(pz * RT_SC(inv_cdz)), uz < 0.f ? max(K - r, 0) : K),
+                        uz > 0.f ? min(K + r, NZ - 1) : K);
+            }
             if (ax == 0) {
                 if (ux > 0.f) {
-                    if (++I == RT_SC(NX)) { I = 0; ox -= RT_SC(Lx); }
-                    tnx = (fminf((float)(I + 1) * RT_SC(cdx), RT_SC(Lx)) - ox) * ivx;
+                    I = ex >= NX ? ex - NX : ex;
+                    px = (float)I * RT_SC(cdx);
                 } else {
-                    if (--I < 0) { I = RT_SC(NX) - 1; ox += RT_SC(Lx); }
-                    tnx = ((float)I * RT_SC(cdx) - ox) * ivx;
+                    I = ex - 1 < 0 ? ex - 1 + NX : ex - 1;
+                    px = I == NX - 1 ? RT_SC(Lx) : (float)(I + 1) * RT_SC(cdx);
                 }
-            } else if (ax == 1) {
-                if (uy > 0.f) {
-                    if (++J == RT_SC(NY)) { J = 0; oy -= RT_SC(Ly); }
-                    tny = (fminf((float)(J + 1) * RT_SC(cdy), RT_SC(Ly)) - oy) * ivy;
-                } else {
-                    if (--J < 0) { J = RT_SC(NY) - 1; oy += RT_SC(Ly); }
-                    tny = ((float)J * RT_SC(cdy) - oy) * ivy;
-                }
-            } else {
-                if (uz > 0.f) {
-                    if (++K == RT_SC(NZ)) { ready = kTop; continue; }
-                    tnz = (fminf((float)(K + 1) * RT_SC(cdz), RT_SC(H)) - oz) * ivz;
-                } else {
-                    if (--K < 0) { ready = kSurface; continue; }
-                    tnz = ((float)K * RT_SC(cdz) - oz) * ivz;
-                }
+            } else if (r > 0) {
+                int c = (int)floorf(px * RT_SC(inv_cdx));
+                c = ux > 0.f ? min(max(c, I), I + r) : (ux < 0.f ? min(max(c, I - r), I) : I);
+                if (c < 0) { c += NX; px += RT_SC(Lx); } else if (c >= NX) { c -= NX; px -= RT_SC(Lx); }
+                I = c;
             }
-            kmaj = load_kmaj();
+            if (ax == 1) {
+                if (uy > 0.f) {
+                    J = ey >= NY ? ey - NY : ey;
+                    py = (float)J * RT_SC(cdy);
+                } else {
+                    J = ey - 1 < 0 ? ey - 1 + NY : ey - 1;
+                    py = J == NY - 1 ? RT_SC(Ly) : (float)(J + 1) * RT_SC(cdy);
+                }
+            } else if (r > 0) {
+                int c = (int)floorf(py * RT_SC(inv_cdy));
+                c = uy > 0.f ? min(max(c, J), J + r) : (uy < 0.f ? min(max(c, J - r), J) : J);
+                if (c < 0) { c += NY; py += RT_SC(Ly); } else if (c >= NY) { c -= NY; py -= RT_SC(Ly); }
+                J = c;
+            }
+            ox = px; oy = py; oz = pz;
+            load_box();
         }
 
         // ---------------- 3. interact ----------------
-        if (ready == kNone) continue;
-        bool end_photon = false;
-        const int ilo = I * RT_SC(cx), ihi = min(ilo + RT_SC(cx), RT_SC(nx));
-        const int jlo = J * RT_SC(cy), jhi = min(jlo + RT_SC(cy), RT_SC(ny));
-        const float px = fmaf(ux, tcur, ox), py = fmaf(uy, tcur, oy);
-        const int fi = min(max((int)(px * RT_SC(inv_dx)), ilo), ihi - 1);
-        const int fj = min(max((int)(py * RT_SC(inv_dy)), jlo), jhi - 1);
-        if (ready == kEvent) {
-            // ---- a5: majorant event: absorb a fraction of the weight ----
-            ++steps;
-            const float pz = fmaf(uz, tcur, oz);
-            const int klo = K * RT_SC(cz), khi = min(klo + RT_SC(cz), RT_SC(nz));
-            const int fk = min(max((int)(pz * RT_SC(inv_dz)), klo), khi - 1);
-            const int cell = (fk * RT_SC(ny) + fj) * RT_SC(nx) + fi;
-            float kabs, ksca, kscl;   // absorption, scattering, scattering times P(cloud)
-            const float4 o = __ldg(RT_SC(rec) + cell);
-            if constexpr (BATCH) {
-                const float s = RT_JB(gas_scale);
-                kabs = fmaf(s, o.x, o.z);
-                ksca = fmaf(s, o.y, o.w);
-                if (RT_SC(pcld_mode) == 1) {
-                    const float kc = o.z + o.w, kext = fmaf(s, o.x + o.y, kc);
-                    kscl = kext > 0.f ? ksca * (kc / kext) : 0.f;
-                } else {
-                    kscl = o.w;
-                }
+        bool fl = false;                     // a partial to flush: the photon left its cell
+        int fcell = 0;
+        bool fdir = false;
+        float facc = 0.f;
+        if (ready == kEvent || ready == kSurface) {
+            // Events (a5-a8) and surface hits (a9) share one path: a position, a
+            // Philox block, possibly a new direction, the next free path, a new
+            // walk origin and roulette.
+            const bool sfc = ready == kSurface;
+            const int nx = RT_SC(nx), ny = RT_SC(ny);
+            float px, py, pz;
+            if (sfc) {
+                px = wrap_coord(ox, RT_SC(Lx)); py = wrap_coord(oy, RT_SC(Ly)); pz = 0.f;
             } else {
-                kabs = o.x; ksca = o.y; kscl = o.z;
+                px = wrap_coord(fmaf(ux, tau, ox), RT_SC(Lx));
+                py = wrap_coord(fmaf(uy, tau, oy), RT_SC(Ly));
+                pz = fmaf(uz, tau, oz);
             }
-            const float pabs = fminf(__fdividef(kabs, kmaj), 1.0f);
-            const float wn = w * (1.0f - pabs);
-            if (cell != pcell || direct != pdir) {
-                flush();
-                pcell = cell; pdir = direct; pacc = 0.f;
-            }
-            pacc += w - wn;
-            w = wn;
-            ++c_ev; ++nev;
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk, 0u),
-                                          RT_JB(key0), RT_JB(key1));
+            const int fi = min(max((int)(px * RT_SC(inv_dx)), 0), nx - 1);
+            const int fj = min(max((int)(py * RT_SC(inv_dy)), 0), ny - 1);
+            const uint4 rn = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk, 0u),
+                                           RT_JB(key0), RT_JB(key1));
             ++blk;
-            // ---- a6/a7: real scattering or null collision ----
-            // scatter if xi < k_sca/(k_max - k_abs), by cloud if xi < k_sca,cloud/(k_max - k_abs)
-            ox = px; oy = py; oz = pz;
-            const float den = kmaj - kabs;
-            bool scattered = false;
-            if (den > 0.f) {
-                const float xd = u01(r.x) * den;
-                if (xd < ksca) {
-                    float mu;
+            bool turned = sfc, scattered = false;
+            float mu = 0.f;
+            if (!sfc) {
+                // ---- a5: majorant event at distance tau, inside the box ----
+                int cell = (min(max((int)(pz * RT_SC(inv_dz)), 0), RT_SC(nz) - 1) * ny + fj) * nx + fi;
+                float kabs, ksca, kscl;   // absorption, scattering, scattering by cloud
+                auto optics = [&]() {
+                    if constexpr (MODE == kOpticsRecord) {
+                        const float4 o = __ldg(RT_SC(rec) + cell);
+                        kabs = o.x; ksca = o.y; kscl = o.z;
+                    } else if constexpr (MODE == kOpticsSplit) {
+                        const float4 o = __ldg(RT_SC(rec) + cell);
+                        const float s = RT_JB(gas_scale);
+                        kabs = fmaf(s, o.x, o.z);
+                        ksca = fmaf(s, o.y, o.w);
+                        if (RT_SC(pcld_mode) == 1) {
+                            const float kc = o.z + o.w, kext = fmaf(s, o.x + o.y, kc);
+                            kscl = kext > 0.f ? ksca * (kc / kext) : 0.f;
+                        } else {
+                            kscl = o.w;
+                        }
+                    } else {
+                        const CellOptics c = cell_optics(__ldg(RT_SC(f_kg) + cell), __ldg(RT_SC(f_wg) + cell),
+                                                         __ldg(RT_SC(f_kc) + cell), __ldg(RT_SC(f_wc) + cell), 0);
+                        kabs = c.kabs; ksca = c.ksca; kscl = c.kscl;
+                    }
+                };
+                optics();
+                if (kabs + ksca > kmaj) {
+                    // The event point lies in the box up to rounding; when rounding
+                    // put it in a neighbouring cell whose extinction the box
+                    // majorant does not bound, take the nearest cell of the box.
+                    const int cx = RT_SC(cx), cy = RT_SC(cy), cz = RT_SC(cz);
+                    int gi = (int)floorf(fmaf(ux, tau, ox) * RT_SC(inv_dx));
+                    gi = min(max(gi, (I - r) * cx), min((I + r + 1) * cx, RT_SC(fxcap)) - 1);
+                    gi += gi < 0 ? nx : (gi >= nx ? -nx : 0);
+                    int gj = (int)floorf(fmaf(uy, tau, oy) * RT_SC(inv_dy));
+                    gj = min(max(gj, (J - r) * cy), min((J + r + 1) * cy, RT_SC(fycap)) - 1);
+                    gj += gj < 0 ? ny : (gj >= ny ? -ny : 0);
+                    const int gk = min(max((int)(pz * RT_SC(inv_dz)), max(K - r, 0) * cz),
+                                       min((K + r + 1) * cz, RT_SC(nz)) - 1);
+                    cell = (gk * ny + gj) * nx + gi;
+                    optics();
+                }
+                const float pabs = fminf(__fdividef(kabs, kmaj), 1.0f);
+                const float wn = w * (1.0f - pabs);
+                if (cell != pcell || direct != pdir) {
+                    fl = pcell >= 0;
+                    fcell = pcell; fdir = pdir; facc = pacc;
+                    pcell = cell; pdir = direct; pacc = 0.f;
+                }
+                pacc += w - wn;
+                w = wn;
+                ++nev;
+                // ---- a6/a7: real scattering or null collision ----
+                // scatter if xi < k_sca/(k_max - k_abs), by cloud if xi < k_sca,cloud/(k_max - k_abs)
+                const float den = kmaj - kabs;
+                const float xd = u01(rn.x) * den;
+                if (den > 0.f && xd < ksca) {
                     if (xd < kscl) {
                         float g;
-                        if constexpr (BATCH) g = __ldg(RT_SC(gcl) + cell);
-                        else g = o.w;
-                        mu = hg_mu(g, u01(r.y));
+                        if constexpr (MODE == kOpticsRecord) g = __ldg(RT_SC(rec) + cell).w;
+                        else g = __ldg(RT_SC(gcl) + cell);
+                        mu = hg_mu(g, u01(rn.y));
                     } else {
-                        mu = rayleigh_mu(u01(r.y));
+                        mu = rayleigh_mu(u01(rn.y));
                     }
-                    float sp, cp;
-                    azimuth(u01(r.z), sp, cp);
-                    turn(ux, uy, uz, mu, sp, cp);
+                    turned = scattered = true;
                     direct = false;
-                    scattered = true;
-                    ++c_sc;
-                    if (BATCH) ++nsc;
+                    ++nsc;
                 }
-            }
-            if (scattered) {
-                start_segment();
             } else {
-                tnx -= tcur; tny -= tcur; tnz -= tcur;
-                tcur = 0.f;
+                // ---- a9: Lambertian surface ----
+                const int col = fj * nx + fi;
+                tally_add((direct ? RT_SC(tal.sfc_dir) : RT_SC(tal.sfc_dif)) + col, w, RT_JB(scale2));
+                atomicAdd(&s_cnt[sid][kCntSurface], 1ull);
+                w *= __ldg(RT_SC(alb) + col);
+                direct = false;
             }
-            tau = -__logf(u01(r.w));
-            // ---- a8: roulette ----
-            if (w < 0.5f) {
-                const uint4 q = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk - 1u, 1u),
-                                              RT_JB(key0), RT_JB(key1));
-                if (u01(q.x) > w) {
-                    atomicAdd(&s_led[sid][1], (double)w * RT_JB(energy));
-                    atomicAdd(&s_cnt[sid][1], 1ull);
-                    end_photon = true;
+            if (turned) {
+                // new direction: polar cosine mu about the old direction (a7), or
+                // cosine-law about the surface normal, mu = sqrt(xi) (a9)
+                float sp, cp;
+                azimuth(u01(rn.z), sp, cp);
+                if (sfc) {
+                    const float xi = u01(rn.y), st = sqrtf(1.0f - xi);
+                    ux = st * cp; uy = st * sp; uz = sqrtf(xi);
                 } else {
-                    atomicAdd(&s_led[sid][0], (double)(1.0f - w) * RT_JB(energy));
-                    w = 1.f;
+                    turn(ux, uy, uz, mu, sp, cp);
                 }
+                set_recip();
             }
-        } else if (ready == kSurface) {
-            // ---- a9: Lambertian surface ----
-            ++steps;
-            const int col = fj * RT_SC(nx) + fi;
-            tally_add((direct ? RT_SC(tal.sfc_dir) : RT_SC(tal.sfc_dif)) + col, w, RT_JB(scale2));
-            atomicAdd(&s_cnt[sid][0], 1ull);
-            w *= __ldg(RT_SC(alb) + col);
-            direct = false;
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk, 0u),
-                                          RT_JB(key0), RT_JB(key1));
-            ++blk;
-            lambert_up(ux, uy, uz, u01(r.x), u01(r.y));
-            tau = -__logf(u01(r.w));
-            K = 0;
-            ox = px; oy = py; oz = 0.f;
-            start_segment();
+            tau = -__logf(u01(rn.w));
+            ox = px; oy = py; oz = pz;
+            locate(px, py, pz);
+            load_box();
+            // ---- a8: roulette (surface: word 0; null event: word 1, unused there;
+            //      after a scattering: word 0 of slot 1 of the same block) ----
             if (w < 0.5f) {
-                if (u01(r.z) > w) {
-                    atomicAdd(&s_led[sid][1], (double)w * RT_JB(energy));
-                    atomicAdd(&s_cnt[sid][1], 1ull);
-                    end_photon = true;
-                } else {
-                    atomicAdd(&s_led[sid][0], (double)(1.0f - w) * RT_JB(energy));
-                    w = 1.f;
-                }
+                float xi = u01(sfc ? rn.x : rn.y);
+                if (scattered)
+                    xi = u01(philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk - 1u, 1u),
+                                           RT_JB(key0), RT_JB(key1)).x);
+                if (roulette(xi)) end_photon();
             }
         } else if (ready == kTop) {
             // ---- a10: leaves through the domain top ----
-            tally_add(RT_SC(tal.toa) + (fj * RT_SC(nx) + fi), w, RT_JB(scale2));
-            end_photon = true;
-        } else {
+            const int nx = RT_SC(nx), ny = RT_SC(ny);
+            const float px = wrap_coord(ox, RT_SC(Lx)), py = wrap_coord(oy, RT_SC(Ly));
+            const int fi = min(max((int)(px * RT_SC(inv_dx)), 0), nx - 1);
+            const int fj = min(max((int)(py * RT_SC(inv_dy)), 0), ny - 1);
+            tally_add(RT_SC(tal.toa) + (fj * nx + fi), w, RT_JB(scale2));
+            end_photon();
+        } else if (ready == kCap) {
             // step cap: record, stop the photon, never spin
-            atomicAdd(&s_cnt[sid][2], 1ull);
+            atomicAdd(&s_cnt[sid][kCntCapped], 1ull);
             atomicAdd(&s_led[sid][2], (double)w * RT_JB(energy));
             atomicOr(&RT_SC(scr)->status, kStatusBudget);
-            end_photon = true;
+            end_photon();
         }
         ready = kNone;
-        if (end_photon) {
-            flush();
-            alive = false;
-            c_max = max(c_max, nev);
-            if (BATCH) {
-                atomicAdd(&s_cnt[sid][3], 1ull);
-                atomicAdd(&s_cnt[sid][4], (unsigned long long)nev);
-                atomicAdd(&s_cnt[sid][5], (unsigned long long)nsc);
-                atomicAdd(&s_cnt[sid][6], (unsigned long long)ncr);
-                atomicMax(&RT_SC(scr)->max_events, (unsigned long long)nev);
-            }
-        }
+        flush(fl, fcell, fdir, facc);
     }
+    // the last photons' absorption partials
+    flush(pcell >= 0, pcell, pdir, pacc);
 
-    // ---- counters: warp reduction, one atomic per warp; block totals once ----
-    if (!BATCH) {
-        const unsigned long long s_ph = warp_sum_u32(c_ph), s_ev = warp_sum_u32(c_ev),
-                                 s_sc = warp_sum_u32(c_sc), s_cr = warp_sum_u32(c_cr);
-        const unsigned m_ev = __reduce_max_sync(kFull, c_max);
-        Scratch *S = A.scene.scr;
-        if (lane == 0) {
-            if (s_ph) atomicAdd(&S->photons, s_ph);
-            if (s_ev) atomicAdd(&S->events, s_ev);
-            if (s_sc) atomicAdd(&S->scatters, s_sc);
-            if (s_cr) atomicAdd(&S->crossings, s_cr);
-            if (m_ev) atomicMax(&S->max_events, (unsigned long long)m_ev);
-        }
-    }
+    // ---- block totals into the launch scratch, once per block and scene ----
     __syncthreads();
     const int nsc_blk = BATCH ? A.nscenes : 1;
     for (int q = threadIdx.x; q < nsc_blk; q += blockDim.x) {
         Scratch *S = BATCH ? s_scenes[q].scr : A.scene.scr;
-        if (s_cnt[q][0]) atomicAdd(&S->surface_hits, s_cnt[q][0]);
-        if (s_cnt[q][1]) atomicAdd(&S->roulette_kills, s_cnt[q][1]);
-        if (s_cnt[q][2]) atomicAdd(&S->capped, s_cnt[q][2]);
-        if (BATCH) {
-            if (s_cnt[q][3]) atomicAdd(&S->photons, s_cnt[q][3]);
-            if (s_cnt[q][4]) atomicAdd(&S->events, s_cnt[q][4]);
-            if (s_cnt[q][5]) atomicAdd(&S->scatters, s_cnt[q][5]);
-            if (s_cnt[q][6]) atomicAdd(&S->crossings, s_cnt[q][6]);
-        }
+        const unsigned long long *c = s_cnt[q];
+        if (c[kCntSurface]) atomicAdd(&S->surface_hits, c[kCntSurface]);
+        if (c[kCntKills]) atomicAdd(&S->roulette_kills, c[kCntKills]);
+        if (c[kCntCapped]) atomicAdd(&S->capped, c[kCntCapped]);
+        if (c[kCntPhotons]) atomicAdd(&S->photons, c[kCntPhotons]);
+        if (c[kCntEvents]) atomicAdd(&S->events, c[kCntEvents]);
+        if (c[kCntScatters]) atomicAdd(&S->scatters, c[kCntScatters]);
+        if (c[kCntSteps]) atomicAdd(&S->crossings, c[kCntSteps]);
+        if (c[kCntMax]) atomicMax(&S->max_events, c[kCntMax]);
         if (s_led[q][0] != 0.0) atomicAdd(&S->created, s_led[q][0]);
         if (s_led[q][1] != 0.0) atomicAdd(&S->destroyed, s_led[q][1]);
         if (s_led[q][2] != 0.0) atomicAdd(&S->capped_energy, s_led[q][2]);
@@ -902,4 +1164,105 @@ __global__ void debug_turn(float dx, float dy, float dz, const float *mu, const 
     out[3 * i] = x; out[3 * i + 1] = y; out[3 * i + 2] = z;
 }
 
+
+// ---------------------------------------------------------------------------
+// Majorant grid straight from the five input fields, for launches that keep no
+// derived record: the per-cell values are formed by cell_optics as
+// derive_optics forms them, so the maxima equal build_majorant's. Invalid
+// optics or albedo (as derive_optics and check_albedo judge them) set *bad.
+// ---------------------------------------------------------------------------
+__global__ void majorant_from_fields(const float *__restrict__ kg, const float *__restrict__ wg,
+                                     const float *__restrict__ kc, const float *__restrict__ wc,
+                                     const float *__restrict__ gc, const float *__restrict__ alb,
+                                     float *__restrict__ kmax, int *bad, int nx, int ny, int nz, int cx, int cy,
+                                     int cz, int NX, int NY, int NZ)
+{
+    const int n = NX * NY * NZ;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const int I = q % NX, J = (q / NX) % NY, K = q / (NX * NY);
+        const int i1 = min(I * cx + cx, nx), j1 = min(J * cy + cy, ny), k1 = min(K * cz + cz, nz);
+        float m = 0.0f;
+        bool ok = true;
+        for (int k = K * cz; k < k1; ++k)
+            for (int j = J * cy; j < j1; ++j)
+                for (int i = I * cx; i < i1; ++i) {
+                    const size_t c = ((size_t)k * ny + j) * nx + i;
+                    const float a = kg[c], b = wg[c], cc = kc[c], d = wc[c], g = gc[c];
+                    ok = ok && (a >= 0.0f) && (a <= 3.0e38f) && (cc >= 0.0f) && (cc <= 3.0e38f) &&
+                         (b >= 0.0f) && (b <= 1.0f) && (d >= 0.0f) && (d <= 1.0f) && (fabsf(g) < 1.0f);
+                    const CellOptics o = cell_optics(a, b, cc, d, 0);
+                    m = fmaxf(m, o.kabs + o.ksca);
+                }
+        if (K == 0)
+            for (int j = J * cy; j < j1; ++j)
+                for (int i = I * cx; i < i1; ++i) {
+                    const float al = alb[(size_t)j * nx + i];
+                    ok = ok && (al >= 0.0f) && (al <= 1.0f);
+                }
+        if (!ok) atomicOr(bad, 1);
+        kmax[q] = m;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side of the majorant-box build: kmax -> box words, `levels` dilation
+// levels (radii 1, 3, 7, 15; a level is skipped once 2r + 1 exceeds the
+// smaller horizontal coarse count, so a box never wraps onto itself). Boxes
+// need coarse cells of one size along x and y (uniform_xy: the coarsening
+// factors divide nx and ny); otherwise every radius stays 0. w0 and w1 are
+// scratch arrays of NX*NY*NZ floats.
+// ---------------------------------------------------------------------------
+inline int box_grid(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 148 * 32)); }
+
+inline cudaError_t build_boxes(const float *kmax, uint32_t *box, float *w0, float *w1, int NX, int NY, int NZ,
+                               double cdx, double cdy, double cdz, int levels, double box_tau, bool uniform_xy,
+                               cudaStream_t st)
+{
+    const int n = NX * NY * NZ, g = box_grid((size_t)n);
+    if (!uniform_xy) levels = 0;
+    box_init<<<g, 256, 0, st>>>(kmax, w0, box, n);
+    const double diag = std::sqrt(cdx * cdx + cdy * cdy + cdz * cdz);
+    float *cur = w0, *tmp = w1;
+    int r_prev = 0;
+    for (int L = 0; L < std::min(levels, kBoxLevels); ++L) {
+        const int rho = 1 << L, r_new = r_prev + rho;
+        if (2 * r_new + 1 > std::min(NX, NY)) break;
+        box_dilate<<<g, 256, 0, st>>>(cur, tmp, NX, NY, NZ, 0, rho);
+        box_dilate<<<g, 256, 0, st>>>(tmp, cur, NX, NY, NZ, 1, rho);
+        box_dilate<<<g, 256, 0, st>>>(cur, tmp, NX, NY, NZ, 2, rho);
+        std::swap(cur, tmp);
+        box_select<<<g, 256, 0, st>>>(cur, box, n, r_prev, r_new, (float)(box_tau / ((2 * r_new + 1) * diag)));
+        r_prev = r_new;
+    }
+    return cudaGetLastError();
+}
+
+// Batched launches: gas and cloud channels dilated apart (w0..w3 scratch).
+inline cudaError_t build_boxes2(const float2 *kmax2, uint2 *box2, float *w0, float *w1, float *w2, float *w3, int NX,
+                                int NY, int NZ, double cdx, double cdy, double cdz, int levels, double box_tau,
+                                bool uniform_xy, cudaStream_t st)
+{
+    const int n = NX * NY * NZ, g = box_grid((size_t)n);
+    if (!uniform_xy) levels = 0;
+    box_init2<<<g, 256, 0, st>>>(kmax2, w0, w2, box2, n);
+    const double diag = std::sqrt(cdx * cdx + cdy * cdy + cdz * cdz);
+    float *cg = w0, *tg = w1, *cc = w2, *tc = w3;
+    int r_prev = 0;
+    for (int L = 0; L < std::min(levels, kBoxLevels); ++L) {
+        const int rho = 1 << L, r_new = r_prev + rho;
+        if (2 * r_new + 1 > std::min(NX, NY)) break;
+        for (int ch = 0; ch < 2; ++ch) {
+            float *&c = ch ? cc : cg, *&t = ch ? tc : tg;
+            box_dilate<<<g, 256, 0, st>>>(c, t, NX, NY, NZ, 0, rho);
+            box_dilate<<<g, 256, 0, st>>>(t, c, NX, NY, NZ, 1, rho);
+            box_dilate<<<g, 256, 0, st>>>(c, t, NX, NY, NZ, 2, rho);
+            std::swap(c, t);
+        }
+        box_select2<<<g, 256, 0, st>>>(cg, cc, box2, n, r_prev, r_new, (float)(box_tau / ((2 * r_new + 1) * diag)));
+        r_prev = r_new;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
 }  // namespace rt

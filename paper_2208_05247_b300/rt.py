@@ -38,7 +38,9 @@ class rt_options(ctypes.Structure):
                 ("refill_chunk", ctypes.c_int), ("max_steps", ctypes.c_uint32),
                 ("pcld_mode", ctypes.c_int), ("tally_precision", ctypes.c_int),
                 ("ready_threshold", ctypes.c_int), ("max_inner", ctypes.c_int),
-                ("batch_optics", ctypes.c_int), ("birth", ctypes.c_int), ("schedule", ctypes.c_int)]
+                ("batch_optics", ctypes.c_int), ("birth", ctypes.c_int), ("schedule", ctypes.c_int),
+                ("box_levels", ctypes.c_int), ("box_tau", ctypes.c_float), ("tally_aggregate", ctypes.c_int),
+                ("refill_min", ctypes.c_int)]
 
 
 class rt_job(ctypes.Structure):
@@ -188,10 +190,11 @@ def rt_set_stream(h, stream=None):
 def rt_set_options(h, **kw):
     o = rt_options()
     _check(library().rt_get_options(h, ctypes.byref(o)))
+    types = dict(rt_options._fields_)
     for k, v in kw.items():
-        if k not in dict(rt_options._fields_):
+        if k not in types:
             raise KeyError(k)
-        setattr(o, k, int(v))
+        setattr(o, k, float(v) if types[k] is ctypes.c_float else int(v))
     return _check(library().rt_set_options(h, ctypes.byref(o)))
 
 

@@ -76,8 +76,14 @@ def test_single_job_batch_matches_rt_trace_statistically(small_scene):
 
 @pytest.mark.parametrize("s", [1e-3, 0.37, 10.0])
 def test_gas_scale_equals_scaled_gas_fields(small_scene, s):
-    """A job with gas_scale s has the expectation of the scene with s * k_gas."""
-    B, N = 12, 2 ** 18
+    """A job with gas_scale s has the expectation of the scene with s * k_gas.
+
+    At s = 1e-3 the clear-air majorant is ~2e-8 m^-1 and each rare gas event
+    deposits a tenth of the photon's weight, so the GPU's absorption tallies
+    vary by 10-20 % between batches of 2^18 photons (the analog oracle's by
+    0.4 %); that case uses 24 batches of 2^20 photons so the batch standard
+    error is estimated reliably."""
+    B, N = (24, 2 ** 20) if s < 0.01 else (12, 2 ** 18)
     sc2 = scaled_gas(small_scene, s)
     tb = batch_tracer(small_scene)
     res_b = {f: [] for f in FIELDS}

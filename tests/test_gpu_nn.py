@@ -414,8 +414,12 @@ def test_pack_and_unpack_round_trip():
     x = torch.empty(D * H * W * 16, dtype=torch.bfloat16, device="cuda")
     nn.nn_pack_inputs(d64(abs3d), d64(sdir), d64(sdif), *[f32(o) for o in opt], x, D, H, W, dz, F)
     xs = host(x).reshape(D, H, W, 16)
-    assert np.allclose(xs[..., 0], nn_ref.bf16_round(100 * abs3d * dz / F), rtol=0, atol=0)
-    assert np.allclose(xs[..., 1], nn_ref.bf16_round(np.broadcast_to(sdir / F, (D, H, W))), rtol=0, atol=0)
+    # the kernel multiplies by the two FP64 factors the host forms once
+    # (100 dz / F and 1 / F); the same products here make exact equality hold
+    # by construction, not by the draw
+    s_abs, s_sfc = 100.0 * dz / F, 1.0 / F
+    assert np.allclose(xs[..., 0], nn_ref.bf16_round(abs3d * s_abs), rtol=0, atol=0)
+    assert np.allclose(xs[..., 1], nn_ref.bf16_round(np.broadcast_to(sdir * s_sfc, (D, H, W))), rtol=0, atol=0)
     assert np.all(xs[..., 6:] == 0)
     pred = rng.normal(size=(D, H, W, 16)).astype(np.float32) * 0.01
     o3, o1, o2 = (torch.empty(D * H * W, dtype=torch.float64, device="cuda"),

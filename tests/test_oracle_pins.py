@@ -175,6 +175,29 @@ def test_mc_no_atmosphere_normalisation():
     assert r.totals["sfc_abs"] == 30_000
 
 
+def test_heating_rate_conversion_literal_factors():
+    """The K/day conversion (reading c15 of the heating rates the paper quotes in
+    K/day, Sec. 3): HR = 86400 A / (rho(z_c) c_p) with c_p = 1004 J/(kg K) and
+    rho = 1.225 exp(-z_c / 8000 m) at the layer CENTRE. The factors below were
+    evaluated by hand (not by the oracle) for dz = 25 m at z_c = 12.5 m (layer
+    0) and z_c = 3187.5 m (layer 127), and for dz = 300 m at z_c = 150 m. A
+    density taken at layer bottoms (z = 0, 3175 m), a wrong c_p, a missing
+    86400, or a conversion broadcast along y or x instead of z fails here."""
+    nz, ny, nx = 128, 2, 3
+    a = np.zeros((nz, ny, nx))
+    a[0, 1, 2] = 2.0          # W m^-3 in layer 0
+    a[127, 0, 1] = 0.5        # W m^-3 in layer 127
+    hr = oracle.heating_rate(a, 25.0)
+    assert hr.shape == (nz, ny, nx)
+    assert np.isclose(hr[0, 1, 2], 2.0 * 70.3594646098895, rtol=1e-12)
+    assert np.isclose(hr[127, 0, 1], 0.5 * 104.63648654442953, rtol=1e-12)
+    assert np.count_nonzero(hr) == 2
+    # density profile itself: sea-level value 1.225 kg m^-3, scale height 8 km
+    rho = oracle.air_density(2, 300.0)
+    assert np.allclose(rho, [1.2022452424910, 1.1579959062988], rtol=1e-9)
+    assert np.isclose(oracle.heating_rate(np.ones((1, 1, 1)), 300.0)[0, 0, 0], 71.57922015488663, rtol=1e-12)
+
+
 def test_mc_conservative_black_surface_and_white_surface():
     """omega = 1 everywhere: nothing is absorbed in the atmosphere; with a white
     surface every photon leaves through the top (R = 1)."""
