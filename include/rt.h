@@ -106,7 +106,7 @@ typedef struct {
     int tally_precision;         /* RT_TALLY_*; applies from the next rt_reset_tallies */
     int ready_threshold;         /* lanes of a warp that must have an event, surface hit or exit
                                     pending before the warp handles them together; 0 = 16 */
-    int max_inner;               /* bound on face-crossing sweeps between two such passes; 0 = 16 */
+    int max_inner;               /* bound on walk sweeps between two such passes; 0 = 16 */
     int batch_optics;            /* 1: rt_set_optics also keeps gas and cloud apart and
                                     rt_build_accel builds the factored majorant, as
                                     rt_trace_batch needs (+20 B per cell); 0 (default): not */

@@ -45,6 +45,15 @@ __device__ __forceinline__ float u01(uint32_t x)
     return (static_cast<float>(x >> 8) + 0.5f) * 5.9604644775390625e-8f;
 }
 
+// A fifth uniform from one Philox block: the low 8 bits of words 0, 1 and 2,
+// which u01 discards. The bits of a uniformly random word are independent, so
+// this is independent of the four uniforms taken from the top bits.
+__device__ __forceinline__ float u01_low(uint4 r)
+{
+    const uint32_t v = (r.x & 0xFFu) | ((r.y & 0xFFu) << 8) | ((r.z & 0xFFu) << 16);
+    return (static_cast<float>(v) + 0.5f) * 5.9604644775390625e-8f;
+}
+
 // ---------------------------------------------------------------------------
 // Sobol start positions (Sec. 2.3: photons enter the domain top at the points
 // of a scrambled Sobol sequence). The first two Sobol dimensions in natural
@@ -81,14 +90,15 @@ __host__ __device__ __forceinline__ uint32_t sobol_dim2(uint32_t k)
 
 // Rayleigh p(mu) = 3/8 (1 + mu^2): the CDF (mu^3 + 3 mu + 4)/8 = xi is the
 // depressed cubic mu^3 + 3 mu = 2a with a = 4 xi - 2, whose single real root is
-// c - 1/c with c = cbrt(a + sqrt(a^2 + 1)). The root is odd in a, so it is
-// evaluated for |a| to avoid cancellation.
+// c - 1/c with c = (a + sqrt(a^2 + 1))^(1/3). The root is odd in a, so it is
+// evaluated for |a| to avoid cancellation. The base lies in [1, 2 + sqrt 5],
+// where the fast power __powf is accurate to a few units in the last place.
 __device__ __forceinline__ float rayleigh_mu(float xi)
 {
     const float a = 4.0f * xi - 2.0f;
     const float t = fabsf(a);
-    const float c = cbrtf(t + sqrtf(fmaf(t, t, 1.0f)));
-    return copysignf(c - __frcp_rn(c), a);
+    const float c = __powf(t + sqrtf(fmaf(t, t, 1.0f)), 0.333333343f);
+    return copysignf(c - __fdividef(1.0f, c), a);
 }
 
 // Henyey-Greenstein: with s = 2 xi - 1 the inverse CDF

@@ -549,11 +549,11 @@ __device__ __forceinline__ float wrap_coord(float p, float L) { return p < 0.f ?
 // Events and surface hits share one code path.
 //
 // Random numbers: block b of photon p is Philox(ctr = (p lo, p hi, b, slot)).
-// Birth uses block 0 (x, y, first free path, diffuse choice); each event or
-// surface hit uses the next block: (choice, mu, phi, next free path) at an
-// event, (roulette, mu, phi, next free path) at the surface. Roulette after a
-// null event uses the event's unused second word; after a scattering, word 0
-// of slot 1 of the same block.
+// A uniform takes the top 24 bits of a word; the low 8 bits of words 0, 1 and
+// 2 form a fifth, independent uniform (u01_low). Birth uses block 0 (x, y,
+// first free path, diffuse choice); each event or surface hit uses the next
+// block: (choice, mu, phi, next free path) at an event, (-, mu, phi, next free
+// path) at the surface, and the fifth uniform for roulette.
 //
 // Counters: per photon (events, scatterings, box steps) into per-block shared
 // totals when the photon ends; per block into the launch scratch at the end.
@@ -600,12 +600,12 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
     __shared__ unsigned long long s_cnt[NS][kCnt];
     __shared__ double s_led[NS][3];          // roulette created, destroyed, capped energy
     // each warp's share of the photon queue: next and end index, queue empty
-    __shared__ unsigned long long s_pool[kMaxWarpsPerBlock][2];
+    __shared__ unsigned long long s_q[kMaxWarpsPerBlock][2];
     __shared__ int s_exh[kMaxWarpsPerBlock];
     for (int q = threadIdx.x; q < NS * kCnt; q += blockDim.x) s_cnt[q / kCnt][q % kCnt] = 0;
     for (int q = threadIdx.x; q < NS * 3; q += blockDim.x) s_led[q / 3][q % 3] = 0.0;
     if (lane == 0) {
-        s_pool[wid][0] = s_pool[wid][1] = 0;
+        s_q[wid][0] = s_q[wid][1] = 0;
         s_exh[wid] = 0;
     }
     if (BATCH) {
@@ -661,7 +661,7 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
         flush_partials<T, AGG>(fl, RT_SC(tal.abs_dir), RT_SC(tal.abs_dif), cell, dir, acc, RT_JB(scale3));
     };
     auto end_photon = [&]() {
-        // the absorption partial stays with the lane until its next refill
+        // the lane flushes the photon's absorption partial at the end of the pass
         alive = false;
         atomicAdd(&s_cnt[sid][kCntPhotons], 1ull);
         atomicAdd(&s_cnt[sid][kCntEvents], (unsigned long long)nev);
@@ -681,14 +681,13 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
     };
 
     for (;;) {
-        // ---------------- 1. refill ----------------
+        // ---------------- 1. refill (a3, a11) ----------------
+        // Births run with only the empty lanes active, so they wait until at
+        // least refill_min lanes are empty (or all are, or the queue is empty).
         const unsigned dead = __ballot_sync(kFull, !alive);
         if (dead && (dead == kFull ||
-                     ((!s_exh[wid] || s_pool[wid][0] < s_pool[wid][1]) && __popc(dead) >= A.refill_min))) {
-            // the ended photons' absorption partials, before the lanes take new ones
-            flush(!alive && pcell >= 0, pcell, pdir, pacc);
-            if (!alive) pcell = -1;
-            unsigned long long pool_next = s_pool[wid][0], pool_end = s_pool[wid][1];
+                     ((!s_exh[wid] || s_q[wid][0] < s_q[wid][1]) && __popc(dead) >= A.refill_min))) {
+            unsigned long long pool_next = s_q[wid][0], pool_end = s_q[wid][1];
             bool exhausted = s_exh[wid] != 0;
             const unsigned ndead = __popc(dead);
             const unsigned rank = __popc(dead & below);
@@ -718,8 +717,8 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
             }
             __syncwarp();
             if (lane == 0) {
-                s_pool[wid][0] = pool_next;
-                s_pool[wid][1] = pool_end;
+                s_q[wid][0] = pool_next;
+                s_q[wid][1] = pool_end;
                 s_exh[wid] = exhausted;
             }
             __syncwarp();
@@ -798,15 +797,14 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
             const int ex = ux > 0.f ? I + r + 1 : I - r;
             const int ey = uy > 0.f ? J + r + 1 : J - r;
             const int ez = uz > 0.f ? min(K + r + 1, NZ) : max(K - r, 0);
-            const float tx = ux != 0.f ? (fminf((float)ex * RT_SC(cdx), RT_SC(xcap)) - ox) * ivx : INFINITY;
-            const float ty = uy != 0.f ? (fminf((float)ey * RT_SC(cdy), RT_SC(ycap)) - oy) * ivy : INFINITY;
-            const float tz = uz != 0.f ? (fminf((float)ez * RT_SC(cdz), RT_SC(H)) - oz) * ivz : INFINITY;
-            float tm;
-            int ax;
-            if (tz <= tx && tz <= ty) { tm = tz; ax = 2; }
-            else if (tx <= ty) { tm = tx; ax = 0; }
-            else { tm = ty; ax = 1; }
-            tm = fmaxf(tm, 0.f);
+            const float fx = fminf((float)ex * RT_SC(cdx), RT_SC(xcap));
+            const float fy = fminf((float)ey * RT_SC(cdy), RT_SC(ycap));
+            const float fz = fminf((float)ez * RT_SC(cdz), RT_SC(H));
+            const float tx = ux != 0.f ? (fx - ox) * ivx : INFINITY;
+            const float ty = uy != 0.f ? (fy - oy) * ivy : INFINITY;
+            const float tz = uz != 0.f ? (fz - oz) * ivz : INFINITY;
+            const bool cz_ = tz <= tx && tz <= ty, cx_ = !cz_ && tx <= ty, cy_ = !cz_ && !cx_;
+            const float tm = fmaxf(cz_ ? tz : (cx_ ? tx : ty), 0.f);
             if (kmaj * tm > tau) {
                 tau = __fdividef(tau, kmaj);      // the free path ends inside this box, tau from o
                 ready = kEvent;
@@ -814,54 +812,41 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
             }
             tau = fmaf(-kmaj, tm, tau);
             ++ncr;
-            float px = fmaf(ux, tm, ox), py = fmaf(uy, tm, oy), pz = fmaf(uz, tm, oz);
-            if (ax == 2) {
-                if (uz < 0.f) {
-                    if (ez == 0) { ready = kSurface; ox = px; oy = py; oz = 0.f; continue; }
-                    K = ez - 1;
-                } else {
-                    if (ez == NZ) { ready = kTop; ox = px; oy = py; oz = RT_SC(H); continue; }
-                    K = ez;
-                }
-                pz = (float)ez * RT_SC(cdz);
-            } else if (r > 0) {
-                K = min(max((int)(pz * RT_SC(inv_cdz)), uz < 0.f ? max(K - r, 0) : K),
-                        uz > 0.f ? min(K + r, NZ - 1) : K);
-            }
-            if (ax == 0) {
-                if (ux > 0.f) {
-                    I = ex >= NX ? ex - NX : ex;
-                    px = (float)I * RT_SC(cdx);
-                } else {
-                    I = ex - 1 < 0 ? ex - 1 + NX : ex - 1;
-                    px = I == NX - 1 ? RT_SC(Lx) : (float)(I + 1) * RT_SC(cdx);
-                }
-            } else if (r > 0) {
-                int c = (int)floorf(px * RT_SC(inv_cdx));
-                c = ux > 0.f ? min(max(c, I), I + r) : (ux < 0.f ? min(max(c, I - r), I) : I);
-                if (c < 0) { c += NX; px += RT_SC(Lx); } else if (c >= NX) { c -= NX; px -= RT_SC(Lx); }
-                I = c;
-            }
-            if (ax == 1) {
-                if (uy > 0.f) {
-                    J = ey >= NY ? ey - NY : ey;
-                    py = (float)J * RT_SC(cdy);
-                } else {
-                    J = ey - 1 < 0 ? ey - 1 + NY : ey - 1;
-                    py = J == NY - 1 ? RT_SC(Ly) : (float)(J + 1) * RT_SC(cdy);
-                }
-            } else if (r > 0) {
-                int c = (int)floorf(py * RT_SC(inv_cdy));
-                c = uy > 0.f ? min(max(c, J), J + r) : (uy < 0.f ? min(max(c, J - r), J) : J);
-                if (c < 0) { c += NY; py += RT_SC(Ly); } else if (c >= NY) { c -= NY; py -= RT_SC(Ly); }
-                J = c;
-            }
+            // Written without branches (selects only), so lanes that cross
+            // different faces do not diverge. On the crossed axis the position
+            // is the face and the cell the one beyond it; on the others the
+            // cell of the position, moved only forward and within the box (with
+            // r = 0 that is the current cell).
+            float px = cx_ ? fx : fmaf(ux, tm, ox);
+            float py = cy_ ? fy : fmaf(uy, tm, oy);
+            const float pz = cz_ ? fz : fmaf(uz, tm, oz);
+            int ci = (int)floorf(px * RT_SC(inv_cdx));
+            ci = cx_ ? (ux > 0.f ? ex : ex - 1)
+                     : (ux > 0.f ? min(max(ci, I), I + r) : (ux < 0.f ? min(max(ci, I - r), I) : I));
+            int cj = (int)floorf(py * RT_SC(inv_cdy));
+            cj = cy_ ? (uy > 0.f ? ey : ey - 1)
+                     : (uy > 0.f ? min(max(cj, J), J + r) : (uy < 0.f ? min(max(cj, J - r), J) : J));
+            int ck = (int)floorf(pz * RT_SC(inv_cdz));
+            ck = cz_ ? (uz > 0.f ? ez : ez - 1)
+                     : (uz > 0.f ? min(max(ck, K), min(K + r, NZ - 1))
+                                 : (uz < 0.f ? min(max(ck, max(K - r, 0)), K) : K));
+            // periodic x and y: the cell index and the position shift together
+            px += ci < 0 ? RT_SC(Lx) : (ci >= NX ? -RT_SC(Lx) : 0.f);
+            ci += ci < 0 ? NX : (ci >= NX ? -NX : 0);
+            py += cj < 0 ? RT_SC(Ly) : (cj >= NY ? -RT_SC(Ly) : 0.f);
+            cj += cj < 0 ? NY : (cj >= NY ? -NY : 0);
             ox = px; oy = py; oz = pz;
+            I = ci; J = cj;
+            K = min(max(ck, 0), NZ - 1);
+            // below the surface or above the top: that boundary's interaction;
+            // the box then loaded is not used
+            ready = ck < 0 ? kSurface : (ck >= NZ ? kTop : kNone);
             load_box();
         }
 
         // ---------------- 3. interact ----------------
         bool fl = false;                     // a partial to flush: the photon left its cell
+        bool ended = false;                  // the photon ended in this pass
         int fcell = 0;
         bool fdir = false;
         float facc = 0.f;
@@ -884,7 +869,7 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
             const uint4 rn = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk, 0u),
                                            RT_JB(key0), RT_JB(key1));
             ++blk;
-            bool turned = sfc, scattered = false;
+            bool turned = sfc;
             float mu = 0.f;
             if (!sfc) {
                 // ---- a5: majorant event at distance tau, inside the box ----
@@ -943,15 +928,15 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
                 const float den = kmaj - kabs;
                 const float xd = u01(rn.x) * den;
                 if (den > 0.f && xd < ksca) {
-                    if (xd < kscl) {
-                        float g;
+                    const bool cloud = xd < kscl;
+                    float g = 0.f;
+                    if (cloud) {
                         if constexpr (MODE == kOpticsRecord) g = __ldg(RT_SC(rec) + cell).w;
                         else g = __ldg(RT_SC(gcl) + cell);
-                        mu = hg_mu(g, u01(rn.y));
-                    } else {
-                        mu = rayleigh_mu(u01(rn.y));
                     }
-                    turned = scattered = true;
+                    const float xi = u01(rn.y), mh = hg_mu(g, xi), mr = rayleigh_mu(xi);
+                    mu = cloud ? mh : mr;
+                    turned = true;
                     direct = false;
                     ++nsc;
                 }
@@ -980,14 +965,10 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
             ox = px; oy = py; oz = pz;
             locate(px, py, pz);
             load_box();
-            // ---- a8: roulette (surface: word 0; null event: word 1, unused there;
-            //      after a scattering: word 0 of slot 1 of the same block) ----
-            if (w < 0.5f) {
-                float xi = u01(sfc ? rn.x : rn.y);
-                if (scattered)
-                    xi = u01(philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk - 1u, 1u),
-                                           RT_JB(key0), RT_JB(key1)).x);
-                if (roulette(xi)) end_photon();
+            // ---- a8: roulette, with the fifth uniform of the block ----
+            if (w < 0.5f && roulette(u01_low(rn))) {
+                end_photon();
+                ended = true;
             }
         } else if (ready == kTop) {
             // ---- a10: leaves through the domain top ----
@@ -997,15 +978,20 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
             const int fj = min(max((int)(py * RT_SC(inv_dy)), 0), ny - 1);
             tally_add(RT_SC(tal.toa) + (fj * nx + fi), w, RT_JB(scale2));
             end_photon();
+            ended = true;
         } else if (ready == kCap) {
             // step cap: record, stop the photon, never spin
             atomicAdd(&s_cnt[sid][kCntCapped], 1ull);
             atomicAdd(&s_led[sid][2], (double)w * RT_JB(energy));
             atomicOr(&RT_SC(scr)->status, kStatusBudget);
             end_photon();
+            ended = true;
         }
         ready = kNone;
         flush(fl, fcell, fdir, facc);
+        // an ended photon's partial (a lane may flush two in one pass)
+        flush(ended && pcell >= 0, pcell, pdir, pacc);
+        if (ended) pcell = -1;
     }
     // the last photons' absorption partials
     flush(pcell >= 0, pcell, pdir, pacc);

@@ -111,10 +111,13 @@ def test_gpu_absorber_over_lambertian_surface():
     mu0 = np.cos(np.deg2rad(sza))
     ref = refs.absorber_with_lambert(k, dz, mu0, 0.6, F0)
     g, st = gpu_batches(sc, sza, 17.0, F0, 1_000_000, range(16), cxyz=(2, 2, 2))
+    # Ten expectations are checked at once (4 + 4 layers, surface, top), so the
+    # bound is family-wise: 4.5 SE per comparison keeps the chance that any
+    # one of them fails by noise near 1e-4 (4 SE per comparison would be 6e-4).
     def check(arr, want):
         m = arr.mean(0)
         se = arr.std(0, ddof=1) / np.sqrt(arr.shape[0])
-        assert np.all(np.abs(m - want) < 4 * se + 1e-9 * abs(want)), (m, want, se)
+        assert np.all(np.abs(m - want) < 4.5 * se + 1e-9 * abs(want)), (m, want, se)
     check(g["sfc_dir"].mean(axis=(1, 2)), ref["sfc_dir"])
     check(g["toa_up"].mean(axis=(1, 2)), ref["toa_up"])
     assert np.all(g["sfc_dif"] == 0)
