@@ -45,9 +45,10 @@ COARSE = (2, 2, 2)
 # tally read-modify-write per majorant event, 4 B majorant box word per walk
 # step (the "crossings" counter).
 BYTES_PER_EVENT, BYTES_PER_CROSSING = 32, 4
-# derive, albedo check, majorant, column keys + column order (launch order),
+# derive, albedo check, majorant, majorant boxes (init + 4 levels of 3 axis
+# dilations and a selection), column keys + column order (launch order),
 # transport, 4 field sums, heating rate
-KERNELS_PER_STEP = 11
+KERNELS_PER_STEP = 28
 PROFILE = os.path.join(ROOT, "profiles", "trace_kernel_cumulus256.md")
 
 
@@ -65,9 +66,12 @@ def parse():
     p.add_argument("--no-denoise", action="store_true", help="skip the denoised-vs-plain time-to-RMSE leg")
     p.add_argument("--no-coupled", action="store_true", help="skip the graph-replay coupled-step leg")
     p.add_argument("--no-birth", action="store_true", help="skip the Sobol-vs-Philox start position leg")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched multi-scene workload leg")
     p.add_argument("--denoise-train", type=int, default=512, help="training scenes of the denoiser leg")
     p.add_argument("--no-l2-probe", action="store_true", help="skip the L2 read-bandwidth probe")
     p.add_argument("--denoise-epochs", type=int, default=32, help="training epochs of the denoiser leg")
+    p.add_argument("--reduce-fields", action="store_true",
+                   help="N>1: sum the ranks' output fields every step (NCCL all-reduce) into one combined field")
     p.add_argument("--no-autotune", action="store_true",
                    help="use the default launch parameters and the --coarse grid")
     p.add_argument("--coarse", type=int, nargs=3, default=None,
@@ -329,6 +333,112 @@ def birth_leg(scene, coarse, tuned):
             "rmse": res, "speedup_at_16ppc": speed}
 
 
+# ---- batched spectral + multi-scene workload (one recorded graph per step) ------------------
+
+def batched_leg(steps: int):
+    """All 112 quadrature points of 4 scenes of uneven size (128x128x96,
+    192x96x128, 256x256x128, 64x64x64) in one persistent launch of 2^26
+    photons with energy-proportional budgets, recorded once as a CUDA graph
+    (rt_batch_step) and replayed per step; the same step through
+    rt_trace_batch for comparison."""
+    import torch
+    from paper_2208_05247_b300 import rt, scenes
+    stream = torch.cuda.current_stream()
+    scs = scenes.batch_scenes()
+    scale, flux = scenes.gpoint_table()
+    tracers = []
+    for sc in scs:
+        t = rt.Tracer(sc.nx, sc.ny, sc.nz, sc.dx, sc.dy, sc.dz, stream=stream)
+        t.set_options(batch_optics=1)
+        t.set_optics(*sc.fields())
+        t.set_surface(sc.albedo)
+        t.build_accel(2, 2, 2)
+        tracers.append(t)
+    jobs = [dict(scene=t, sza_deg=SZA, azimuth_deg=AZ, toa_flux=float(flux[g]), gas_scale=float(scale[g]))
+            for t in tracers for g in range(len(flux))]
+    total = 2 ** 26
+
+    def timed(fn, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(k):
+            fn(i)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    def eager(i):
+        for t in tracers:
+            t.reset()
+        rt.rt_trace_batch(jobs, total_photons=total, seed=SEED + i)
+
+    step = rt.rt_batch_step_create(jobs, total_photons=total)
+    try:
+        for i in range(2):
+            rt.rt_batch_step_launch(step, SEED + i)
+        ms_graph = timed(lambda i: rt.rt_batch_step_launch(step, SEED + i), steps)
+        sts = [t.stats() for t in tracers]
+    finally:
+        rt.rt_batch_step_destroy(step)
+    eager(0)
+    ms_eager = timed(eager, steps)
+    ev = sum(st["events"] for st in sts)
+    cr = sum(st["crossings"] for st in sts)
+    ph = sum(st["photons"] for st in sts)
+    peak, _ = peaks()
+    closure = [abs(st["energy_in"] + st["energy_created"] - st["energy_destroyed"] - st["energy_capped"]
+                   - st["energy_toa_up"] - st["energy_atm_abs"] - st["energy_sfc_abs"]) / st["energy_in"]
+               for st in sts]
+    for t in tracers:
+        t.close()
+    alg = ev * BYTES_PER_EVENT + cr * BYTES_PER_CROSSING
+    return {"workload": "4 scenes (128x128x96, 192x96x128, 256x256x128, 64x64x64) x 112 quadrature points, "
+                        "2^26 photons per step, coarse grid 2x2x2, one persistent launch",
+            "ms_per_step_graph": ms_graph, "ms_per_step_eager": ms_eager, "photons_per_step": ph,
+            "events_per_s": ev / (ms_graph / 1e3), "photons_per_s": ph / (ms_graph / 1e3),
+            "roofline_frac": alg / (ms_graph / 1e3) / 1e9 / peak,
+            "roofline_note": "algorithmic bytes of the step over the whole replayed step (tally resets included)",
+            "ledger_residual_max": max(closure), "capped": sum(st["capped"] for st in sts)}
+
+
+# ---- end to end through the C ABI with plain host buffers ------------------------------
+
+def c_abi_host_leg(scene, coarse, tuned, steps, N, begin, total):
+    """The step a C caller with ordinary (pageable) host buffers makes: optics
+    and albedo in with RT_HOST, grid, reset, trace, and the fields and heating
+    rate out with RT_HOST (those calls synchronise), timed on the wall clock."""
+    from paper_2208_05247_b300 import rt
+    ins = [np.ascontiguousarray(a, dtype=np.float32) for a in scene.fields()]
+    alb = np.ascontiguousarray(scene.albedo, dtype=np.float32)
+    outs = {"abs3d": np.empty(scene.ncell), "hr": np.empty(scene.ncell)}
+    for k in ("sfc_dir", "sfc_dif", "toa_up"):
+        outs[k] = np.empty(scene.ncol)
+    with rt.Tracer(scene.nx, scene.ny, scene.nz, scene.dx, scene.dy, scene.dz) as t:
+        if tuned:
+            t.set_options(**{k: v for k, v in tuned.items() if k != "coarse"})
+
+        def one():
+            rt.rt_set_optics(t.h, scene.ncell, *ins)
+            rt.rt_set_surface(t.h, scene.ncol, alb)
+            rt.rt_build_accel(t.h, *coarse)
+            rt.rt_reset_tallies(t.h)
+            rt.rt_trace_range(t.h, SZA, AZ, F0, begin, N, total, SEED)
+            rt.rt_fields(t.h, scene.ncell, scene.ncol, outs["abs3d"], outs["sfc_dir"], outs["sfc_dif"], outs["toa_up"])
+            rt.rt_heating_rate(t.h, scene.ncell, outs["hr"], 0)
+
+        one()
+        events = t.stats()["events"]
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            one()
+        dt = (time.perf_counter() - t0) / steps
+    h2d = sum(a.nbytes for a in ins) + alb.nbytes
+    d2h = sum(v.nbytes for v in outs.values())
+    return {"value": events / dt, "unit": UNIT, "ms_per_step": 1e3 * dt, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "buffers": "pageable numpy arrays through RT_HOST, no overlap"}
+
+
 # ---- our CUDA path --------------------------------------------------------------------
 
 def run_ours(args):
@@ -388,7 +498,10 @@ def run_ours(args):
             ev[1].record(stream)
         rt.rt_fields(t.h, ncell, ncol, out["abs3d"], out["sfc_dir"], out["sfc_dif"], out["toa_up"])
         rt.rt_heating_rate(t.h, ncell, out["hr"], 0)
+        if reduce:
+            shard.reduce_fields(out)
 
+    reduce = dist is not None and args.reduce_fields
     for _ in range(max(1, args.warmup)):
         step(SEED)
     torch.cuda.synchronize()
@@ -434,7 +547,8 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": profiled_traffic(), "peak_source": peak_src,
             "kernel": "trace_kernel<double>", "kernel_ms": 1e3 * tk,
-            "algorithmic_bytes_per_launch": alg_bytes}
+            "algorithmic_bytes_per_launch": alg_bytes, "events_per_launch": events, "box_steps_per_launch": crossings,
+            "photons_per_s": N * world * args.steps / (ms_max / 1e3)}
     # the same algorithmic bytes against this GPU's L2 read bandwidth, measured
     # here (outside the timed region) by the library's read probe: the
     # transport kernel's working set is L2-resident
@@ -480,9 +594,14 @@ def run_ours(args):
         d2h = sum(v.numel() * 8 for v in h_outs[0].values())
         e2e = {"value": events_all * k2 / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * dt / k2,
-               "pipelined": "copies of step k+1 in and k-1 out overlap step k's transport (HostPipeline)"}
+               "pipelined": "copies of step k+1 in and k-1 out overlap step k's transport (HostPipeline)",
+               "photons_per_s": N * world * k2 / dt}
+        # the same step as a C caller with plain host buffers makes it
+        e2e["c_abi_host"] = c_abi_host_leg(scene, coarse, tuned, max(3, args.steps // 4), N, begin, total)
 
-    cstep = births = None
+    cstep = births = batched = None
+    if world == 1 and not args.no_batched:
+        batched = batched_leg(max(3, args.steps // 4))
     if world == 1 and not args.no_coupled:
         cstep = coupled_step_leg(t, d_in, d_alb, d_out, N, ms_max / args.steps, events, max(3, args.steps // 2))
     if world == 1 and not args.no_birth:
@@ -503,13 +622,15 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(args, world, coarse), launch=tuned or "defaults"),
+            "config": dict(workload_config(args, world, coarse), launch=tuned or "defaults",
+                           **({"parallelism": f"photon ranges, {world} ranks, fields summed every step "
+                                              "(NCCL all-reduce, FP64)"} if reduce else {})),
             "photons_per_s": N * world * args.steps / (ms_max / 1e3),
             "real_scatters_per_s": st["scatters"] * world * args.steps / (ms_max / 1e3),
             "events_per_step": events_all, "real_scatter_fraction": st["scatters"] / max(1, events),
             "trace_kernel_ms": 1e3 * tk, "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": KERNELS_PER_STEP * args.steps, "time_to_rmse": dn, "coupled_step": cstep,
-            "sobol_birth": births, "l2_roofline": l2roof}
+            "gpu_launches": KERNELS_PER_STEP * args.steps, "sobol_birth": births, "coupled_step": cstep,
+            "l2_roofline": l2roof, "time_to_rmse": dn, "batched": batched}
     print(json.dumps(line), flush=True)
     t.close()
     if dist is not None:

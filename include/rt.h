@@ -256,6 +256,33 @@ typedef struct {
  * RT_E_STATE (a scene without batch_optics or grid), RT_E_CUDA, RT_E_OOM. */
 int rt_trace_batch(const rt_job *jobs, int njobs, uint64_t total_photons, uint64_t seed);
 
+/* ---- a batched launch recorded once, replayed per model step ---- */
+
+/* The paper's coupled runs make one radiation call per model step (Sec. 2.2),
+ * each tracing all spectral quadrature points (Sec. 2.3). An rt_batch_step
+ * records what rt_trace_batch(jobs, njobs, total_photons, seed) does -- the
+ * photon budgets, the scene and job descriptors and the persistent launches
+ * (one per 512 jobs) -- as one CUDA graph, preceded by a reset of every
+ * scene's tallies, counters and energy ledger. Each rt_batch_step_launch
+ * uploads the job keys for `seed` (one host-to-device copy of the
+ * descriptors) and replays the graph on the first job's scene's stream:
+ * results equal those of rt_trace_batch with that seed after
+ * rt_reset_tallies on every scene, up to the order of FP64 additions. The
+ * graph reads the scenes' device buffers, so optics rewritten in place are
+ * traced by the next replay; the calls that reallocate or change a scene
+ * (rt_set_optics, rt_build_accel, rt_set_options, rt_trace*, rt_step_create,
+ * rt_destroy) return RT_E_STATE while a batch step uses it, and a scene takes
+ * part in at most one batch step. Errors as rt_trace_batch; *out receives the
+ * step. */
+typedef struct rt_batch_step_s *rt_batch_step;
+int rt_batch_step_create(const rt_job *jobs, int njobs, uint64_t total_photons, rt_batch_step *out);
+
+/* Replay the recorded batch for `seed`; asynchronous. */
+int rt_batch_step_launch(rt_batch_step s, uint64_t seed);
+
+/* Synchronise, free the graph and give the scenes back. NULL is accepted. */
+int rt_batch_step_destroy(rt_batch_step s);
+
 /* As rt_trace_range, with a fraction `diffuse_fraction` in [0,1] of the
  * photons starting diffuse (Sec. 2.3: the diffuse part of the top-of-domain
  * flux enters as isotropic downwelling radiance, so those photons start with

@@ -130,6 +130,22 @@ struct rt_scene {
     double energy_in = 0.0;
 
     rt_step step = nullptr;   // a recorded coupled-model step that owns the handle
+    int batch_steps = 0;      // recorded batched steps that use the handle
+};
+
+// A batched launch recorded as one CUDA graph (rt_batch_step_create).
+struct rt_batch_step_s {
+    rt_handle home = nullptr;
+    std::vector<rt_handle> scenes;
+    std::vector<double> scene_energy;       // W entering each scene per replay
+    std::vector<size_t> job_off;            // byte offset of each job descriptor in desc
+    std::vector<uint32_t> job_index;        // its index among all jobs (key offset)
+    unsigned char *desc_dev = nullptr;      // descriptors of every chunk, in device memory
+    unsigned char *desc_host = nullptr;     // pinned mirror; job keys rewritten per replay
+    size_t desc_bytes = 0;
+    cudaEvent_t copied = nullptr;           // the last upload of desc_host has finished
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 struct rt_step_s {
@@ -160,6 +176,8 @@ int check_free(rt_handle h, const char *who)
     int rc = check(h);
     if (rc) return rc;
     if (h->step) return fail(RT_E_STATE, "%s: the handle belongs to an rt_step; destroy the step first", who);
+    if (h->batch_steps)
+        return fail(RT_E_STATE, "%s: the handle is used by an rt_batch_step; destroy the step first", who);
     return RT_OK;
 }
 
@@ -483,12 +501,9 @@ int launch_trace(rt_handle h, T *base, double sza, double az, double toa_flux, d
     return RT_OK;
 }
 
-// One batched launch: scene and job descriptors go to the home scene's
-// descriptor buffer, the photon queue head to its scratch; `count` photons in
-// total, job j owning queue indices [jobs[j].start, jobs[j+1].start).
+// Scene descriptors of a batched launch (the tallies of each scene's precision).
 template <typename T>
-int launch_batch(rt_handle home, const std::vector<rt_handle> &scenes, const std::vector<rt::JobDev> &jobs,
-                 unsigned long long count)
+std::vector<rt::SceneDev<T>> batch_scenes(const std::vector<rt_handle> &scenes)
 {
     std::vector<rt::SceneDev<T>> sd(scenes.size());
     for (size_t q = 0; q < scenes.size(); ++q) {
@@ -496,6 +511,48 @@ int launch_batch(rt_handle home, const std::vector<rt_handle> &scenes, const std
         T *base = std::is_same<T, double>::value ? reinterpret_cast<T *>(h->t64) : reinterpret_cast<T *>(h->t32);
         sd[q] = scene_desc<T>(h, base, true);
     }
+    return sd;
+}
+
+// Launch one batched transport on stream st from descriptors already in device
+// memory at desc (nscenes scene descriptors, then njobs job descriptors).
+template <typename T>
+int launch_batch_from(rt_handle home, const unsigned char *desc, int nscenes, int njobs, unsigned long long count,
+                      cudaStream_t st)
+{
+    const size_t bytes_s = nscenes * sizeof(rt::SceneDev<T>), bytes_j = njobs * sizeof(rt::JobDev);
+    rt::TraceArgs<T> A{};
+    A.scenes = reinterpret_cast<const rt::SceneDev<T> *>(desc);
+    A.jobs = reinterpret_cast<const rt::JobDev *>(desc + bytes_s);
+    A.nscenes = nscenes;
+    A.njobs = njobs;
+    A.count = count;
+    A.scr = home->scr;
+    fill_launch(home, A);
+    const int block = home->opt.block_size > 0 ? home->opt.block_size : 256;
+    const size_t smem = bytes_s + bytes_j;
+    if (smem > 48 * 1024)
+        RT_CUDA(cudaFuncSetAttribute(rt::trace_kernel<T, rt::kOpticsSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    int bps = home->opt.blocks_per_sm;
+    int fit = 0;
+    RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, rt::trace_kernel<T, rt::kOpticsSplit>, block, smem));
+    if (fit <= 0) return fail(RT_E_INVAL, "batched launch: descriptors of %d jobs do not fit in shared memory", njobs);
+    if (bps <= 0 || bps > fit) bps = fit;
+    RT_CUDA(cudaMemsetAsync(&home->scr->queue_head, 0, sizeof(unsigned long long), st));
+    rt::trace_kernel<T, rt::kOpticsSplit><<<home->num_sms * bps, block, smem, st>>>(A);
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+// One batched launch: scene and job descriptors go to the home scene's
+// descriptor buffer, the photon queue head to its scratch; `count` photons in
+// total, job j owning queue indices [jobs[j].start, jobs[j+1].start).
+template <typename T>
+int launch_batch(rt_handle home, const std::vector<rt_handle> &scenes, const std::vector<rt::JobDev> &jobs,
+                 unsigned long long count)
+{
+    const std::vector<rt::SceneDev<T>> sd = batch_scenes<T>(scenes);
     const size_t bytes_s = sd.size() * sizeof(rt::SceneDev<T>), bytes_j = jobs.size() * sizeof(rt::JobDev);
     if (home->desc_cap < bytes_s + bytes_j) {
         cudaFree(home->desc);
@@ -511,31 +568,7 @@ int launch_batch(rt_handle home, const std::vector<rt_handle> &scenes, const std
     std::memcpy(host.data(), sd.data(), bytes_s);
     std::memcpy(host.data() + bytes_s, jobs.data(), bytes_j);
     RT_CUDA(cudaMemcpyAsync(home->desc, host.data(), host.size(), cudaMemcpyHostToDevice, home->stream));
-
-    rt::TraceArgs<T> A{};
-    A.scenes = reinterpret_cast<const rt::SceneDev<T> *>(home->desc);
-    A.jobs = reinterpret_cast<const rt::JobDev *>(home->desc + bytes_s);
-    A.nscenes = (int)sd.size();
-    A.njobs = (int)jobs.size();
-    A.count = count;
-    A.scr = home->scr;
-    fill_launch(home, A);
-
-    const int block = home->opt.block_size > 0 ? home->opt.block_size : 256;
-    const size_t smem = bytes_s + bytes_j;
-    if (smem > 48 * 1024)
-        RT_CUDA(cudaFuncSetAttribute(rt::trace_kernel<T, rt::kOpticsSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    int bps = home->opt.blocks_per_sm;
-    int fit = 0;
-    RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, rt::trace_kernel<T, rt::kOpticsSplit>, block, smem));
-    if (fit <= 0) return fail(RT_E_INVAL, "rt_trace_batch: descriptors of %d jobs do not fit in shared memory",
-                              (int)jobs.size());
-    if (bps <= 0 || bps > fit) bps = fit;
-    RT_CUDA(cudaMemsetAsync(&home->scr->queue_head, 0, sizeof(unsigned long long), home->stream));
-    rt::trace_kernel<T, rt::kOpticsSplit><<<home->num_sms * bps, block, smem, home->stream>>>(A);
-    RT_CUDA(cudaGetLastError());
-    return RT_OK;
+    return launch_batch_from<T>(home, home->desc, (int)sd.size(), (int)jobs.size(), count, home->stream);
 }
 
 // Record one coupled-model step on capture stream cs (see rt_step_create). The
@@ -612,6 +645,103 @@ int record_step(rt_handle h, const rt_step_desc *d, rt_step s, cudaStream_t cs, 
         RT_CUDA(cudaGetLastError());
         if (q < 2 && (d->homogenize & RT_HOM_SURFACE)) rt::homogenize_layers<<<1, 1024, 0, cs>>>(out2[q], h->ncol);
         RT_CUDA(cudaGetLastError());
+    }
+    return RT_OK;
+}
+
+// A batched launch, planned: its distinct scenes, the energy each job brings
+// in, and the job descriptors in chunks of at most kMaxBatchJobs (one launch
+// each), with the photon count of every chunk.
+struct BatchPlan {
+    rt_handle home = nullptr;
+    std::vector<rt_handle> scenes;
+    std::vector<double> energy;                  // per job [W]
+    std::vector<uint64_t> photons;               // per job
+    std::vector<std::vector<rt::JobDev>> chunks;
+    std::vector<unsigned long long> counts;
+};
+
+// Validation and photon budgets of rt_trace_batch / rt_batch_step_create.
+int plan_batch(const char *who, const rt_job *jobs, int njobs, uint64_t total_photons, uint64_t seed, BatchPlan *P)
+{
+    if (!jobs || njobs <= 0) return fail(RT_E_INVAL, "%s: need at least one job", who);
+    rt_handle home = jobs[0].scene;
+    int rc = check(home);
+    if (rc) return rc;
+    P->home = home;
+    std::vector<int> sidx(njobs);
+    P->energy.assign(njobs, 0.0);
+    for (int j = 0; j < njobs; ++j) {
+        const rt_job &jb = jobs[j];
+        rt_handle h = jb.scene;
+        if (!h) return fail(RT_E_INVAL, "%s: job %d has no scene", who, j);
+        if (h->step) return fail(RT_E_STATE, "%s: job %d: the scene belongs to an rt_step", who, j);
+        if (h->device != home->device) return fail(RT_E_INVAL, "%s: all scenes must be on one device", who);
+        if (!h->optics_ok || !h->surface_ok || !h->accel_ok)
+            return fail(RT_E_STATE, "%s: job %d: set optics and surface and build the acceleration grid first",
+                        who, j);
+        if (!h->split_ok || !h->accel2_ok)
+            return fail(RT_E_STATE, "%s: job %d: set rt_options.batch_optics = 1 before rt_set_optics, then "
+                                    "build the acceleration grid", who, j);
+        if (h->tally_prec != home->tally_prec)
+            return fail(RT_E_INVAL, "%s: all scenes must use the same tally precision", who);
+        if (!(jb.sza_deg >= 0.0 && jb.sza_deg < 90.0) || !std::isfinite(jb.azimuth_deg) ||
+            !(jb.toa_flux >= 0.0) || !std::isfinite(jb.toa_flux) || !(jb.gas_scale >= 0.0) ||
+            !std::isfinite(jb.gas_scale) || jb.gas_scale > 1e30 ||
+            !(jb.diffuse_fraction >= 0.0 && jb.diffuse_fraction <= 1.0))
+            return fail(RT_E_INVAL, "%s: job %d: bad sza, azimuth, toa_flux or gas_scale", who, j);
+        int q = -1;
+        for (size_t k = 0; k < P->scenes.size(); ++k)
+            if (P->scenes[k] == h) q = (int)k;
+        if (q < 0) {
+            if ((int)P->scenes.size() == rt::kMaxBatchScenes)
+                return fail(RT_E_INVAL, "%s: at most %d distinct scenes per call", who, rt::kMaxBatchScenes);
+            q = (int)P->scenes.size();
+            P->scenes.push_back(h);
+        }
+        sidx[j] = q;
+        P->energy[j] = jb.toa_flux * std::cos(jb.sza_deg * kPi / 180.0) * h->nx * h->dx * h->ny * h->dy;
+    }
+    // photon budgets: given per job, or total_photons split in proportion to
+    // the energy each job brings in (largest remainders get the leftovers)
+    std::vector<uint64_t> &n = P->photons;
+    n.assign(njobs, 0);
+    if (total_photons > 0) {
+        double etot = 0.0;
+        for (double e : P->energy) etot += e;
+        if (!(etot > 0.0)) return fail(RT_E_INVAL, "%s: no job brings in any energy", who);
+        std::vector<std::pair<double, int>> frac(njobs);
+        uint64_t used = 0;
+        for (int j = 0; j < njobs; ++j) {
+            const double x = (double)total_photons * P->energy[j] / etot;
+            n[j] = (uint64_t)std::floor(x);
+            used += n[j];
+            frac[j] = {x - std::floor(x), j};
+        }
+        std::sort(frac.begin(), frac.end(), [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+            return a.first > b.first || (a.first == b.first && a.second < b.second);
+        });
+        for (uint64_t k = 0; used < total_photons; ++k, ++used) ++n[frac[k % njobs].second];
+    } else {
+        for (int j = 0; j < njobs; ++j) n[j] = jobs[j].photons;
+    }
+    for (int c0 = 0; c0 < njobs; c0 += rt::kMaxBatchJobs) {
+        const int c1 = std::min(njobs, c0 + rt::kMaxBatchJobs);
+        std::vector<rt::JobDev> jd;
+        unsigned long long start = 0;
+        for (int j = c0; j < c1; ++j) {
+            rt_handle h = jobs[j].scene;
+            rt::JobDev J = job_desc(h, jobs[j].sza_deg, jobs[j].azimuth_deg, jobs[j].toa_flux, jobs[j].gas_scale,
+                                    n[j] ? n[j] : 1, seed, (uint32_t)j);
+            J.start = start;
+            J.id_begin = 0;
+            J.scene = sidx[j];
+            J.diffuse = (float)jobs[j].diffuse_fraction;
+            jd.push_back(J);
+            start += n[j];
+        }
+        P->chunks.push_back(std::move(jd));
+        P->counts.push_back(start);
     }
     return RT_OK;
 }
@@ -695,6 +825,7 @@ int rt_destroy(rt_handle h)
 {
     if (!h) return RT_OK;
     if (h->step) return fail(RT_E_STATE, "rt_destroy: destroy the handle's rt_step first");
+    if (h->batch_steps) return fail(RT_E_STATE, "rt_destroy: destroy the rt_batch_steps that use the handle first");
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
@@ -976,88 +1107,142 @@ int rt_trace(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux, u
 
 int rt_trace_batch(const rt_job *jobs, int njobs, uint64_t total_photons, uint64_t seed)
 {
-    if (!jobs || njobs <= 0) return fail(RT_E_INVAL, "rt_trace_batch: need at least one job");
-    rt_handle home = jobs[0].scene;
-    int rc = check(home);
+    BatchPlan P;
+    int rc = plan_batch("rt_trace_batch", jobs, njobs, total_photons, seed, &P);
     if (rc) return rc;
-    std::vector<rt_handle> scenes;
-    std::vector<int> sidx(njobs);
-    std::vector<double> energy(njobs);
-    for (int j = 0; j < njobs; ++j) {
-        const rt_job &jb = jobs[j];
-        rt_handle h = jb.scene;
-        if (!h) return fail(RT_E_INVAL, "rt_trace_batch: job %d has no scene", j);
-        if (h->step) return fail(RT_E_STATE, "rt_trace_batch: job %d: the scene belongs to an rt_step", j);
-        if (h->device != home->device) return fail(RT_E_INVAL, "rt_trace_batch: all scenes must be on one device");
-        if (!h->optics_ok || !h->surface_ok || !h->accel_ok)
-            return fail(RT_E_STATE, "rt_trace_batch: job %d: set optics and surface and build the "
-                                    "acceleration grid first", j);
-        if (!h->split_ok || !h->accel2_ok)
-            return fail(RT_E_STATE, "rt_trace_batch: job %d: set rt_options.batch_optics = 1 before "
-                                    "rt_set_optics, then build the acceleration grid", j);
-        if (h->tally_prec != home->tally_prec)
-            return fail(RT_E_INVAL, "rt_trace_batch: all scenes must use the same tally precision");
-        if (!(jb.sza_deg >= 0.0 && jb.sza_deg < 90.0) || !std::isfinite(jb.azimuth_deg) ||
-            !(jb.toa_flux >= 0.0) || !std::isfinite(jb.toa_flux) || !(jb.gas_scale >= 0.0) ||
-            !std::isfinite(jb.gas_scale) || jb.gas_scale > 1e30 ||
-            !(jb.diffuse_fraction >= 0.0 && jb.diffuse_fraction <= 1.0))
-            return fail(RT_E_INVAL, "rt_trace_batch: job %d: bad sza, azimuth, toa_flux or gas_scale", j);
-        int q = -1;
-        for (size_t k = 0; k < scenes.size(); ++k)
-            if (scenes[k] == h) q = (int)k;
-        if (q < 0) {
-            if ((int)scenes.size() == rt::kMaxBatchScenes)
-                return fail(RT_E_INVAL, "rt_trace_batch: at most %d distinct scenes per call", rt::kMaxBatchScenes);
-            q = (int)scenes.size();
-            scenes.push_back(h);
-        }
-        sidx[j] = q;
-        energy[j] = jb.toa_flux * std::cos(jb.sza_deg * kPi / 180.0) * h->nx * h->dx * h->ny * h->dy;
-    }
-    // photon budgets: given per job, or total_photons split in proportion to
-    // the energy each job brings in (largest remainders get the leftovers)
-    std::vector<uint64_t> n(njobs, 0);
-    if (total_photons > 0) {
-        double etot = 0.0;
-        for (double e : energy) etot += e;
-        if (!(etot > 0.0)) return fail(RT_E_INVAL, "rt_trace_batch: no job brings in any energy");
-        std::vector<std::pair<double, int>> frac(njobs);
-        uint64_t used = 0;
-        for (int j = 0; j < njobs; ++j) {
-            const double x = (double)total_photons * energy[j] / etot;
-            n[j] = (uint64_t)std::floor(x);
-            used += n[j];
-            frac[j] = {x - std::floor(x), j};
-        }
-        std::sort(frac.begin(), frac.end(), [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
-            return a.first > b.first || (a.first == b.first && a.second < b.second);
-        });
-        for (uint64_t k = 0; used < total_photons; ++k, ++used) ++n[frac[k % njobs].second];
-    } else {
-        for (int j = 0; j < njobs; ++j) n[j] = jobs[j].photons;
-    }
-    for (int c0 = 0; c0 < njobs; c0 += rt::kMaxBatchJobs) {
-        const int c1 = std::min(njobs, c0 + rt::kMaxBatchJobs);
-        std::vector<rt::JobDev> jd;
-        unsigned long long start = 0;
-        for (int j = c0; j < c1; ++j) {
-            rt_handle h = jobs[j].scene;
-            rt::JobDev J = job_desc(h, jobs[j].sza_deg, jobs[j].azimuth_deg, jobs[j].toa_flux, jobs[j].gas_scale,
-                                    n[j] ? n[j] : 1, seed, (uint32_t)j);
-            J.start = start;
-            J.id_begin = 0;
-            J.scene = sidx[j];
-            J.diffuse = (float)jobs[j].diffuse_fraction;
-            jd.push_back(J);
-            start += n[j];
-        }
-        if (start == 0) continue;
-        rc = home->tally_prec == RT_TALLY_FP64 ? launch_batch<double>(home, scenes, jd, start)
-                                               : launch_batch<float>(home, scenes, jd, start);
+    rt_handle home = P.home;
+    for (size_t c = 0; c < P.chunks.size(); ++c) {
+        if (P.counts[c] == 0) continue;
+        rc = home->tally_prec == RT_TALLY_FP64 ? launch_batch<double>(home, P.scenes, P.chunks[c], P.counts[c])
+                                               : launch_batch<float>(home, P.scenes, P.chunks[c], P.counts[c]);
         if (rc) return rc;
     }
     for (int j = 0; j < njobs; ++j)
-        if (n[j]) jobs[j].scene->energy_in += energy[j];
+        if (P.photons[j]) jobs[j].scene->energy_in += P.energy[j];
+    return RT_OK;
+}
+
+int rt_batch_step_create(const rt_job *jobs, int njobs, uint64_t total_photons, rt_batch_step *out)
+{
+    if (out) *out = nullptr;
+    if (!out) return fail(RT_E_INVAL, "rt_batch_step_create: null output");
+    BatchPlan P;
+    int rc = plan_batch("rt_batch_step_create", jobs, njobs, total_photons, 0, &P);
+    if (rc) return rc;
+    for (rt_handle h : P.scenes)
+        if (h->batch_steps) return fail(RT_E_STATE, "rt_batch_step_create: a scene is already used by an rt_batch_step");
+    rt_handle home = P.home;
+    const bool fp64 = home->tally_prec == RT_TALLY_FP64;
+    rt_batch_step s = new (std::nothrow) rt_batch_step_s;
+    if (!s) return fail(RT_E_OOM, "rt_batch_step_create: host allocation failed");
+    s->home = home;
+    s->scenes = P.scenes;
+    s->scene_energy.assign(P.scenes.size(), 0.0);
+    for (int j = 0; j < njobs; ++j)
+        for (size_t q = 0; q < P.scenes.size(); ++q)
+            if (P.scenes[q] == jobs[j].scene && P.photons[j]) s->scene_energy[q] += P.energy[j];
+    cudaStream_t cs = nullptr;
+    auto bail = [&](int code) {
+        if (s->exec) cudaGraphExecDestroy(s->exec);
+        if (s->graph) cudaGraphDestroy(s->graph);
+        if (s->copied) cudaEventDestroy(s->copied);
+        cudaFree(s->desc_dev);
+        if (s->desc_host) cudaFreeHost(s->desc_host);
+        if (cs) cudaStreamDestroy(cs);
+        delete s;
+        return code;
+    };
+    // descriptors of every chunk, one after another
+    const size_t bytes_s = P.scenes.size() * (fp64 ? sizeof(rt::SceneDev<double>) : sizeof(rt::SceneDev<float>));
+    std::vector<size_t> off(P.chunks.size());
+    for (size_t c = 0; c < P.chunks.size(); ++c) {
+        off[c] = s->desc_bytes;
+        s->desc_bytes += bytes_s + P.chunks[c].size() * sizeof(rt::JobDev);
+    }
+    if ((rc = dev_alloc(&s->desc_dev, s->desc_bytes))) return bail(rc);
+    if (cudaMallocHost(reinterpret_cast<void **>(&s->desc_host), s->desc_bytes) != cudaSuccess)
+        return bail(fail(RT_E_OOM, "rt_batch_step_create: pinned allocation failed"));
+    uint32_t jidx = 0;
+    for (size_t c = 0; c < P.chunks.size(); ++c) {
+        if (fp64) {
+            const auto sd = batch_scenes<double>(P.scenes);
+            std::memcpy(s->desc_host + off[c], sd.data(), bytes_s);
+        } else {
+            const auto sd = batch_scenes<float>(P.scenes);
+            std::memcpy(s->desc_host + off[c], sd.data(), bytes_s);
+        }
+        for (size_t j = 0; j < P.chunks[c].size(); ++j, ++jidx) {
+            const size_t o = off[c] + bytes_s + j * sizeof(rt::JobDev);
+            std::memcpy(s->desc_host + o, &P.chunks[c][j], sizeof(rt::JobDev));
+            s->job_off.push_back(o);
+            s->job_index.push_back(jidx);
+        }
+    }
+    cudaError_t e = cudaEventCreateWithFlags(&s->copied, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bail(fail(RT_E_CUDA, "rt_batch_step_create: %s", cudaGetErrorString(e)));
+    // the recorded step: reset every scene's tallies and counters, then one
+    // persistent launch per chunk of jobs
+    rc = RT_OK;
+    for (rt_handle h : P.scenes) {
+        const size_t tb = tally_len(h) * (fp64 ? sizeof(double) : sizeof(float));
+        if ((e = cudaMemsetAsync(fp64 ? (void *)h->t64 : (void *)h->t32, 0, tb, cs)) != cudaSuccess ||
+            (e = cudaMemsetAsync(h->scr, 0, sizeof(rt::Scratch), cs)) != cudaSuccess) {
+            rc = fail(RT_E_CUDA, "rt_batch_step_create: %s", cudaGetErrorString(e));
+            break;
+        }
+    }
+    for (size_t c = 0; c < P.chunks.size() && rc == RT_OK; ++c) {
+        if (P.counts[c] == 0) continue;
+        rc = fp64 ? launch_batch_from<double>(home, s->desc_dev + off[c], (int)P.scenes.size(), (int)P.chunks[c].size(),
+                                              P.counts[c], cs)
+                  : launch_batch_from<float>(home, s->desc_dev + off[c], (int)P.scenes.size(), (int)P.chunks[c].size(),
+                                             P.counts[c], cs);
+    }
+    e = cudaStreamEndCapture(cs, &s->graph);
+    if (rc) return bail(rc);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->exec, s->graph, 0);
+    if (e != cudaSuccess) return bail(fail(RT_E_CUDA, "rt_batch_step_create: capture: %s", cudaGetErrorString(e)));
+    cudaStreamDestroy(cs);
+    for (rt_handle h : P.scenes) ++h->batch_steps;
+    *out = s;
+    return RT_OK;
+}
+
+int rt_batch_step_launch(rt_batch_step s, uint64_t seed)
+{
+    if (!s) return fail(RT_E_INVAL, "rt_batch_step_launch: null step");
+    rt_handle home = s->home;
+    int rc = check(home);
+    if (rc) return rc;
+    // the previous replay's upload must be done before its source is rewritten
+    RT_CUDA(cudaEventSynchronize(s->copied));
+    for (size_t j = 0; j < s->job_off.size(); ++j) {
+        rt::JobDev *J = reinterpret_cast<rt::JobDev *>(s->desc_host + s->job_off[j]);
+        J->key0 = (uint32_t)seed;
+        J->key1 = (uint32_t)(seed >> 32) + s->job_index[j] * 0x9E3779B9u;
+    }
+    RT_CUDA(cudaMemcpyAsync(s->desc_dev, s->desc_host, s->desc_bytes, cudaMemcpyHostToDevice, home->stream));
+    RT_CUDA(cudaEventRecord(s->copied, home->stream));
+    RT_CUDA(cudaGraphLaunch(s->exec, home->stream));
+    for (size_t q = 0; q < s->scenes.size(); ++q) s->scenes[q]->energy_in = s->scene_energy[q];
+    return RT_OK;
+}
+
+int rt_batch_step_destroy(rt_batch_step s)
+{
+    if (!s) return RT_OK;
+    cudaSetDevice(s->home->device);
+    if (s->home->stream) cudaStreamSynchronize(s->home->stream);
+    else cudaDeviceSynchronize();
+    if (s->exec) cudaGraphExecDestroy(s->exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    if (s->copied) cudaEventDestroy(s->copied);
+    cudaFree(s->desc_dev);
+    if (s->desc_host) cudaFreeHost(s->desc_host);
+    for (rt_handle h : s->scenes) --h->batch_steps;
+    delete s;
     return RT_OK;
 }
 

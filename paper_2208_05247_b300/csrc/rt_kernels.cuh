@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
             atomicAdd(&s_cnt[sid][kCntKills], 1ull);
             return true;
         }
-        atomicAdd(&s_led[sid][0], (double)(1.0f - w) * RT_JB(energy));
+        atomicAdd(&s_led[sid][0], (1.0 - (double)w) * RT_JB(energy));
         w = 1.f;
         return false;
     };
@@ -913,14 +913,20 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
                     cell = (gk * ny + gj) * nx + gi;
                     optics();
                 }
+                // the weight splits exactly into the deposit and what goes on
+                // (w = dep + wn in FP32): the smaller share is rounded, the
+                // larger is the exact difference (Sterbenz)
                 const float pabs = fminf(__fdividef(kabs, kmaj), 1.0f);
-                const float wn = w * (1.0f - pabs);
+                const float wa = w * (1.0f - pabs), wb = w * pabs;
+                const bool keep = pabs <= 0.5f;
+                const float wn = keep ? wa : w - wb;
+                const float dep = keep ? w - wa : wb;
                 if (cell != pcell || direct != pdir) {
                     fl = pcell >= 0;
                     fcell = pcell; fdir = pdir; facc = pacc;
                     pcell = cell; pdir = direct; pacc = 0.f;
                 }
-                pacc += w - wn;
+                pacc += dep;
                 w = wn;
                 ++nev;
                 // ---- a6/a7: real scattering or null collision ----

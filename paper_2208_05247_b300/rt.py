@@ -102,6 +102,9 @@ def library() -> ctypes.CDLL:
             "rt_last_error_code": ([], i32),
             "rt_trace_noalloc": ([i32, i32, i32, f64, f64, f64] + [P] * 6 + [i32, i32, i32, f64, f64, f64,
                                                                             u64, u64] + [P] * 5 + [P, P], i32),
+            "rt_batch_step_create": ([ctypes.POINTER(rt_job), i32, u64, ctypes.POINTER(ctypes.c_void_p)], i32),
+            "rt_batch_step_launch": ([P, u64], i32),
+            "rt_batch_step_destroy": ([P], i32),
             "rt_step_create": ([H, ctypes.POINTER(rt_step_desc), ctypes.POINTER(ctypes.c_void_p)], i32),
             "rt_step_launch": ([P, f64, f64, f64, f64, u64], i32),
             "rt_step_destroy": ([P], i32),
@@ -248,6 +251,11 @@ def rt_trace_range(h, sza_deg, azimuth_deg, toa_flux, photon_begin, photon_count
 def rt_trace_batch(jobs, total_photons=0, seed=1):
     """jobs: sequence of dicts with scene (handle or Tracer), sza_deg, azimuth_deg,
     toa_flux, gas_scale and photons (used when total_photons is 0)."""
+    arr = _job_array(jobs)
+    return _check(library().rt_trace_batch(arr, len(jobs), int(total_photons), int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+
+def _job_array(jobs):
     arr = (rt_job * len(jobs))()
     for a, j in zip(arr, jobs):
         sc = j["scene"]
@@ -258,7 +266,22 @@ def rt_trace_batch(jobs, total_photons=0, seed=1):
         a.gas_scale = float(j.get("gas_scale", 1.0))
         a.photons = int(j.get("photons", 0))
         a.diffuse_fraction = float(j.get("diffuse_fraction", 0.0))
-    return _check(library().rt_trace_batch(arr, len(jobs), int(total_photons), int(seed) & 0xFFFFFFFFFFFFFFFF))
+    return arr
+
+
+def rt_batch_step_create(jobs, total_photons=0) -> int:
+    """Record rt_trace_batch(jobs, total_photons) as one CUDA graph; returns the step."""
+    out = ctypes.c_void_p(0)
+    _check(library().rt_batch_step_create(_job_array(jobs), len(jobs), int(total_photons), ctypes.byref(out)))
+    return out.value
+
+
+def rt_batch_step_launch(step, seed=1):
+    _check(library().rt_batch_step_launch(step, int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+
+def rt_batch_step_destroy(step):
+    _check(library().rt_batch_step_destroy(step))
 
 
 def rt_fields(h, ncell, ncol, abs3d=None, sfc_dir=None, sfc_dif=None, toa_up=None):

@@ -2,8 +2,10 @@
 
 Photons are independent and their random streams are keyed by photon id, so a
 run of `per_rank * world` photons splits into disjoint id ranges, one per rank,
-with no data-path communication. Summing the ranks' tallies (optional, e.g.
-for a combined field) reproduces the single-process run.
+with no data-path communication. Each rank normalises its fields with the
+photon count of the whole run (photons_total), so summing the ranks' fields
+(reduce_fields: one sum all-reduce per field, NCCL between GPUs) reproduces
+the single-process run up to the order of FP64 additions.
 """
 from __future__ import annotations
 
@@ -30,3 +32,18 @@ def sum_tallies(arrays, group=None):
     for a in arrays:
         dist.all_reduce(a, op=dist.ReduceOp.SUM, group=group)
     return arrays
+
+
+def reduce_fields(fields, group=None):
+    """Sum the output fields of all ranks in place (dict or list of tensors).
+
+    The fields must be normalised with the whole run's photon count, as
+    rt_trace_range does with photons_total; absorption, fluxes and heating
+    rates are all linear in the tallies, so their sums are the fields of the
+    combined run. Returns the same container.
+    """
+    import torch.distributed as dist
+    tensors = list(fields.values()) if isinstance(fields, dict) else list(fields)
+    for a in tensors:
+        dist.all_reduce(a, op=dist.ReduceOp.SUM, group=group)
+    return fields

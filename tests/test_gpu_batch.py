@@ -45,7 +45,7 @@ def energy_of(scene, job):
     return job["toa_flux"] * np.cos(np.deg2rad(job["sza_deg"])) * scene.nx * scene.dx * scene.ny * scene.dy
 
 
-def closes(st, tol=2e-6):
+def closes(st, tol=1e-9):
     lhs = st["energy_in"] + st["energy_created"] - st["energy_destroyed"] - st["energy_capped"]
     rhs = st["energy_toa_up"] + st["energy_atm_abs"] + st["energy_sfc_abs"]
     return abs(lhs - rhs) < tol * st["energy_in"]
@@ -149,7 +149,7 @@ def test_multi_scene_batch_parity_with_oracle():
     for name in ("A", "B"):
         for f in FIELDS:
             rel, se = refs.domain_compare(np.stack(gpu[name][f]), np.stack(orc[name][f]))
-            assert abs(rel) < max(0.005, 4 * se), (name, f, rel, se)
+            assert abs(rel) < 4 * se + 1e-12, (name, f, rel, se)
 
 
 def test_zero_flux_jobs_and_more_than_512_jobs(small_scene):
@@ -210,3 +210,48 @@ def test_full_batched_workload_closes_and_splits_budgets():
         area = sc.nx * sc.dx * sc.ny * sc.dy
         assert np.isclose(st["energy_in"], 1000.0 * np.cos(np.deg2rad(30.0)) * area, rtol=1e-9)
         t.close()
+
+
+def test_batch_step_graph_replay_equals_eager_batch():
+    """rt_batch_step records the batched launch as one CUDA graph; a replay for a
+    seed equals rt_trace_batch with that seed on freshly reset tallies."""
+    scA = scenes.ellipsoid_scene(seed=0)
+    scB = scenes.cumulus_scene(seed=5, nx=48, ny=40, nz=32)
+    tA, tB = batch_tracer(scA), batch_tracer(scB)
+    try:
+        jobs = []
+        for t, sza in ((tA, 30.0), (tB, 45.0)):
+            for s, f in ((0.05, 300.0), (1.0, 500.0), (4.0, 200.0)):
+                jobs.append(dict(scene=t, sza_deg=sza, azimuth_deg=15.0, toa_flux=f, gas_scale=s))
+        total = 2 ** 20
+
+        def eager(seed):
+            for t in (tA, tB):
+                t.reset()
+            rt.rt_trace_batch(jobs, total_photons=total, seed=seed)
+            return [(t.fields(split=True), t.stats()) for t in (tA, tB)]
+
+        want = {seed: eager(seed) for seed in (11, 12)}
+        step = rt.rt_batch_step_create(jobs, total_photons=total)
+        try:
+            # the scenes belong to the step until it is destroyed
+            with pytest.raises(rt.RtError) as e:
+                tA.build_accel(4, 4, 4)
+            assert e.value.code == rt.RT_E_STATE
+            for seed in (11, 12, 11):
+                rt.rt_batch_step_launch(step, seed)
+                for t, (wf, ws) in zip((tA, tB), want[seed]):
+                    f, st = t.fields(split=True), t.stats()
+                    for k in ("photons", "events", "scatters", "crossings", "surface_hits", "roulette_kills"):
+                        assert st[k] == ws[k], (seed, k, st[k], ws[k])
+                    assert st["energy_in"] == ws["energy_in"]
+                    assert closes(st)
+                    for k in FIELDS:
+                        scale = np.abs(wf[k]).max()
+                        assert np.allclose(f[k], wf[k], rtol=1e-12, atol=1e-12 * scale), (seed, k)
+        finally:
+            rt.rt_batch_step_destroy(step)
+        tA.build_accel(4, 4, 4)            # the scene is free again
+    finally:
+        tA.close()
+        tB.close()

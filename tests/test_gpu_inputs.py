@@ -57,7 +57,7 @@ def test_gpu_diffuse_fraction_parity_with_oracle(small_scene):
             o[k].append(getattr(r, k))
     for k in FIELDS:
         rel, se = refs.domain_compare(np.stack(g[k]), np.stack(o[k]))
-        assert abs(rel) < max(0.005, 4 * se), (k, rel, se)
+        assert abs(rel) < 4 * se + 1e-12, (k, rel, se)
 
 
 def test_gpu_paper_optics_inputs(small_scene):
@@ -92,7 +92,7 @@ def test_gpu_paper_optics_inputs(small_scene):
             o[k].append(getattr(r, k))
     for k in FIELDS:
         rel, se = refs.domain_compare(np.stack(g[k]), np.stack(o[k]))
-        assert abs(rel) < max(0.005, 4 * se), (k, rel, se)
+        assert abs(rel) < 4 * se + 1e-12, (k, rel, se)
 
 
 def test_batch_job_with_diffuse_fraction(small_scene):

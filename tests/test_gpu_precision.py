@@ -84,5 +84,5 @@ def test_precision_study_cumulus():
         # differences are what the noise predicts (no structured error)
         assert r["rms"] < 1.3 * r["rms_noise"], (f, r)
     table["closure_residual"] = {"fp64_tally_max": float(np.abs(c64).max()), "fp32_tally_max": float(np.abs(c32).max())}
-    assert np.abs(c64).max() < 2e-6
+    assert np.abs(c64).max() < 1e-9
     print(json.dumps(table, indent=1))

@@ -90,12 +90,11 @@ def test_replay_equals_ordinary_calls_and_follows_updated_optics(small_scene):
         want, wst = ordinary(sc, 30.0, 20.0, 1000.0, rig.photons, 11, (4, 4, 4))
         assert st["events"] == wst["events"] and st["photons"] == rig.photons
         assert_same(got, want)
-        # the energy ledger of the replay closes as an ordinary call's does (the
-        # deposits are scaled to watts in FP32, hence the 2e-6)
+        # the energy ledger of the replay closes as an ordinary call's does
         lhs = st["energy_in"] + st["energy_created"] - st["energy_destroyed"] - st["energy_capped"]
         rhs = st["energy_toa_up"] + st["energy_atm_abs"] + st["energy_sfc_abs"]
         assert st["energy_in"] == wst["energy_in"]
-        assert abs(lhs - rhs) < 2e-6 * st["energy_in"]
+        assert abs(lhs - rhs) < 1e-9 * st["energy_in"]
 
         # the next model step: thicker clouds and a darker surface, written in place
         sc2 = scenes.Scene("step2", sc.nx, sc.ny, sc.nz, sc.dx, sc.dy, sc.dz, sc.k_gas, sc.ssa_gas,

@@ -186,10 +186,10 @@ def test_parity_cellwise_with_oracle(c0_parity, field):
     rep = refs.parity_report(g[field], o[field], pilot=(gp[field], op[field]))
     assert rep["frac_over"] <= rep["bound"], (field, rep["frac_over"], rep["bound"], rep["max_abs_z"])
     assert rep["n"] >= 0.8 * rep["n_total"], (field, rep["n"], rep["n_total"])
-    assert rep["pooled_max_abs_z"] < 4.5, (field, rep["pooled_max_abs_z"])
-    # the standardised differences look like noise (KS against the normal law)
-    z = rep["z"][np.isfinite(rep["z"])]
-    assert stats.kstest(z, "norm").pvalue > 1e-4 or np.std(z) < 1.15, (field, np.std(z))
+    assert rep["pooled_p_family"] >= 1e-3, (field, rep["pooled_max_abs_z"], rep["pooled_p_family"])
+    # the standardised differences are distributed as noise alone makes them
+    # (KS distance of their Welch-t CDF values from the uniform law)
+    assert rep["ks_d"] <= rep["ks_bound"], (field, rep["ks_d"], rep["ks_bound"])
 
 
 @pytest.mark.parametrize("field", FIELDS)
@@ -205,7 +205,7 @@ def test_energy_ledger_closes(c0_parity):
     for s in st:
         lhs = s["energy_in"] + s["energy_created"] - s["energy_destroyed"] - s["energy_capped"]
         rhs = s["energy_toa_up"] + s["energy_atm_abs"] + s["energy_sfc_abs"]
-        assert abs(lhs - rhs) < 2e-6 * s["energy_in"], (lhs, rhs)
+        assert abs(lhs - rhs) < 1e-9 * s["energy_in"], (lhs, rhs)
         assert s["status"] == 0 and s["capped"] == 0
         assert s["photons"] == 2 ** 22
 
@@ -431,7 +431,7 @@ def test_step_cap_sets_budget_status_and_returns(small_scene):
         assert s["capped"] > 0 and s["status"] == rt.RT_E_BUDGET
         lhs = s["energy_in"] + s["energy_created"] - s["energy_destroyed"] - s["energy_capped"]
         rhs = s["energy_toa_up"] + s["energy_atm_abs"] + s["energy_sfc_abs"]
-        assert abs(lhs - rhs) < 2e-6 * s["energy_in"]
+        assert abs(lhs - rhs) < 1e-9 * s["energy_in"]
         t.reset()
         t.set_options(max_steps=0)
         t.trace(30.0, 0.0, 1000.0, 50_000, 1)
@@ -457,7 +457,7 @@ def test_fullsize_cumulus_direct_beam_and_closure(c1_scene):
     for s in st:
         lhs = s["energy_in"] + s["energy_created"] - s["energy_destroyed"] - s["energy_capped"]
         rhs = s["energy_toa_up"] + s["energy_atm_abs"] + s["energy_sfc_abs"]
-        assert abs(lhs - rhs) < 2e-6 * s["energy_in"]
+        assert abs(lhs - rhs) < 1e-9 * s["energy_in"]
         assert s["capped"] == 0
     rng = np.random.default_rng(0)
     cols = rng.choice(sc.ncol, 256, replace=False)
@@ -476,11 +476,80 @@ def test_fullsize_cumulus_direct_beam_and_closure(c1_scene):
     assert abs(m.mean() / want.mean() - 1) < 0.005
 
 
-def test_fullsize_cumulus_domain_means_match_oracle(c1_scene):
+# --- parity with the oracle on the full 256x256x128 cumulus scene -------------------
+
+# the benchmark's launch configuration (majorant boxes on a 2x2x2 grid)
+C1_LAUNCH = dict(ready_threshold=16, max_inner=64, refill_chunk=128)
+C1_PPC, C1_B, C1_PILOT = 64, 16, 8
+
+
+@pytest.fixture(scope="module")
+def c1_parity(c1_scene):
+    """Streamed per-cell moments of 16 GPU and 16 oracle batches of 64 photons
+    per column (4.2 M photons each), and the cells that independent pilots (8
+    batches a side) find well sampled."""
     sc = c1_scene
-    N = sc.ncol
-    g, _ = gpu_batches(sc, 30.0, 0.0, 1000.0, 4 * N, range(8))
-    o = oracle_batches(sc, 30.0, 0.0, 1000.0, N, range(900, 916))
-    for f in FIELDS:
-        rel, se = refs.domain_compare(g[f], o[f])
-        assert abs(rel) < max(0.005, 4 * se), (f, rel, se)
+    N = C1_PPC * sc.ncol
+    cnt_g = {f: 0 for f in FIELDS}
+    cnt_o = {f: 0 for f in FIELDS}
+    with rt.Tracer.from_scene(sc, 2, 2, 2, **C1_LAUNCH) as t:
+        for s in range(C1_PILOT):
+            t.reset()
+            t.trace(30.0, 0.0, 1000.0, N, 7000 + s)
+            f = t.fields(split=True)
+            for k in FIELDS:
+                cnt_g[k] = cnt_g[k] + (f[k] != 0)
+        for s in range(C1_PILOT):
+            r = oracle.trace(sc, 30.0, 0.0, 1000.0, N, 8000 + s)
+            for k in FIELDS:
+                cnt_o[k] = cnt_o[k] + (getattr(r, k) != 0)
+        good = {k: (cnt_g[k] >= 0.9 * C1_PILOT) & (cnt_o[k] >= 0.9 * C1_PILOT) for k in FIELDS}
+        mg = {k: refs.BatchMoments(~good[k]) for k in FIELDS}
+        mo = {k: refs.BatchMoments(~good[k]) for k in FIELDS}
+        stats_list = []
+        for s in range(C1_B):
+            t.reset()
+            t.trace(30.0, 0.0, 1000.0, N, 7100 + s)
+            f = t.fields(split=True)
+            for k in FIELDS:
+                mg[k].add(f[k])
+            stats_list.append(t.stats())
+    for s in range(C1_B):
+        r = oracle.trace(sc, 30.0, 0.0, 1000.0, N, 8100 + s)
+        for k in FIELDS:
+            mo[k].add(getattr(r, k))
+    return good, mg, mo, stats_list
+
+
+@pytest.mark.parametrize("field", FIELDS)
+def test_fullsize_parity_cellwise_with_oracle(c1_parity, field):
+    """Cell-wise parity on the full scene (8.4 M cells), where the majorant
+    boxes, the launch order and L2 eviction all act: the same criterion as on
+    the 32^3 scene."""
+    good, mg, mo, _ = c1_parity
+    rep = refs.parity_from_moments(mg[field], mo[field], good[field])
+    assert rep["frac_over"] <= rep["bound"], (field, rep["frac_over"], rep["bound"], rep["max_abs_z"])
+    assert rep["pooled_p_family"] >= 1e-3, (field, rep["pooled_max_abs_z"], rep["pooled_p_family"])
+    assert rep["ks_d"] <= rep["ks_bound"], (field, rep["ks_d"], rep["ks_bound"])
+    assert rep["n"] > 0
+
+
+@pytest.mark.parametrize("field", FIELDS)
+def test_fullsize_domain_means_within_half_percent(c1_parity, field):
+    """Domain means within 0.5 % of the oracle's, with enough oracle photons
+    (16 x 4.2 M) that 4 standard errors stay well below that."""
+    _, mg, mo, _ = c1_parity
+    rep = refs.domain_from_moments(mg[field], mo[field])
+    assert 4 * rep["domain_rel_se"] < 0.005, (field, rep["domain_rel_se"])
+    assert abs(rep["domain_rel"]) < 0.005, (field, rep["domain_rel"])
+    assert abs(rep["domain_rel"]) < 4 * rep["domain_rel_se"] + 1e-12, (field, rep["domain_rel"], rep["domain_rel_se"])
+
+
+def test_fullsize_ledger_closes(c1_parity):
+    for st in c1_parity[3]:
+        lhs = st["energy_in"] + st["energy_created"] - st["energy_destroyed"] - st["energy_capped"]
+        rhs = st["energy_toa_up"] + st["energy_atm_abs"] + st["energy_sfc_abs"]
+        assert abs(lhs - rhs) < 1e-9 * st["energy_in"], (lhs - rhs) / st["energy_in"]
+        assert st["status"] == 0 and st["capped"] == 0
+
+

@@ -24,8 +24,9 @@ def test_criterion_passes_for_independent_oracle_runs(small_scene):
     for f in oracle.FIELDS:
         rep = refs.parity_report(a[f], b[f], pilot=(pa[f], pb[f]))
         assert rep["frac_over"] <= rep["bound"], (f, rep["frac_over"], rep["bound"])
-        assert rep["pooled_max_abs_z"] < 4.5, (f, rep["pooled_max_abs_z"])
+        assert rep["pooled_p_family"] >= 1e-3, (f, rep["pooled_max_abs_z"], rep["pooled_p_family"])
         assert abs(rep["domain_rel"]) < 4 * rep["domain_rel_se"] + 1e-12
+        assert rep["ks_d"] <= rep["ks_bound"], (f, rep["ks_d"], rep["ks_bound"])
 
 
 def test_criterion_catches_a_planted_error(small_scene):
@@ -39,3 +40,7 @@ def test_criterion_catches_a_planted_error(small_scene):
     pb = _batches(wrong, range(4100, 4104), 2 ** 15)
     rep = refs.parity_report(a["sfc_dif"], b["sfc_dif"], pilot=(pa["sfc_dif"], pb["sfc_dif"]))
     assert rep["frac_over"] > rep["bound"] or abs(rep["domain_rel"]) > 4 * rep["domain_rel_se"]
+    # each criterion alone also catches it
+    assert rep["ks_d"] > rep["ks_bound"], (rep["ks_d"], rep["ks_bound"])
+    rep3 = refs.parity_report(a["abs_dif"], b["abs_dif"], pilot=(pa["abs_dif"], pb["abs_dif"]))
+    assert rep3["frac_over"] > rep3["bound"] and rep3["ks_d"] > rep3["ks_bound"]
