@@ -38,20 +38,39 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, ui
     return c;
 }
 
-// Uniform float in the open interval (0,1): the top 24 bits plus one half, so
-// -log(u) is always finite.
-__device__ __forceinline__ float u01(uint32_t x)
+// Uniform float in the open interval (0,1) from the top 23 bits m of a word:
+// the float 1 + m 2^-23 (those bits as its mantissa) minus 1 - 2^-24 is
+// exactly (m + 1/2) 2^-23, so -log(u) is always finite. Integer and add
+// instructions only, no int-to-float conversion.
+__device__ __forceinline__ float u01_bits23(uint32_t m)
 {
-    return (static_cast<float>(x >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    return __uint_as_float(0x3F800000u | m) - 0.99999994039535522461f;
 }
 
-// A fifth uniform from one Philox block: the low 8 bits of words 0, 1 and 2,
-// which u01 discards. The bits of a uniformly random word are independent, so
-// this is independent of the four uniforms taken from the top bits.
+__device__ __forceinline__ float u01(uint32_t x) { return u01_bits23(x >> 9); }
+
+// A fifth uniform from one Philox block: the low 9 bits of words 0 and 1 and
+// the low 5 of word 2 (23 bits), which u01 discards. The bits of a uniformly
+// random word are independent, so this is independent of the four uniforms
+// taken from the top bits.
 __device__ __forceinline__ float u01_low(uint4 r)
 {
-    const uint32_t v = (r.x & 0xFFu) | ((r.y & 0xFFu) << 8) | ((r.z & 0xFFu) << 16);
-    return (static_cast<float>(v) + 0.5f) * 5.9604644775390625e-8f;
+    return u01_bits23((r.x & 0x1FFu) | ((r.y & 0x1FFu) << 9) | ((r.z & 0x1Fu) << 18));
+}
+
+// (float)i for |i| < 2^22 with an integer add and a float subtract (no
+// conversion instruction): i added to the bits of 1.5 * 2^23 gives the float
+// 1.5 * 2^23 + i exactly, since floats of that binade are spaced by 1.
+__device__ __forceinline__ float small_int_to_float(int i)
+{
+    return __int_as_float(0x4B400000 + i) - 12582912.0f;
+}
+
+// sqrt(x) for x >= 0 from the reciprocal square root (a few units in the last
+// place; 0 maps to 0): shorter than the correctly rounded square root.
+__device__ __forceinline__ float sqrt_fast(float x)
+{
+    return x * rsqrtf(fmaxf(x, 1e-30f));
 }
 
 // ---------------------------------------------------------------------------
@@ -97,7 +116,7 @@ __device__ __forceinline__ float rayleigh_mu(float xi)
 {
     const float a = 4.0f * xi - 2.0f;
     const float t = fabsf(a);
-    const float c = __powf(t + sqrtf(fmaf(t, t, 1.0f)), 0.333333343f);
+    const float c = __powf(t + sqrt_fast(fmaf(t, t, 1.0f)), 0.333333343f);
     return copysignf(c - __fdividef(1.0f, c), a);
 }
 
@@ -126,7 +145,7 @@ __device__ __forceinline__ void azimuth(float xi, float &sp, float &cp)
 // e2 = (-uy, ux, 0)/sqrt(1-uz^2); renormalised against FP32 drift.
 __device__ __forceinline__ void turn(float &ux, float &uy, float &uz, float mu, float sp, float cp)
 {
-    const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+    const float st = sqrt_fast(fmaxf(0.0f, 1.0f - mu * mu));
     float nx, ny, nz;
     const float q = 1.0f - uz * uz;
     if (q > 1e-10f) {
@@ -149,8 +168,8 @@ __device__ __forceinline__ void turn(float &ux, float &uy, float &uz, float mu, 
 // Lambertian (cosine-law) reflection into the upper hemisphere (Sec. 2.3).
 __device__ __forceinline__ void lambert_up(float &ux, float &uy, float &uz, float xi_mu, float xi_phi)
 {
-    const float mu = sqrtf(xi_mu);
-    const float st = sqrtf(fmaxf(0.0f, 1.0f - xi_mu));
+    const float mu = sqrt_fast(xi_mu);
+    const float st = sqrt_fast(fmaxf(0.0f, 1.0f - xi_mu));
     float sp, cp;
     azimuth(xi_phi, sp, cp);
     ux = st * cp;

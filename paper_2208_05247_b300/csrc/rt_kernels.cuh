@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 #include <utility>
 
 #include <cuda_runtime.h>
@@ -634,23 +635,29 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
     bool pdir = false;
     float pacc = 0.f;
 
-    auto load_box = [&]() {
-        const int q = (K * RT_SC(NY) + J) * RT_SC(NX) + I;
+    using BoxWord = typename std::conditional<BATCH, uint2, uint32_t>::type;
+    auto set_box = [&](BoxWord b) {
         if constexpr (BATCH) {
-            const uint2 b = __ldg(RT_SC(box2) + q);
             r = box_radius(b.x);
             kmaj = fmaf(RT_JB(gas_scale), box_kmaj(b.x), box_kmaj(b.y));
         } else {
-            const uint32_t b = __ldg(RT_SC(box) + q);
             r = box_radius(b);
             kmaj = box_kmaj(b);
         }
     };
-    // coarse cell of a position inside the periodic domain
-    auto locate = [&](float px, float py, float pz) {
-        I = min(max((int)(px * RT_SC(inv_cdx)), 0), RT_SC(NX) - 1);
-        J = min(max((int)(py * RT_SC(inv_cdy)), 0), RT_SC(NY) - 1);
-        K = min(max((int)(pz * RT_SC(inv_cdz)), 0), RT_SC(NZ) - 1);
+    // coarse cell of a position inside the periodic domain (cell_of: its
+    // index only; locate: make it the walk's current cell)
+    auto cell_of = [&](float px, float py, float pz, int &i, int &j, int &k) {
+        i = min(max((int)(px * RT_SC(inv_cdx)), 0), RT_SC(NX) - 1);
+        j = min(max((int)(py * RT_SC(inv_cdy)), 0), RT_SC(NY) - 1);
+        k = min(max((int)(pz * RT_SC(inv_cdz)), 0), RT_SC(NZ) - 1);
+        return (k * RT_SC(NY) + j) * RT_SC(NX) + i;
+    };
+    auto locate = [&](float px, float py, float pz) { cell_of(px, py, pz, I, J, K); };
+    auto load_box = [&]() {
+        const int q = (K * RT_SC(NY) + J) * RT_SC(NX) + I;
+        if constexpr (BATCH) set_box(__ldg(RT_SC(box2) + q));
+        else set_box(__ldg(RT_SC(box) + q));
     };
     auto set_recip = [&]() {
         ivx = __fdividef(1.0f, ux);
@@ -797,9 +804,9 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
             const int ex = ux > 0.f ? I + r + 1 : I - r;
             const int ey = uy > 0.f ? J + r + 1 : J - r;
             const int ez = uz > 0.f ? min(K + r + 1, NZ) : max(K - r, 0);
-            const float fx = fminf((float)ex * RT_SC(cdx), RT_SC(xcap));
-            const float fy = fminf((float)ey * RT_SC(cdy), RT_SC(ycap));
-            const float fz = fminf((float)ez * RT_SC(cdz), RT_SC(H));
+            const float fx = fminf(small_int_to_float(ex) * RT_SC(cdx), RT_SC(xcap));
+            const float fy = fminf(small_int_to_float(ey) * RT_SC(cdy), RT_SC(ycap));
+            const float fz = fminf(small_int_to_float(ez) * RT_SC(cdz), RT_SC(H));
             const float tx = ux != 0.f ? (fx - ox) * ivx : INFINITY;
             const float ty = uy != 0.f ? (fy - oy) * ivy : INFINITY;
             const float tz = uz != 0.f ? (fz - oz) * ivz : INFINITY;
@@ -866,6 +873,21 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
             }
             const int fi = min(max((int)(px * RT_SC(inv_dx)), 0), nx - 1);
             const int fj = min(max((int)(py * RT_SC(inv_dy)), 0), ny - 1);
+            int cell = (min(max((int)(pz * RT_SC(inv_dz)), 0), RT_SC(nz) - 1) * ny + fj) * nx + fi;
+            // Both gathers of this pass are issued before the Philox block so
+            // that their latencies overlap it and each other: the optics of the
+            // event cell (record mode; a surface hit loads layer 0 and ignores
+            // it) and the box word of the coarse cell the next walk starts in,
+            // decoded after the event, whose acceptance uses the current box.
+            float4 orec;
+            if constexpr (MODE == kOpticsRecord) orec = __ldg(RT_SC(rec) + cell);
+            BoxWord bnext;
+            {
+                int i, j, k;
+                const int q = cell_of(px, py, pz, i, j, k);
+                if constexpr (BATCH) bnext = __ldg(RT_SC(box2) + q);
+                else bnext = __ldg(RT_SC(box) + q);
+            }
             const uint4 rn = philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), blk, 0u),
                                            RT_JB(key0), RT_JB(key1));
             ++blk;
@@ -873,12 +895,10 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
             float mu = 0.f;
             if (!sfc) {
                 // ---- a5: majorant event at distance tau, inside the box ----
-                int cell = (min(max((int)(pz * RT_SC(inv_dz)), 0), RT_SC(nz) - 1) * ny + fj) * nx + fi;
                 float kabs, ksca, kscl;   // absorption, scattering, scattering by cloud
                 auto optics = [&]() {
                     if constexpr (MODE == kOpticsRecord) {
-                        const float4 o = __ldg(RT_SC(rec) + cell);
-                        kabs = o.x; ksca = o.y; kscl = o.z;
+                        kabs = orec.x; ksca = orec.y; kscl = orec.z;
                     } else if constexpr (MODE == kOpticsSplit) {
                         const float4 o = __ldg(RT_SC(rec) + cell);
                         const float s = RT_JB(gas_scale);
@@ -911,6 +931,7 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
                     const int gk = min(max((int)(pz * RT_SC(inv_dz)), max(K - r, 0) * cz),
                                        min((K + r + 1) * cz, RT_SC(nz)) - 1);
                     cell = (gk * ny + gj) * nx + gi;
+                    if constexpr (MODE == kOpticsRecord) orec = __ldg(RT_SC(rec) + cell);
                     optics();
                 }
                 // the weight splits exactly into the deposit and what goes on
@@ -937,7 +958,7 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
                     const bool cloud = xd < kscl;
                     float g = 0.f;
                     if (cloud) {
-                        if constexpr (MODE == kOpticsRecord) g = __ldg(RT_SC(rec) + cell).w;
+                        if constexpr (MODE == kOpticsRecord) g = orec.w;
                         else g = __ldg(RT_SC(gcl) + cell);
                     }
                     const float xi = u01(rn.y), mh = hg_mu(g, xi), mr = rayleigh_mu(xi);
@@ -960,8 +981,8 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
                 float sp, cp;
                 azimuth(u01(rn.z), sp, cp);
                 if (sfc) {
-                    const float xi = u01(rn.y), st = sqrtf(1.0f - xi);
-                    ux = st * cp; uy = st * sp; uz = sqrtf(xi);
+                    const float xi = u01(rn.y), st = sqrt_fast(1.0f - xi);
+                    ux = st * cp; uy = st * sp; uz = sqrt_fast(xi);
                 } else {
                     turn(ux, uy, uz, mu, sp, cp);
                 }
@@ -969,8 +990,8 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
             }
             tau = -__logf(u01(rn.w));
             ox = px; oy = py; oz = pz;
-            locate(px, py, pz);
-            load_box();
+            locate(px, py, pz);       // the cell of that box word, recomputed
+            set_box(bnext);
             // ---- a8: roulette, with the fifth uniform of the block ----
             if (w < 0.5f && roulette(u01_low(rn))) {
                 end_photon();
