@@ -114,3 +114,53 @@ def grid(**axes):
     keys = list(axes)
     for vals in itertools.product(*axes.values()):
         yield dict(zip(keys, vals))
+
+
+def launch_times(tracer, sza, az, flux, ppcs, seed=77, repeats=3):
+    """Launch time against photons per column (best of `repeats`, after one
+    warm-up launch), with the launch's events and its longest history: how
+    the fixed cost of a launch (its longest random walks) and the per-photon
+    rate share the time. Rows of dicts."""
+    import torch
+    stream = torch.cuda.current_stream()
+    tracer.set_stream(stream)
+    ncol = tracer.nx * tracer.ny
+    rows = []
+    for ppc in ppcs:
+        best = None
+        for r in range(repeats + 1):
+            tracer.reset()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tracer.trace(sza, az, flux, ppc * ncol, seed + r)
+            b.record(stream)
+            b.synchronize()
+            if r > 0:
+                ms = a.elapsed_time(b)
+                best = ms if best is None else min(best, ms)
+        st = tracer.stats()
+        rows.append({"ppc": ppc, "ms": best, "photons_per_s": ppc * ncol / (best / 1e3), "events": st["events"],
+                     "max_events_photon": st["max_events_photon"]})
+    return rows
+
+
+def main(argv=None):
+    """Launch-time sweep on the 256x256x128 cumulus scene at the bench's launch shape."""
+    import argparse
+    import json
+    from paper_2208_05247_b300 import build, rt, scenes
+    p = argparse.ArgumentParser(description=main.__doc__)
+    p.add_argument("--sweep-ppc", type=int, nargs="+", default=[1, 4, 16, 64, 128, 256, 512, 1024, 2048])
+    p.add_argument("--coarse", type=int, nargs=3, default=(2, 2, 2))
+    p.add_argument("--launch", type=int, nargs=3, default=(16, 64, 128), metavar=("READY", "INNER", "CHUNK"))
+    a = p.parse_args(argv)
+    build.build()
+    sc = scenes.cumulus_scene(seed=1)
+    with rt.Tracer.from_scene(sc, *a.coarse, ready_threshold=a.launch[0], max_inner=a.launch[1],
+                              refill_chunk=a.launch[2]) as t:
+        for row in launch_times(t, 30.0, 0.0, 1000.0, a.sweep_ppc):
+            print(json.dumps(row), flush=True)
+
+
+if __name__ == "__main__":
+    main()

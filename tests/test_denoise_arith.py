@@ -38,3 +38,23 @@ def test_time_fit_is_least_squares():
     A = np.stack([np.ones(len(PPC)), np.array(PPC, float)], 1)
     want = np.linalg.lstsq(A, np.array(ms), rcond=None)[0]
     assert np.allclose([t0, t1], want, rtol=1e-10, atol=1e-12)
+
+
+def test_truth_noise_term():
+    """Errors against a noisy truth of Nt photons/column: rmse^2 =
+    a^2 (1/p + 1/Nt) for plain runs. The prefactor and the match are then
+    recovered exactly, and the match lies beyond the naive a/sqrt(p) one
+    (part of the measured target error is the truth's own noise)."""
+    a, nt = 331.0, 16384
+    rmse = [a * math.sqrt(1.0 / p + 1.0 / nt) for p in PPC]
+    for n_true in (100.0, 1810.0, 8000.0):
+        target = a * math.sqrt(1.0 / n_true + 1.0 / nt)      # a run of n_true photons, measured the same way
+        got = denoise.plain_ppc_to_match(PPC, rmse, target, truth_ppc=nt)
+        assert math.isclose(got, n_true, rel_tol=1e-9)
+        if n_true > 1000:    # where the truth's noise is a visible part of the target error
+            assert got > 1.08 * denoise.plain_ppc_to_match(PPC, rmse, target)
+    # at or below the truth's noise floor no plain run can be matched
+    assert denoise.plain_ppc_to_match(PPC, rmse, a / math.sqrt(nt), truth_ppc=nt) == math.inf
+    # the noise-free-truth limit is the plain a / sqrt(p) model
+    assert math.isclose(denoise.plain_ppc_to_match(PPC, [a / math.sqrt(p) for p in PPC], 8.0, truth_ppc=None),
+                        (a / 8.0) ** 2, rel_tol=1e-12)
