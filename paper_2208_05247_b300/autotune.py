@@ -13,6 +13,8 @@ from __future__ import annotations
 
 import itertools
 
+import numpy as np
+
 
 COARSE = [(2, 2, 2), (2, 2, 1), (4, 4, 2), (4, 4, 4), (8, 8, 4), (8, 8, 8)]
 BOX_LEVELS = [0, 2, 3, 4]
@@ -144,8 +146,60 @@ def launch_times(tracer, sza, az, flux, ppcs, seed=77, repeats=3):
     return rows
 
 
+def optics_layouts(scene, ppc=256, coarse=(2, 2, 2), repeats=3, seed=91):
+    """The transport kernel on the two optics layouts, same photons and launch
+    shape (refill chunk 32, ready threshold 16, 16 walk sweeps, photon-id order):
+
+    - packed record: `rt_trace` on a handle, one float4 {k_abs, k_sca,
+      k_sca P(cloud), g} per event, derived once per rt_set_optics;
+    - SoA fields: `rt_trace_noalloc`, the same kernel reading the five input
+      arrays (k_gas, ssa_gas, k_cld, ssa_cld, then g for cloud scatterings)
+      and deriving the optics at every event.
+
+    Each time (CUDA events, best of `repeats` after a warm-up) covers the
+    majorant and box build plus the trace, as both calls do them; the event
+    counts must agree (the histories are the same)."""
+    import torch
+    from paper_2208_05247_b300 import rt
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda")
+    f = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in scene.fields()]
+    alb = torch.from_numpy(scene.albedo).to(dev)
+    out = [torch.zeros(scene.ncell, dtype=torch.float64, device=dev) for _ in range(2)] + \
+          [torch.zeros(scene.ncol, dtype=torch.float64, device=dev) for _ in range(3)]
+    n = ppc * scene.ncol
+
+    def timed(fn):
+        best, res = None, None
+        for r in range(repeats + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res = fn(r)
+            b.record(stream)
+            b.synchronize()
+            if r > 0:
+                ms = a.elapsed_time(b)
+                best = ms if best is None else min(best, ms)
+        return best, res
+
+    # photon-id order on both sides (the no-allocation call has no launch-order table)
+    with rt.Tracer.from_scene(scene, *coarse, stream=stream, ready_threshold=16, max_inner=16,
+                              refill_chunk=32, schedule=0) as t:
+        def packed(r):
+            t.reset()
+            t.build_accel(*coarse)
+            t.trace(30.0, 0.0, 1000.0, n, seed)
+            return t.stats()["events"]
+        ms_rec, ev_rec = timed(packed)
+    ms_soa, ev_soa = timed(lambda r: rt.rt_trace_noalloc(scene.nx, scene.ny, scene.nz, scene.dx, scene.dy, scene.dz,
+                                                        *f, alb, 30.0, 0.0, 1000.0, n, seed, *out, coarse=coarse,
+                                                        stream=stream))
+    return {"photons": n, "coarse": list(coarse), "packed_record": {"ms": ms_rec, "events": ev_rec},
+            "soa_fields": {"ms": ms_soa, "events": ev_soa}, "same_histories": ev_rec == ev_soa}
+
+
 def main(argv=None):
-    """Launch-time sweep on the 256x256x128 cumulus scene at the bench's launch shape."""
+    """Launch-time sweep (or the optics-layout comparison) on the 256x256x128 cumulus scene."""
     import argparse
     import json
     from paper_2208_05247_b300 import build, rt, scenes
@@ -153,9 +207,14 @@ def main(argv=None):
     p.add_argument("--sweep-ppc", type=int, nargs="+", default=[1, 4, 16, 64, 128, 256, 512, 1024, 2048])
     p.add_argument("--coarse", type=int, nargs=3, default=(2, 2, 2))
     p.add_argument("--launch", type=int, nargs=3, default=(16, 64, 128), metavar=("READY", "INNER", "CHUNK"))
+    p.add_argument("--layouts", action="store_true",
+                   help="time the packed optics record against the SoA input fields instead")
     a = p.parse_args(argv)
     build.build()
     sc = scenes.cumulus_scene(seed=1)
+    if a.layouts:
+        print(json.dumps(optics_layouts(sc, coarse=tuple(a.coarse))), flush=True)
+        return
     with rt.Tracer.from_scene(sc, *a.coarse, ready_threshold=a.launch[0], max_inner=a.launch[1],
                               refill_chunk=a.launch[2]) as t:
         for row in launch_times(t, 30.0, 0.0, 1000.0, a.sweep_ppc):
