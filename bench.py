@@ -555,6 +555,10 @@ def run_ours(args):
             "traffic": profiled_traffic(), "peak_source": peak_src,
             "kernel": "trace_kernel<double>", "kernel_ms": 1e3 * tk,
             "algorithmic_bytes_per_launch": alg_bytes, "events_per_launch": events, "box_steps_per_launch": crossings,
+            # the same launch at sector granularity (a random 16-byte gather, an
+            # 8-byte tally update and a 4-byte box word each move a 32-byte sector)
+            "sector_bytes_per_launch": events * 64 + crossings * 32,
+            "sector_frac": (events * 64 + crossings * 32) / tk / 1e9 / peak,
             "photons_per_s": N * world * args.steps / (ms_max / 1e3)}
     # the same algorithmic bytes against this GPU's L2 read bandwidth, measured
     # here (outside the timed region) by the library's read probe: the
