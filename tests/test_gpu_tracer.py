@@ -313,6 +313,47 @@ def test_partition_invariance(small_scene):
     assert np.isclose(sf["energy_in"], sp["energy_in"], rtol=1e-14)
 
 
+def test_photon_ids_beyond_2_32(small_scene):
+    """Photon ids that cross 2^32 (the kernel's 64-bit id, column and launch-
+    order arithmetic), with the thick-first schedule engaged (whole rounds of
+    >= 64 photons per column): one call over the range equals two calls over
+    its halves, and the domain means match the oracle's over the same ids."""
+    sc = small_scene
+    ncol = sc.ncol
+    B = (1 << 32) - 96 * ncol            # a multiple of ncol; the range crosses 2^32
+    n = 192 * ncol
+    total = B + n
+    with rt.Tracer.from_scene(sc) as t:
+        t.trace_range(30.0, 0.0, 1000.0, B, n, total, 5)
+        full, sf = t.fields(split=True), t.stats()
+    with rt.Tracer.from_scene(sc) as t:
+        t.trace_range(30.0, 0.0, 1000.0, B, n // 2, total, 5)
+        t.trace_range(30.0, 0.0, 1000.0, B + n // 2, n // 2, total, 5)
+        part, sp = t.fields(split=True), t.stats()
+    for k in ("photons", "events", "scatters", "crossings"):
+        assert sf[k] == sp[k], k
+    for k in FIELDS:
+        assert np.allclose(full[k], part[k], rtol=1e-12, atol=1e-12 * np.abs(full[k]).max())
+    # statistics: 8 disjoint sub-ranges a side, each normalised by the whole range
+    g, o = {k: [] for k in FIELDS}, {k: [] for k in FIELDS}
+    m = n // 8
+    with rt.Tracer.from_scene(sc) as t:
+        for i in range(8):
+            t.reset()
+            t.trace_range(30.0, 0.0, 1000.0, B + i * m, m, B + 8 * m, 5)
+            f = t.fields(split=True)
+            for k in FIELDS:
+                g[k].append(8 * f[k].sum())
+    for i in range(8):
+        r = oracle.trace(sc, 30.0, 0.0, 1000.0, m, 17, id_begin=B + i * m, photons_total=B + 8 * m)
+        for k in FIELDS:
+            o[k].append(8 * getattr(r, k).sum())
+    for k in FIELDS:
+        a, b = np.array(g[k]), np.array(o[k])
+        se = np.sqrt(a.var(ddof=1) / a.size + b.var(ddof=1) / b.size)
+        assert abs(a.mean() - b.mean()) < 4 * se + 1e-12 * abs(b.mean()), (k, a.mean(), b.mean(), se)
+
+
 def test_coarse_factors_do_not_change_the_expectation(small_scene):
     """Any majorant grid (1x1x1 up to one coarse cell per axis) is unbiased."""
     res = {}
@@ -543,6 +584,39 @@ def test_fullsize_domain_means_within_half_percent(c1_parity, field):
     assert 4 * rep["domain_rel_se"] < 0.005, (field, rep["domain_rel_se"])
     assert abs(rep["domain_rel"]) < 0.005, (field, rep["domain_rel"])
     assert abs(rep["domain_rel"]) < 4 * rep["domain_rel_se"] + 1e-12, (field, rep["domain_rel"], rep["domain_rel_se"])
+
+
+@pytest.mark.parametrize("sza", [0.0, 60.0])
+def test_fullsize_domain_means_at_other_sun_angles(c1_scene, sza):
+    """The full scene at the other two sun angles of the workload, bench launch
+    shape, 8 + 8 batches of 64 photons per column: every field's domain mean
+    within 0.5 % of the oracle's and within 4 combined SE, the SE small enough
+    for the 0.5 % bound to mean something, and the ledger closed."""
+    sc = c1_scene
+    N = C1_PPC * sc.ncol
+    B = 8
+    tg, to = {f: [] for f in FIELDS}, {f: [] for f in FIELDS}
+    with rt.Tracer.from_scene(sc, 2, 2, 2, **C1_LAUNCH) as t:
+        for s in range(B):
+            t.reset()
+            t.trace(sza, 0.0, 1000.0, N, 7300 + s)
+            f = t.fields(split=True)
+            for k in FIELDS:
+                tg[k].append(f[k].sum())
+            st = t.stats()
+            lhs = st["energy_in"] + st["energy_created"] - st["energy_destroyed"] - st["energy_capped"]
+            rhs = st["energy_toa_up"] + st["energy_atm_abs"] + st["energy_sfc_abs"]
+            assert abs(lhs - rhs) < 1e-9 * st["energy_in"] and st["status"] == 0
+    for s in range(B):
+        r = oracle.trace(sc, sza, 0.0, 1000.0, N, 8300 + s)
+        for k in FIELDS:
+            to[k].append(getattr(r, k).sum())
+    for k in FIELDS:
+        a, b = np.array(tg[k]), np.array(to[k])
+        rel = (a.mean() - b.mean()) / b.mean()
+        se = np.sqrt(a.var(ddof=1) / B + b.var(ddof=1) / B) / abs(b.mean())
+        assert 4 * se < 0.005, (k, sza, se)
+        assert abs(rel) < 0.005 and abs(rel) < 4 * se + 1e-12, (k, sza, rel, se)
 
 
 def test_fullsize_ledger_closes(c1_parity):
