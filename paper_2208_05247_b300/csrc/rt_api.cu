@@ -125,6 +125,11 @@ struct rt_scene {
     rt::Scratch *scr = nullptr;
     int *bad = nullptr;
     rt::Scratch *host_scr = nullptr;   // pinned
+    // status flags read back without the copy engines: a one-thread kernel
+    // stores them into this mapped pinned word pair (a small device-to-host
+    // copy would queue behind any large copy in flight, e.g. a caller's
+    // output copy on another stream)
+    int *flag_host = nullptr, *flag_dev = nullptr;
 
     bool optics_ok = false, surface_ok = false, accel_ok = false;
     double energy_in = 0.0;
@@ -209,12 +214,17 @@ int copy_in(rt_handle h, float *dst, const float *src, size_t n, int mem)
     return RT_OK;
 }
 
-int read_bad(rt_handle h, int *bad)
+// The device word src, read on the host after the handle's stream reaches it.
+int read_flag(rt_handle h, const int *src, int *value)
 {
-    RT_CUDA(cudaMemcpyAsync(bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    rt::store_flag<<<1, 1, 0, h->stream>>>(src, h->flag_dev);
+    RT_CUDA(cudaGetLastError());
     RT_CUDA(cudaStreamSynchronize(h->stream));
+    *value = *reinterpret_cast<volatile int *>(h->flag_host);
     return RT_OK;
 }
+
+int read_bad(rt_handle h, int *bad) { return read_flag(h, h->bad, bad); }
 
 // Copy n doubles from device src to dst (host or device) on the handle's stream.
 int copy_out(rt_handle h, double *dst, const double *src, size_t n, int mem)
@@ -340,8 +350,8 @@ void set_order(rt_handle h, rt::TraceArgs<T> &A, uint64_t begin, uint64_t count)
 int device_status(rt_handle h)
 {
     int st = 0;
-    RT_CUDA(cudaMemcpyAsync(&st, &h->scr->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    RT_CUDA(cudaStreamSynchronize(h->stream));
+    int rc = read_flag(h, &h->scr->status, &st);
+    if (rc) return rc;
     if (st & rt::kStatusInput)
         return fail(RT_E_INVAL, "the last rt_step launch found an invalid optical property or albedo "
                                 "in its inputs and traced nothing");
@@ -790,7 +800,9 @@ rt_handle rt_create(int nx, int ny, int nz, double dx, double dy, double dz)
         (rc = dev_alloc(&h->t64, tally_len(h))) || (rc = dev_alloc(&h->scr, 1)) ||
         (rc = dev_alloc(&h->bad, 1)) || (rc = dev_alloc(&h->hr_factor, (size_t)nz)))
         return bail(rc);
-    if (cudaMallocHost(reinterpret_cast<void **>(&h->host_scr), sizeof(rt::Scratch)) != cudaSuccess) {
+    if (cudaMallocHost(reinterpret_cast<void **>(&h->host_scr), sizeof(rt::Scratch)) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void **>(&h->flag_host), 2 * sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&h->flag_dev), h->flag_host, 0) != cudaSuccess) {
         fail(RT_E_OOM, "rt_create: pinned allocation failed");
         return bail(RT_E_OOM);
     }
@@ -849,6 +861,7 @@ int rt_destroy(rt_handle h)
     cudaFree(h->scr);
     cudaFree(h->bad);
     if (h->host_scr) cudaFreeHost(h->host_scr);
+    if (h->flag_host) cudaFreeHost(h->flag_host);
     delete h;
     return RT_OK;
 }

@@ -1046,6 +1046,13 @@ __global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ T
 #undef RT_SC
 #undef RT_JB
 
+// One device word into mapped pinned host memory (status reads that must not
+// wait behind copies on the copy engines).
+__global__ void store_flag(const int *__restrict__ src, int *dst)
+{
+    *reinterpret_cast<volatile int *>(dst) = *src;
+}
+
 // ---------------------------------------------------------------------------
 // a12: FP64 normalisation and output fields. Tallies already hold W m^-3 and
 // W m^-2 (the per-call photon energy is applied when they are accumulated).
