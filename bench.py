@@ -67,6 +67,7 @@ def parse():
     p.add_argument("--no-coupled", action="store_true", help="skip the graph-replay coupled-step leg")
     p.add_argument("--no-birth", action="store_true", help="skip the Sobol-vs-Philox start position leg")
     p.add_argument("--no-batched", action="store_true", help="skip the batched multi-scene workload leg")
+    p.add_argument("--no-sweep", action="store_true", help="skip the sun-angle x photons-per-column sweep")
     p.add_argument("--denoise-train", type=int, default=512, help="training scenes of the denoiser leg")
     p.add_argument("--denoise-eval", type=int, default=64, help="held-out scenes of the denoiser leg")
     p.add_argument("--no-l2-probe", action="store_true", help="skip the L2 read-bandwidth probe")
@@ -223,6 +224,38 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                     "photons_per_s": photons / secs}}
     print(json.dumps(line), flush=True)
+
+
+# ---- the full config-1 grid: sun angles x photons per column ------------------------------
+
+def sweep_leg(t, coarse):
+    """Transport on the benchmark scene at every sun angle and photon count of
+    the workload (SZA 0, 30, 60 x 1, 4, 16, 64, 256 photons/column): CUDA-event
+    time of one trace (best of 3 after a warm-up), photons/s and majorant
+    events/s. The tracer keeps the bench's launch configuration."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ncol = t.nx * t.ny
+    rows = []
+    for sza in (0.0, 30.0, 60.0):
+        for ppc in (1, 4, 16, 64, 256):
+            best = None
+            for r in range(4):
+                t.reset()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                t.trace(sza, AZ, F0, ppc * ncol, SEED + 50 + r)
+                b.record(stream)
+                b.synchronize()
+                if r:
+                    ms = a.elapsed_time(b)
+                    best = ms if best is None else min(best, ms)
+            st = t.stats()
+            rows.append({"sza": sza, "ppc": ppc, "ms": best, "photons_per_s": ppc * ncol / (best / 1e3),
+                         "events_per_s": st["events"] / (best / 1e3), "events_per_photon": st["events"] / (ppc * ncol),
+                         "max_events_photon": st["max_events_photon"]})
+    return {"workload": "cumulus 256x256x128, coarse grid %dx%dx%d, one trace per point" % tuple(coarse),
+            "rows": rows}
 
 
 # ---- denoised vs plain: wall time to a target RMS error ----------------------------------
@@ -610,7 +643,9 @@ def run_ours(args):
         # the same step as a C caller with plain host buffers makes it
         e2e["c_abi_host"] = c_abi_host_leg(scene, coarse, tuned, max(3, args.steps // 4), N, begin, total)
 
-    cstep = births = batched = None
+    cstep = births = batched = sweep = None
+    if world == 1 and not args.no_sweep:
+        sweep = sweep_leg(t, coarse)
     if world == 1 and not args.no_batched:
         batched = batched_leg(max(3, args.steps // 4))
     if world == 1 and not args.no_coupled:
@@ -641,7 +676,7 @@ def run_ours(args):
             "events_per_step": events_all, "real_scatter_fraction": st["scatters"] / max(1, events),
             "trace_kernel_ms": 1e3 * tk, "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps, "sobol_birth": births, "coupled_step": cstep,
-            "l2_roofline": l2roof, "time_to_rmse": dn, "batched": batched}
+            "l2_roofline": l2roof, "time_to_rmse": dn, "batched": batched, "config1_sweep": sweep}
     print(json.dumps(line), flush=True)
     t.close()
     if dist is not None:
