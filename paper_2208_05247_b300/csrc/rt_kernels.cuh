@@ -583,8 +583,11 @@ constexpr int kMaxWarpsPerBlock = 8;          // blocks of up to 256 threads
 // Five blocks of 256 threads per SM (register budget 48 per thread).
 // AGG (single-scene launches with rt_options.tally_aggregate) compiles the
 // grouped flush as a separate instantiation.
+// Five resident blocks of 256 threads per SM (48 registers) for single-scene
+// launches; batched launches carry more per-lane state (scene, job, gas
+// scale) and run faster at four blocks without spills.
 template <typename T, int MODE, bool AGG = false>
-__global__ void __launch_bounds__(256, 5) trace_kernel(const __grid_constant__ TraceArgs<T> A)
+__global__ void __launch_bounds__(256, MODE == kOpticsSplit ? 4 : 5) trace_kernel(const __grid_constant__ TraceArgs<T> A)
 {
     constexpr bool BATCH = MODE == kOpticsSplit;
     static_assert(!(AGG && BATCH), "batched launches flush per lane (jobs differ in energy)");
