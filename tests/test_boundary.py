@@ -80,3 +80,44 @@ def test_no_gpu_means_a_loud_error(lib):
     with pytest.raises(rt.RtError) as e:
         rt.rt_create(4, 4, 4, 1, 1, 1)
     assert e.value.code in (rt.RT_E_CUDA, rt.RT_E_OOM)
+
+
+C_CALLER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "rt.h"
+#include "nn.h"
+
+/* A plain C caller: without a usable GPU rt_create returns NULL and leaves a
+   message; argument checks fail before any device work. */
+int main(void)
+{
+    rt_handle h = rt_create(32, 32, 32, 100.0, 100.0, 100.0);
+    if (h) {
+        rt_destroy(h);
+        printf("handle\n");
+        return 0;
+    }
+    printf("code %d: %s\n", rt_last_error_code(), rt_last_error());
+    return strlen(rt_last_error()) > 0 ? 0 : 1;
+}
+"""
+
+
+def test_headers_are_c99_and_a_c_program_links(lib, tmp_path):
+    """include/*.h compile as C99 (no C++ in the ABI), and a C program links
+    against the library and gets a loud error, not a crash, without a GPU."""
+    import subprocess
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(rt.LIB)
+    cmd = ["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+           str(src), "-o", str(exe), "-L", libdir, "-l:" + os.path.basename(rt.LIB), "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.stdout, r.stderr)
+    import torch
+    if not torch.cuda.is_available():
+        assert r.stdout.startswith("code "), r.stdout
