@@ -63,7 +63,10 @@ enum {
     RT_E_STATE = -2,   /* call made in the wrong order (e.g. trace before optics) */
     RT_E_CUDA = -3,    /* CUDA runtime error */
     RT_E_OOM = -4,     /* device allocation failed */
-    RT_E_BUDGET = -5   /* a photon hit the per-photon step cap; tallies are incomplete */
+    RT_E_BUDGET = -5,  /* a photon hit the per-photon step cap; tallies are incomplete */
+    RT_E_BOUNDS = -6   /* the bounds-checking build (librt_b300_checked.so) found an index
+                          outside its array; that access was redirected in bounds and the
+                          results are invalid (a library bug, never expected) */
 };
 
 enum { RT_HOST = 0, RT_DEVICE = 1 };

@@ -24,23 +24,43 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-gencode", "arch=compute_103a,code=s
          "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-I", INCLUDE]
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+# The bounds-checking variant of the tracer (RT_CHECK_BOUNDS=1): every gather,
+# tally and box index in the transport kernel is checked, and a failed check
+# sets a status bit (RT_E_BOUNDS) instead of trapping. Test-only; it holds the
+# rt_* entry points (not the denoiser's nn_* ones).
+CHECKED_LIB = os.path.join(PKG, "librt_b300_checked.so")
+CHECKED_SOURCES = [os.path.join(CSRC, "rt_api.cu"), os.path.join(CSRC, "rt_noalloc.cu")]
+
+
+def needs_build(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in DEPS)
 
 
+def _compile(lib, sources, extra, verbose):
+    tmp = lib + ".tmp%d" % os.getpid()
+    cmd = [NVCC, *FLAGS, *extra, "-o", tmp, *sources]
+    if verbose:
+        cmd.insert(1, "-Xptxas=-v")
+    subprocess.check_call(cmd)
+    os.replace(tmp, lib)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    if force or needs_build():
-        tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = [NVCC, *FLAGS, "-o", tmp, *SOURCES]
-        if verbose:
-            cmd.insert(1, "-Xptxas=-v")
-        subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
+    if force or needs_build(LIB):
+        _compile(LIB, SOURCES, [], verbose)
     return LIB
+
+
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    """The bounds-checking variant of the tracer library; returns its path."""
+    if force or needs_build(CHECKED_LIB):
+        _compile(CHECKED_LIB, CHECKED_SOURCES, ["-DRT_CHECK_BOUNDS=1"], verbose)
+    return CHECKED_LIB
 
 
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
+    print(build_checked(force=True))

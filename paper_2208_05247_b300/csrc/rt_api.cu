@@ -11,9 +11,19 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "rt.h"
 #include "rt_kernels.cuh"
+
+// NVTX range over one C-ABI call (a no-op unless a profiler is attached), so a
+// timeline shows which library call issued each kernel.
+struct ApiRange {
+    explicit ApiRange(const char *name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+    ApiRange(const ApiRange &) = delete;
+    ApiRange &operator=(const ApiRange &) = delete;
+};
 
 namespace {
 
@@ -352,6 +362,8 @@ int device_status(rt_handle h)
     int st = 0;
     int rc = read_flag(h, &h->scr->status, &st);
     if (rc) return rc;
+    if (st & rt::kStatusBounds)
+        return fail(RT_E_BOUNDS, "an index check of the bounds-checking build failed");
     if (st & rt::kStatusInput)
         return fail(RT_E_INVAL, "the last rt_step launch found an invalid optical property or albedo "
                                 "in its inputs and traced nothing");
@@ -933,6 +945,7 @@ int rt_get_options(rt_handle h, rt_options *o)
 int rt_set_optics(rt_handle h, const float *k_gas, const float *ssa_gas, const float *k_cld,
                   const float *ssa_cld, const float *g_cld, int mem)
 {
+    ApiRange nvtx_range("rt_set_optics");
     int rc = check_free(h, "rt_set_optics");
     if (rc) return rc;
     if (!k_gas || !ssa_gas || !k_cld || !ssa_cld || !g_cld)
@@ -977,6 +990,7 @@ int rt_set_optics(rt_handle h, const float *k_gas, const float *ssa_gas, const f
 int rt_set_optics_total(rt_handle h, const float *k_ext, const float *k_ext_cld, const float *ssa,
                         const float *g_cld, int mem)
 {
+    ApiRange nvtx_range("rt_set_optics_total");
     int rc = check_free(h, "rt_set_optics_total");
     if (rc) return rc;
     if (!k_ext || !k_ext_cld || !ssa || !g_cld) return fail(RT_E_INVAL, "rt_set_optics_total: null field pointer");
@@ -1008,6 +1022,7 @@ int rt_set_optics_total(rt_handle h, const float *k_ext, const float *k_ext_cld,
 
 int rt_set_surface(rt_handle h, const float *albedo, int mem)
 {
+    ApiRange nvtx_range("rt_set_surface");
     int rc = check(h);
     if (rc) return rc;
     if (!albedo) return fail(RT_E_INVAL, "rt_set_surface: null albedo");
@@ -1028,6 +1043,7 @@ int rt_set_surface(rt_handle h, const float *albedo, int mem)
 
 int rt_build_accel(rt_handle h, int cx, int cy, int cz)
 {
+    ApiRange nvtx_range("rt_build_accel");
     int rc = check_free(h, "rt_build_accel");
     if (rc) return rc;
     if (!h->optics_ok) return fail(RT_E_STATE, "rt_build_accel: set valid optics first");
@@ -1085,6 +1101,7 @@ int rt_build_accel(rt_handle h, int cx, int cy, int cz)
 int rt_trace_ex(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux, double diffuse_fraction,
                 uint64_t photon_begin, uint64_t photon_count, uint64_t photons_total, uint64_t seed)
 {
+    ApiRange nvtx_range("rt_trace_ex");
     int rc = check_free(h, "rt_trace");
     if (rc) return rc;
     if (!h->optics_ok || !h->surface_ok || !h->accel_ok)
@@ -1120,6 +1137,7 @@ int rt_trace(rt_handle h, double sza_deg, double azimuth_deg, double toa_flux, u
 
 int rt_trace_batch(const rt_job *jobs, int njobs, uint64_t total_photons, uint64_t seed)
 {
+    ApiRange nvtx_range("rt_trace_batch");
     BatchPlan P;
     int rc = plan_batch("rt_trace_batch", jobs, njobs, total_photons, seed, &P);
     if (rc) return rc;
@@ -1225,6 +1243,7 @@ int rt_batch_step_create(const rt_job *jobs, int njobs, uint64_t total_photons, 
 
 int rt_batch_step_launch(rt_batch_step s, uint64_t seed)
 {
+    ApiRange nvtx_range("rt_batch_step_launch");
     if (!s) return fail(RT_E_INVAL, "rt_batch_step_launch: null step");
     rt_handle home = s->home;
     int rc = check(home);
@@ -1320,6 +1339,7 @@ int rt_step_create(rt_handle h, const rt_step_desc *d, rt_step *out)
 int rt_step_launch(rt_step s, double sza_deg, double azimuth_deg, double toa_flux, double diffuse_fraction,
                    uint64_t seed)
 {
+    ApiRange nvtx_range("rt_step_launch");
     if (!s) return fail(RT_E_INVAL, "rt_step_launch: null step");
     rt_handle h = s->h;
     int rc = check(h);
@@ -1367,6 +1387,7 @@ int rt_step_destroy(rt_step s)
 
 int rt_reset_tallies(rt_handle h)
 {
+    ApiRange nvtx_range("rt_reset_tallies");
     int rc = check(h);
     if (rc) return rc;
     h->tally_prec = h->opt.tally_precision;
@@ -1382,6 +1403,7 @@ int rt_reset_tallies(rt_handle h)
 
 int rt_fields(rt_handle h, double *abs3d, double *sfc_dir, double *sfc_dif, double *toa_up, int mem)
 {
+    ApiRange nvtx_range("rt_fields");
     int rc = check(h);
     if (rc) return rc;
     if (mem != RT_HOST && mem != RT_DEVICE) return fail(RT_E_INVAL, "rt_fields: bad mem flag");
@@ -1393,6 +1415,7 @@ int rt_fields(rt_handle h, double *abs3d, double *sfc_dir, double *sfc_dif, doub
 
 int rt_fields_split(rt_handle h, double *abs_dir, double *abs_dif, double *sfc_abs, int mem)
 {
+    ApiRange nvtx_range("rt_fields_split");
     int rc = check(h);
     if (rc) return rc;
     if (mem != RT_HOST && mem != RT_DEVICE) return fail(RT_E_INVAL, "rt_fields_split: bad mem flag");
@@ -1405,6 +1428,7 @@ int rt_fields_split(rt_handle h, double *abs_dir, double *abs_dif, double *sfc_a
 
 int rt_heating_rate(rt_handle h, double *hr, int which, int mem)
 {
+    ApiRange nvtx_range("rt_heating_rate");
     int rc = check(h);
     if (rc) return rc;
     if (!hr || which < 0 || which > 2 || (mem != RT_HOST && mem != RT_DEVICE))
@@ -1436,6 +1460,7 @@ int rt_heating_rate(rt_handle h, double *hr, int which, int mem)
 
 int rt_stats(rt_handle h, rt_stats_t *out)
 {
+    ApiRange nvtx_range("rt_stats");
     int rc = check(h);
     if (rc) return rc;
     if (!out) return fail(RT_E_INVAL, "rt_stats: null output");
@@ -1469,7 +1494,9 @@ int rt_stats(rt_handle h, rt_stats_t *out)
     out->energy_created = s.created;
     out->energy_destroyed = s.destroyed;
     out->energy_capped = s.capped_energy;
-    out->status = (s.status & rt::kStatusInput) ? RT_E_INVAL : (s.status & rt::kStatusBudget) ? RT_E_BUDGET : RT_OK;
+    out->status = (s.status & rt::kStatusBounds) ? RT_E_BOUNDS
+                  : (s.status & rt::kStatusInput) ? RT_E_INVAL
+                  : (s.status & rt::kStatusBudget) ? RT_E_BUDGET : RT_OK;
     return RT_OK;
 }
 

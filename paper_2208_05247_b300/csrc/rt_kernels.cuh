@@ -30,6 +30,29 @@ namespace {   // internal linkage: each .cu file that includes this header has i
 
 constexpr int kStatusBudget = 1;
 constexpr int kStatusInput = 2;                        // an rt_step launch found invalid inputs
+constexpr int kStatusBounds = 4;                       // an index check failed (RT_CHECK_BOUNDS builds)
+
+// Index i into an array of n elements. Unchanged in normal builds. A build
+// with RT_CHECK_BOUNDS=1 (the library's bounds-checking variant, for tests:
+// compute-sanitizer is not available) checks it: an index outside [0, n) sets
+// kStatusBounds in the launch's status word and is replaced by 0, so the access
+// stays inside the array and nothing traps.
+#ifndef RT_CHECK_BOUNDS
+#define RT_CHECK_BOUNDS 0
+#endif
+__device__ __forceinline__ long long checked_index(long long i, long long n, int *status)
+{
+#if RT_CHECK_BOUNDS
+    if (i < 0 || i >= n) {
+        atomicOr(status, kStatusBounds);
+        return 0;
+    }
+#else
+    (void)n;
+    (void)status;
+#endif
+    return i;
+}
 constexpr unsigned long long kQueueClosed = 1ull << 62; // queue head that no launch ever reaches
 
 // Per-handle device scratch: the photon queue head, counters and ledger.
@@ -654,11 +677,13 @@ __global__ void __launch_bounds__(256, MODE == kOpticsSplit ? 4 : 5) trace_kerne
         i = min(max((int)(px * RT_SC(inv_cdx)), 0), RT_SC(NX) - 1);
         j = min(max((int)(py * RT_SC(inv_cdy)), 0), RT_SC(NY) - 1);
         k = min(max((int)(pz * RT_SC(inv_cdz)), 0), RT_SC(NZ) - 1);
-        return (k * RT_SC(NY) + j) * RT_SC(NX) + i;
+        return (int)checked_index((k * RT_SC(NY) + j) * RT_SC(NX) + i,
+                                  (long long)RT_SC(NX) * RT_SC(NY) * RT_SC(NZ), &RT_SC(scr)->status);
     };
     auto locate = [&](float px, float py, float pz) { cell_of(px, py, pz, I, J, K); };
     auto load_box = [&]() {
-        const int q = (K * RT_SC(NY) + J) * RT_SC(NX) + I;
+        const int q = (int)checked_index((K * RT_SC(NY) + J) * RT_SC(NX) + I,
+                                         (long long)RT_SC(NX) * RT_SC(NY) * RT_SC(NZ), &RT_SC(scr)->status);
         if constexpr (BATCH) set_box(__ldg(RT_SC(box2) + q));
         else set_box(__ldg(RT_SC(box) + q));
     };
@@ -740,14 +765,15 @@ __global__ void __launch_bounds__(256, MODE == kOpticsSplit ? 4 : 5) trace_kerne
                         const int mid = (lo + hi + 1) >> 1;
                         if (s_jobs[mid].start <= mine) lo = mid; else hi = mid - 1;
                     }
-                    jid = lo;
-                    sid = s_jobs[jid].scene;
+                    jid = (int)checked_index(lo, A.njobs, &A.scr->status);
+                    sid = (int)checked_index(s_jobs[jid].scene, A.nscenes, &A.scr->status);
                 }
                 // ---- a3: birth at the domain top, along the sun beam ----
                 if (!BATCH && A.order) {
                     const unsigned long long cr =
                         (mine >> 32) ? mine / A.order_ppc : (unsigned long long)((uint32_t)mine / A.order_ppc);
-                    gid = (A.order_k0 + (mine - cr * A.order_ppc)) * RT_JB(ncol) + __ldg(A.order + cr);
+                    gid = (A.order_k0 + (mine - cr * A.order_ppc)) * RT_JB(ncol) +
+                          __ldg(A.order + checked_index((long long)cr, (long long)RT_JB(ncol), &A.scr->status));
                 } else {
                     gid = RT_JB(id_begin) + (mine - RT_JB(start));
                 }
@@ -876,7 +902,9 @@ __global__ void __launch_bounds__(256, MODE == kOpticsSplit ? 4 : 5) trace_kerne
             }
             const int fi = min(max((int)(px * RT_SC(inv_dx)), 0), nx - 1);
             const int fj = min(max((int)(py * RT_SC(inv_dy)), 0), ny - 1);
-            int cell = (min(max((int)(pz * RT_SC(inv_dz)), 0), RT_SC(nz) - 1) * ny + fj) * nx + fi;
+            const long long ncell = (long long)nx * ny * RT_SC(nz);
+            int cell = (int)checked_index((min(max((int)(pz * RT_SC(inv_dz)), 0), RT_SC(nz) - 1) * ny + fj) * nx + fi,
+                                          ncell, &RT_SC(scr)->status);
             // Both gathers of this pass are issued before the Philox block so
             // that their latencies overlap it and each other: the optics of the
             // event cell (record mode; a surface hit loads layer 0 and ignores
@@ -933,7 +961,7 @@ __global__ void __launch_bounds__(256, MODE == kOpticsSplit ? 4 : 5) trace_kerne
                     gj += gj < 0 ? ny : (gj >= ny ? -ny : 0);
                     const int gk = min(max((int)(pz * RT_SC(inv_dz)), max(K - r, 0) * cz),
                                        min((K + r + 1) * cz, RT_SC(nz)) - 1);
-                    cell = (gk * ny + gj) * nx + gi;
+                    cell = (int)checked_index((gk * ny + gj) * nx + gi, ncell, &RT_SC(scr)->status);
                     if constexpr (MODE == kOpticsRecord) orec = __ldg(RT_SC(rec) + cell);
                     optics();
                 }
@@ -972,7 +1000,7 @@ __global__ void __launch_bounds__(256, MODE == kOpticsSplit ? 4 : 5) trace_kerne
                 }
             } else {
                 // ---- a9: Lambertian surface ----
-                const int col = fj * nx + fi;
+                const int col = (int)checked_index(fj * nx + fi, (long long)nx * ny, &RT_SC(scr)->status);
                 tally_add((direct ? RT_SC(tal.sfc_dir) : RT_SC(tal.sfc_dif)) + col, w, RT_JB(scale2));
                 atomicAdd(&s_cnt[sid][kCntSurface], 1ull);
                 w *= __ldg(RT_SC(alb) + col);
@@ -1006,7 +1034,8 @@ __global__ void __launch_bounds__(256, MODE == kOpticsSplit ? 4 : 5) trace_kerne
             const float px = wrap_coord(ox, RT_SC(Lx)), py = wrap_coord(oy, RT_SC(Ly));
             const int fi = min(max((int)(px * RT_SC(inv_dx)), 0), nx - 1);
             const int fj = min(max((int)(py * RT_SC(inv_dy)), 0), ny - 1);
-            tally_add(RT_SC(tal.toa) + (fj * nx + fi), w, RT_JB(scale2));
+            tally_add(RT_SC(tal.toa) + checked_index(fj * nx + fi, (long long)nx * ny, &RT_SC(scr)->status), w,
+                      RT_JB(scale2));
             end_photon();
             ended = true;
         } else if (ready == kCap) {

@@ -25,6 +25,7 @@
 #include <cstdio>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "rt.h"
 #include "rt_kernels.cuh"
@@ -71,6 +72,8 @@ extern "C" int rt_trace_noalloc(int nx, int ny, int nz, double dx, double dy, do
                                 uint64_t seed, double *abs_dir, double *abs_dif, double *sfc_dir,
                                 double *sfc_dif, double *toa_up, void *stream, uint64_t *events_out)
 {
+    nvtxRangePushA("rt_trace_noalloc");
+    struct PopRange { ~PopRange() { nvtxRangePop(); } } nvtx_pop;
     char msg[256];
     if (nx <= 0 || ny <= 0 || nz <= 0 || !(dx > 0) || !(dy > 0) || !(dz > 0) || !std::isfinite(dx) ||
         !std::isfinite(dy) || !std::isfinite(dz))
@@ -184,6 +187,8 @@ extern "C" int rt_trace_noalloc(int nx, int ny, int nz, double dx, double dy, do
         return rt::record_error(RT_E_CUDA, msg);
     }
     if (events_out) *events_out = h.events;
+    if (h.status & rt::kStatusBounds)
+        return rt::record_error(RT_E_BOUNDS, "rt_trace_noalloc: an index check of the bounds-checking build failed");
     if (h.status & rt::kStatusInput)
         return rt::record_error(RT_E_INVAL, "rt_trace_noalloc: invalid optical property (NaN, negative "
                                             "extinction, albedo outside [0,1] or |g| >= 1); outputs unchanged");

@@ -14,7 +14,7 @@ import numpy as np
 
 from .build import LIB
 
-RT_OK, RT_E_INVAL, RT_E_STATE, RT_E_CUDA, RT_E_OOM, RT_E_BUDGET = 0, -1, -2, -3, -4, -5
+RT_OK, RT_E_INVAL, RT_E_STATE, RT_E_CUDA, RT_E_OOM, RT_E_BUDGET, RT_E_BOUNDS = 0, -1, -2, -3, -4, -5, -6
 RT_HOST, RT_DEVICE = 0, 1
 RT_PCLD_SCATTERING, RT_PCLD_EXTINCTION = 0, 1
 RT_TALLY_FP64, RT_TALLY_FP32 = 0, 1
@@ -24,7 +24,8 @@ RT_BIRTH_PHILOX, RT_BIRTH_SOBOL = 0, 1
 RT_SCHEDULE_IDS, RT_SCHEDULE_THICK_FIRST = 0, 1
 
 _ERRNAMES = {RT_E_INVAL: "RT_E_INVAL", RT_E_STATE: "RT_E_STATE", RT_E_CUDA: "RT_E_CUDA",
-             RT_E_OOM: "RT_E_OOM", RT_E_BUDGET: "RT_E_BUDGET"}
+             RT_E_OOM: "RT_E_OOM", RT_E_BUDGET: "RT_E_BUDGET",
+             RT_E_BOUNDS: "RT_E_BOUNDS"}
 
 
 class RtError(RuntimeError):
