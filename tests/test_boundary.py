@@ -121,3 +121,20 @@ def test_headers_are_c99_and_a_c_program_links(lib, tmp_path):
     import torch
     if not torch.cuda.is_available():
         assert r.stdout.startswith("code "), r.stdout
+
+
+def test_readme_c_example_compiles(tmp_path):
+    """The C usage example in README.md compiles against include/rt.h."""
+    import subprocess
+    text = open(os.path.join(ROOT, "README.md")).read()
+    block = re.search(r"```c\n(.*?)```", text, flags=re.S).group(1)
+    body = "\n".join(ln for ln in block.splitlines() if not ln.startswith("#include"))
+    src = tmp_path / "example.c"
+    src.write_text('#include <stdint.h>\n#include "rt.h"\n'
+                   "void example(int nx, int ny, int nz, const float *k_gas, const float *ssa_gas,\n"
+                   "             const float *k_cld, const float *ssa_cld, const float *g_cld, const float *albedo,\n"
+                   "             double *abs3d, double *sfc_dir, double *sfc_dif, double *toa_up)\n{\n"
+                   + body + "\n}\n")
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
