@@ -992,8 +992,19 @@ __global__ void __launch_bounds__(256, MODE == kOpticsSplit ? 4 : 5) trace_kerne
                         if constexpr (MODE == kOpticsRecord) g = orec.w;
                         else g = __ldg(RT_SC(gcl) + cell);
                     }
-                    const float xi = u01(rn.y), mh = hg_mu(g, xi), mr = rayleigh_mu(xi);
-                    mu = cloud ? mh : mr;
+                    const float xi = u01(rn.y);
+                    // the scattering lanes of this pass agree on the scatterer more often
+                    // than not (a warp's lanes share a column): then only one sampler runs
+                    const unsigned am = __activemask();
+                    const unsigned cm = __ballot_sync(am, cloud);
+                    if (cm == am) {
+                        mu = hg_mu(g, xi);
+                    } else if (cm == 0u) {
+                        mu = rayleigh_mu(xi);
+                    } else {
+                        const float mh = hg_mu(g, xi), mr = rayleigh_mu(xi);
+                        mu = cloud ? mh : mr;
+                    }
                     turned = true;
                     direct = false;
                     ++nsc;
