@@ -203,6 +203,22 @@ def layered_scene(nx: int, ny: int, nz: int, dx: float, dy: float, dz: float,
                  lay(g_cld), alb)
 
 
+def random_scene(nx: int, ny: int, nz: int, seed: int, d: float = 100.0) -> Scene:
+    """Cell-by-cell random optics on a small grid (edge-case parity tests):
+    gas k U(0, 5e-3) m^-1 with albedo U(0.3, 1); cloud in half of the cells,
+    k U(0.005, 0.05) m^-1, albedo U(0.9, 1), g U(0, 0.9); surface albedo
+    U(0, 0.6) per column."""
+    rng = np.random.default_rng(seed)
+    s3 = (nz, ny, nx)
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)   # noqa: E731
+    cloudy = rng.random(s3) < 0.5
+    k_cld = np.where(cloudy, rng.uniform(0.005, 0.05, s3), 0.0)
+    return Scene("random%dx%dx%d" % (nx, ny, nz), nx, ny, nz, d, d, d,
+                 f32(rng.uniform(0.0, 5e-3, s3)), f32(rng.uniform(0.3, 1.0, s3)), f32(k_cld),
+                 f32(np.where(cloudy, rng.uniform(0.9, 1.0, s3), 0.0)),
+                 f32(np.where(cloudy, rng.uniform(0.0, 0.9, s3), 0.0)), f32(rng.uniform(0.0, 0.6, (ny, nx))))
+
+
 # --- batched spectral + multi-scene workload ---------------------------------------
 
 BATCH_SCENE_SHAPES = ((128, 128, 96), (192, 96, 128), (256, 256, 128), (64, 64, 64))
