@@ -226,11 +226,14 @@ __global__ void check_albedo(const float *__restrict__ alb, size_t n, int *bad)
 // the fine cells it covers). One thread per coarse cell; the last coarse cell
 // along an axis covers the remainder.
 // ---------------------------------------------------------------------------
+// Grid-stride loops over coarse cells count with an unsigned index: n < 2^31,
+// and q + stride (at most 148 * 32 blocks of 256 threads) then stays below
+// 2^32, where a signed index could overflow on grids of nearly 2^31 cells.
 __global__ void build_majorant(const float4 *__restrict__ rec, float *__restrict__ kmax, int nx,
                                int ny, int nz, int cx, int cy, int cz, int NX, int NY, int NZ)
 {
     const int n = NX * NY * NZ;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < (unsigned)n; q += gridDim.x * blockDim.x) {
         const int I = q % NX, J = (q / NX) % NY, K = q / (NX * NY);
         const int i1 = min(I * cx + cx, nx), j1 = min(J * cy + cy, ny), k1 = min(K * cz + cz, nz);
         float m = 0.0f;
@@ -262,7 +265,7 @@ __global__ void column_keys(const float *__restrict__ kmax, int NX, int NY, int 
                             unsigned char *__restrict__ key)
 {
     const int n = NX * NY;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < (unsigned)n; q += gridDim.x * blockDim.x) {
         float tau = 0.f;
         for (int K = 0; K < NZ; ++K)
             tau = fmaf(__ldg(kmax + (size_t)K * n + q), fminf(cdz, H - (float)K * cdz), tau);
@@ -343,7 +346,7 @@ __global__ void build_majorant_split(const float4 *__restrict__ rec2, float2 *__
                                      int ny, int nz, int cx, int cy, int cz, int NX, int NY, int NZ)
 {
     const int n = NX * NY * NZ;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < (unsigned)n; q += gridDim.x * blockDim.x) {
         const int I = q % NX, J = (q / NX) % NY, K = q / (NX * NY);
         const int i1 = min(I * cx + cx, nx), j1 = min(J * cy + cy, ny), k1 = min(K * cz + cz, nz);
         float mg = 0.0f, mc = 0.0f;
@@ -398,7 +401,7 @@ __device__ __forceinline__ int box_radius(uint32_t w) { return (int)(w & 0xFu); 
 // radius 0: every box is its own coarse cell
 __global__ void box_init(const float *__restrict__ kmax, float *__restrict__ cur, uint32_t *__restrict__ box, int n)
 {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < (unsigned)n; q += gridDim.x * blockDim.x) {
         const float k = kmax[q];
         cur[q] = k;
         box[q] = box_word(k, 0);
@@ -408,7 +411,7 @@ __global__ void box_init(const float *__restrict__ kmax, float *__restrict__ cur
 __global__ void box_init2(const float2 *__restrict__ kmax2, float *__restrict__ curg, float *__restrict__ curc,
                           uint2 *__restrict__ box2, int n)
 {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < (unsigned)n; q += gridDim.x * blockDim.x) {
         const float2 m = kmax2[q];
         curg[q] = m.x;
         curc[q] = m.y;
@@ -422,7 +425,7 @@ __global__ void box_dilate(const float *__restrict__ in, float *__restrict__ out
                            int rho)
 {
     const int n = NX * NY * NZ;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < (unsigned)n; q += gridDim.x * blockDim.x) {
         const int I = q % NX, J = (q / NX) % NY, K = q / (NX * NY);
         float m = in[q];
         if (axis == 0) {
@@ -450,7 +453,7 @@ __global__ void box_dilate(const float *__restrict__ in, float *__restrict__ out
 __global__ void box_select(const float *__restrict__ m, uint32_t *__restrict__ box, int n, int r_prev, int r_new,
                            float limit)
 {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < (unsigned)n; q += gridDim.x * blockDim.x) {
         const uint32_t w = box[q];
         if (box_radius(w) == r_prev && m[q] <= limit) box[q] = box_word(m[q], r_new);
     }
@@ -461,7 +464,7 @@ __global__ void box_select(const float *__restrict__ m, uint32_t *__restrict__ b
 __global__ void box_select2(const float *__restrict__ mg, const float *__restrict__ mc, uint2 *__restrict__ box2,
                             int n, int r_prev, int r_new, float limit)
 {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < (unsigned)n; q += gridDim.x * blockDim.x) {
         const uint2 w = box2[q];
         if (box_radius(w.x) == r_prev && mg[q] + mc[q] <= limit)
             box2[q] = make_uint2(box_word(mg[q], r_new), __float_as_uint(mc[q]) | 0xFu);
@@ -1241,7 +1244,7 @@ __global__ void majorant_from_fields(const float *__restrict__ kg, const float *
                                      int cz, int NX, int NY, int NZ)
 {
     const int n = NX * NY * NZ;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < (unsigned)n; q += gridDim.x * blockDim.x) {
         const int I = q % NX, J = (q / NX) % NY, K = q / (NX * NY);
         const int i1 = min(I * cx + cx, nx), j1 = min(J * cy + cy, ny), k1 = min(K * cz + cz, nz);
         float m = 0.0f;
