@@ -662,3 +662,42 @@ def test_tiny_and_degenerate_grids_match_the_oracle(shape, seed):
             assert rep["frac_over"] <= rep["bound"], (shape, cxyz, field, rep["max_abs_z"])
             assert rep["pooled_p_family"] >= 1e-3, (shape, cxyz, field, rep["pooled_max_abs_z"])
             assert abs(rep["domain_rel"]) < 4 * rep["domain_rel_se"] + 1e-9, (shape, cxyz, field, rep["domain_rel"])
+
+
+def test_empty_atmosphere_and_zero_photons_are_exact():
+    """No extinction anywhere: every photon reaches the surface unscattered.
+    With the sun overhead and whole rounds of photons per column, each column
+    receives exactly its own photons: its direct irradiance is exactly F, its
+    surface absorption F (1 - albedo), and the reflected share leaves through
+    the top untouched (its roulette below weight 1/2 makes the domain mean
+    upward flux F times the mean albedo in expectation). Under a slanted sun photons land in other columns, but the
+    domain mean direct irradiance is still exactly F cos(sza). Nothing is
+    absorbed in the atmosphere, and a trace of zero photons tallies nothing."""
+    nx, ny, nz = 12, 10, 8
+    sc = scenes.layered_scene(nx, ny, nz, 80.0, 80.0, 60.0, k_gas=0.0, ssa_gas=0.0)
+    rng = np.random.default_rng(3)
+    sc.albedo = rng.uniform(0.0, 0.8, (ny, nx)).astype(np.float32)
+    alb = sc.albedo.astype(np.float64)
+    with rt.Tracer.from_scene(sc) as t:
+        t.trace(37.0, 123.0, 1000.0, 0, 5)
+        f = t.fields(split=True)
+        assert all(float(np.abs(f[k]).max()) == 0.0 for k in f), "zero photons must tally nothing"
+        assert t.stats()["photons"] == 0
+        t.trace(0.0, 0.0, 1000.0, 64 * sc.ncol, 5)
+        f, st = t.fields(split=True), t.stats()
+        assert st["status"] == 0 and st["scatters"] == 0
+        assert np.allclose(f["sfc_dir"], 1000.0, rtol=1e-12)
+        assert np.allclose(f["sfc_abs"], 1000.0 * (1.0 - alb), rtol=1e-6)
+        # the reflected weight goes through roulette when it is below 1/2 (Sec.
+        # 2.3): survival with probability a at weight 1, so the top flux is
+        # exact only in expectation; per photon the variance is a (1 - a)
+        var = np.where(alb < 0.5, alb * (1.0 - alb), 0.0)
+        se = 1000.0 * np.sqrt(64 * var.sum()) / (64 * sc.ncol)
+        assert abs(f["toa_up"].mean() - 1000.0 * alb.mean()) < 4 * se + 1e-9, (f["toa_up"].mean(), alb.mean(), se)
+        for k in ("sfc_dif", "abs3d"):
+            assert float(np.abs(f[k]).max()) == 0.0, k
+        t.reset()
+        t.trace(37.0, 123.0, 1000.0, 64 * sc.ncol, 6)
+        f = t.fields(split=True)
+        assert np.isclose(f["sfc_dir"].mean(), 1000.0 * np.cos(np.deg2rad(37.0)), rtol=1e-12)
+        assert float(np.abs(f["abs3d"]).max()) == 0.0
