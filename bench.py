@@ -45,10 +45,11 @@ COARSE = (2, 2, 2)
 # tally read-modify-write per majorant event, 4 B majorant box word per walk
 # step (the "crossings" counter).
 BYTES_PER_EVENT, BYTES_PER_CROSSING = 32, 4
-# derive, albedo check, majorant, majorant boxes (init + 4 levels of 3 axis
-# dilations and a selection), column keys + column order (launch order),
-# transport, 4 field sums, heating rate
-KERNELS_PER_STEP = 28
+# derive, albedo check, two status-word stores (the optics and albedo checks
+# read back), majorant, majorant boxes (init + 4 levels of 3 axis dilations and
+# a selection), column keys + column order (launch order), transport, 4 field
+# sums, heating rate
+KERNELS_PER_STEP = 30
 PROFILE = os.path.join(ROOT, "profiles", "trace_kernel_cumulus256.md")
 
 
