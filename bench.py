@@ -278,14 +278,15 @@ def denoise_leg(args):
                            chw=denoise.channel_weights(pairs, direct=False))
     t_train = time.time() - t0
     del pairs
-    res = denoise.evaluate(net, list(range(1512, 1512 + args.denoise_eval)), shape, truth_ppc=16384,
+    res = denoise.evaluate(net, list(range(1512, 1512 + args.denoise_eval)), shape, truth_ppc=65536,
                            workers=os.cpu_count() or 8)
     return {"workload": "one quadrature point on cumulus 128x128x128 (dx=dy=50 m, dz=25 m), sza 0/30/60, "
                         f"{args.denoise_eval} held-out scenes (seeds 1512-{1511 + args.denoise_eval}), "
-                        "truth 16384 photons/column, plain runs 4-4096 photons/column",
+                        "truth 65536 photons/column, plain runs 4-16384 photons/column",
             "fit": res["fit"], "plain_time_fit_ms": res["plain_time_fit_ms"],
             "training": {"scenes": args.denoise_train, "epochs": args.denoise_epochs, "pairs_s": t_pairs,
                          "train_s": t_train, "weights": "moving average over the last tenth of the steps",
+                         "schedule": "Adam, linear warmup over 5 % of the steps, cosine decay 1e-3 to 1e-4",
                          "guards": getattr(net, "train_log", None),
                          "loss_first": losses[0][1], "loss_last": losses[-1][1]},
             "plain": res["plain"], "denoised": res["denoised"], "noisy_input": res["noisy_input"],
