@@ -11,10 +11,13 @@ the persistent transport kernel, and the FP64 output fields (3D absorption,
 surface direct/diffuse, top upward flux, heating rate) into device buffers.
 
 Prints one JSON line. `value` is majorant collision events per second over
-the timed steps (CUDA events on the tracer's stream); `e2e` is the same metric
-through the C ABI with host buffers (host->device inputs and device->host
-outputs inside the timed region). `roofline` uses the transport kernel's own
-CUDA-event duration. `cpu_baseline` times the FP64 CPU oracle on a bounded
+the timed steps, which alternate between two tracer handles on two streams so
+that one step's transport tail overlaps the next step (`--streams 1`: one
+after the other, also timed as `serial_ms_per_step`); CUDA events on the
+default stream, which waits for both. `e2e` is the same metric through the C
+ABI with host buffers (host->device inputs and device->host outputs inside the
+timed region). `roofline` uses the transport kernel's own CUDA-event duration
+in the single-stream loop, where one launch has the GPU to itself. `cpu_baseline` times the FP64 CPU oracle on a bounded
 sample of the same scene.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -73,6 +76,9 @@ def parse():
     p.add_argument("--denoise-eval", type=int, default=64, help="held-out scenes of the denoiser leg")
     p.add_argument("--no-l2-probe", action="store_true", help="skip the L2 read-bandwidth probe")
     p.add_argument("--denoise-epochs", type=int, default=32, help="training epochs of the denoiser leg")
+    p.add_argument("--streams", type=int, default=2,
+                   help="tracer handles (one stream each) that the timed steps alternate between; 1 = one after "
+                        "the other")
     p.add_argument("--reduce-fields", action="store_true",
                    help="N>1: sum the ranks' output fields every step (NCCL all-reduce) into one combined field")
     p.add_argument("--no-autotune", action="store_true",
@@ -415,14 +421,53 @@ def batched_leg(steps: int):
             t.reset()
         rt.rt_trace_batch(jobs, total_photons=total, seed=SEED + i)
 
+    # a second set of handles on its own stream, with its own recorded step:
+    # replays that alternate between the two sets overlap one step's tail
+    # with the next step
+    s_a, s_b = torch.cuda.Stream(), torch.cuda.Stream()
+    tracers_b = []
+    for sc in scs:
+        t = rt.Tracer(sc.nx, sc.ny, sc.nz, sc.dx, sc.dy, sc.dz, stream=s_b)
+        t.set_options(batch_optics=1)
+        t.set_optics(*sc.fields())
+        t.set_surface(sc.albedo)
+        t.build_accel(2, 2, 2)
+        tracers_b.append(t)
+    jobs_b = [dict(j, scene=tracers_b[tracers.index(j["scene"])]) for j in jobs]
+
+    def timed_two(fn, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s_a.wait_stream(stream)
+        s_b.wait_stream(stream)
+        for i in range(k):
+            fn(i)
+        stream.wait_stream(s_a)
+        stream.wait_stream(s_b)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
+
     step = rt.rt_batch_step_create(jobs, total_photons=total)
+    step_b = rt.rt_batch_step_create(jobs_b, total_photons=total)
     try:
         for i in range(2):
             rt.rt_batch_step_launch(step, SEED + i)
         ms_graph = timed(lambda i: rt.rt_batch_step_launch(step, SEED + i), steps)
         sts = [t.stats() for t in tracers]
+        for t in tracers:
+            t.set_stream(s_a)
+        two = lambda i: rt.rt_batch_step_launch(step if i % 2 == 0 else step_b, SEED + i)   # noqa: E731
+        for i in range(4):
+            two(i)
+        ms_two = timed_two(two, 2 * ((steps + 1) // 2))
+        sts_two = [t.stats() for t in tracers + tracers_b]
+        for t in tracers:
+            t.set_stream(stream)
     finally:
         rt.rt_batch_step_destroy(step)
+        rt.rt_batch_step_destroy(step_b)
     eager(0)
     ms_eager = timed(eager, steps)
     ev = sum(st["events"] for st in sts)
@@ -431,8 +476,8 @@ def batched_leg(steps: int):
     peak, _ = peaks()
     closure = [abs(st["energy_in"] + st["energy_created"] - st["energy_destroyed"] - st["energy_capped"]
                    - st["energy_toa_up"] - st["energy_atm_abs"] - st["energy_sfc_abs"]) / st["energy_in"]
-               for st in sts]
-    for t in tracers:
+               for st in sts + sts_two]
+    for t in tracers + tracers_b:
         t.close()
     alg = ev * BYTES_PER_EVENT + cr * BYTES_PER_CROSSING
     return {"workload": "4 scenes (128x128x96, 192x96x128, 256x256x128, 64x64x64) x 112 quadrature points, "
@@ -441,7 +486,11 @@ def batched_leg(steps: int):
             "events_per_s": ev / (ms_graph / 1e3), "photons_per_s": ph / (ms_graph / 1e3),
             "roofline_frac": alg / (ms_graph / 1e3) / 1e9 / peak,
             "roofline_note": "algorithmic bytes of the step over the whole replayed step (tally resets included)",
-            "ledger_residual_max": max(closure), "capped": sum(st["capped"] for st in sts)}
+            "two_streams": {"ms_per_step_graph": ms_two, "events_per_s": ev / (ms_two / 1e3),
+                            "photons_per_s": ph / (ms_two / 1e3), "roofline_frac": alg / (ms_two / 1e3) / 1e9 / peak,
+                            "note": "replays alternate between two sets of the four scene handles and two "
+                                    "recorded steps, one stream each (events per step from the one-stream run)"},
+            "ledger_residual_max": max(closure), "capped": sum(st["capped"] for st in sts + sts_two)}
 
 
 # ---- end to end through the C ABI with plain host buffers ------------------------------
@@ -548,34 +597,77 @@ def run_ours(args):
         step(SEED)
     torch.cuda.synchronize()
     ref_stats = t.stats()
+    clocks = Clocks(local)
 
+    def timed(run, k):
+        """k steps of `run`, bracketed by a barrier and a device synchronize,
+        timed by CUDA events on the default stream (max over ranks)."""
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            v = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(v, op=dist.ReduceOp.MAX)
+            ms = float(v.item())
+        return ms
+
+    # (1) one handle on one stream: the steps run one after the other, and the
+    # transport launches' CUDA-event durations give the kernel's roofline
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = Clocks(local)
-    barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    e0.record(stream)
-    for k in range(args.steps):
-        step(SEED, evs[k])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
+
+    def serial(k):
+        for i in range(k):
+            step(SEED, evs[i])
+    ms_serial = timed(serial, args.steps)
     trace_ms = [a.elapsed_time(b) for a, b in evs]
     st = t.stats()
     assert st["events"] == ref_stats["events"], "event count changed between identical steps"
     assert st["status"] == 0, "transport reported a capped photon"
 
+    # (2) the product path: steps alternate between `streams` handles, one
+    # stream each (pipeline.StepRing), so that a step's transport starts on the
+    # SMs that the previous step's tail leaves idle
+    ring = None
+    ms = ms_serial
+    if args.streams > 1:
+        from paper_2208_05247_b300 import pipeline
+        extra = []
+        for _ in range(args.streams - 1):
+            t2 = rt.Tracer(scene.nx, scene.ny, scene.nz, scene.dx, scene.dy, scene.dz)
+            if tuned:
+                t2.set_options(**{k: v for k, v in tuned.items() if k != "coarse"})
+            extra.append(t2)
+        ring = pipeline.StepRing([t] + extra, coarse)
+        after = (lambda s, o: shard.reduce_fields(o)) if reduce else None
+
+        def ring_steps(k):
+            ring.wait_on(stream)
+            for _ in range(k):
+                ring.submit(d_in, d_alb, args.sza, AZ, F0, N, SEED, photon_begin=begin, photons_total=total,
+                            after=after)
+            ring.join(stream)
+        ring_steps(max(2, args.warmup) * args.streams)
+        torch.cuda.synchronize()
+        ms = timed(ring_steps, args.steps)
+        for tr in ring.ts:
+            s2 = tr.stats()
+            assert s2["events"] == ref_stats["events"], "a ring handle traced different histories"
+            assert s2["status"] == 0, "transport reported a capped photon"
+        t.set_stream(stream)
+    clk = clocks.stop()
+
     events = st["events"]
     crossings = st["crossings"]
     ms_max, events_all = ms, events
     if dist is not None:
-        v = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(v, op=dist.ReduceOp.MAX)
-        ms_max = float(v.item())
         e = torch.tensor([events], dtype=torch.float64, device=dev)
         dist.all_reduce(e)
         events_all = int(e.item())
@@ -594,6 +686,12 @@ def run_ours(args):
             # 8-byte tally update and a 4-byte box word each move a 32-byte sector)
             "sector_bytes_per_launch": events * 64 + crossings * 32,
             "sector_frac": (events * 64 + crossings * 32) / tk / 1e9 / peak,
+            "kernel_ms_source": "CUDA events around each transport launch of the single-stream timed loop "
+                                "(one launch on the GPU at a time)",
+            # the same bytes over the whole product step (all kernels, with the
+            # handles' steps overlapping): what the timed `value` reaches
+            "step_achieved": alg_bytes / (ms / args.steps / 1e3) / 1e9,
+            "step_frac": alg_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
             "photons_per_s": N * world * args.steps / (ms_max / 1e3)}
     # the same algorithmic bytes against this GPU's L2 read bandwidth, measured
     # here (outside the timed region) by the library's read probe: the
@@ -618,10 +716,10 @@ def run_ours(args):
         h_alb = torch.from_numpy(scene.albedo).pin_memory()
         h_outs = [{k: torch.empty(v.numel(), dtype=torch.float64).pin_memory() for k, v in d_out.items()}
                   for _ in range(2)]
-        pipe = pipeline.HostPipeline(t, coarse)
+        pipe = pipeline.HostPipeline(ring.ts if ring is not None else t, coarse)
         pipe.submit(h_in, h_alb, args.sza, AZ, F0, N, SEED, h_outs[0], photon_begin=begin, photons_total=total)
         pipe.synchronize()
-        assert t.stats()["events"] == events, "pipelined step traced different histories"
+        assert all(tr.stats()["events"] == events for tr in pipe.ts), "pipelined step traced different histories"
         barrier()
         k2 = max(3, args.steps // 2)
         t0 = time.perf_counter()
@@ -640,7 +738,8 @@ def run_ours(args):
         d2h = sum(v.numel() * 8 for v in h_outs[0].values())
         e2e = {"value": events_all * k2 / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * dt / k2,
-               "pipelined": "copies of step k+1 in and k-1 out overlap step k's transport (HostPipeline)",
+               "pipelined": "copies of step k+1 in and k-1 out overlap step k's transport (HostPipeline); "
+                            f"steps alternate between {len(pipe.ts)} handle(s), one stream each",
                "photons_per_s": N * world * k2 / dt}
         # the same step as a C caller with plain host buffers makes it
         e2e["c_abi_host"] = c_abi_host_leg(scene, coarse, tuned, max(3, args.steps // 4), N, begin, total)
@@ -651,7 +750,7 @@ def run_ours(args):
     if world == 1 and not args.no_batched:
         batched = batched_leg(max(3, args.steps // 4))
     if world == 1 and not args.no_coupled:
-        cstep = coupled_step_leg(t, d_in, d_alb, d_out, N, ms_max / args.steps, events, max(3, args.steps // 2))
+        cstep = coupled_step_leg(t, d_in, d_alb, d_out, N, ms_serial / args.steps, events, max(3, args.steps // 2))
     if world == 1 and not args.no_birth:
         births = birth_leg(scene, coarse, tuned)
 
@@ -671,16 +770,19 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(args, world, coarse), launch=tuned or "defaults",
+                           streams=f"{args.streams} tracer handle(s), one stream each; steps alternate between them",
                            **({"parallelism": f"photon ranges, {world} ranks, fields summed every step "
                                               "(NCCL all-reduce, FP64)"} if reduce else {})),
             "photons_per_s": N * world * args.steps / (ms_max / 1e3),
             "real_scatters_per_s": st["scatters"] * world * args.steps / (ms_max / 1e3),
             "events_per_step": events_all, "real_scatter_fraction": st["scatters"] / max(1, events),
-            "trace_kernel_ms": 1e3 * tk, "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "trace_kernel_ms": 1e3 * tk, "serial_ms_per_step": ms_serial / args.steps,
+            "serial_events_per_s": events_all * args.steps / (ms_serial / 1e3), "clocks": clk, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps, "sobol_birth": births, "coupled_step": cstep,
             "l2_roofline": l2roof, "time_to_rmse": dn, "batched": batched, "config1_sweep": sweep}
     print(json.dumps(line), flush=True)
-    t.close()
+    for tr in (ring.ts if ring is not None else [t]):
+        tr.close()
     if dist is not None:
         dist.destroy_process_group()
 

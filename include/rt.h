@@ -162,7 +162,11 @@ rt_handle rt_create(int nx, int ny, int nz, double dx, double dy, double dz);
 int rt_destroy(rt_handle h);
 
 /* Order all following calls of this handle on `stream` (a cudaStream_t, e.g.
- * torch.cuda.current_stream().cuda_stream); NULL selects the default stream. */
+ * torch.cuda.current_stream().cuda_stream); NULL selects the default stream.
+ * Handles share no device state, so the calls of two handles on two streams
+ * may run at the same time: repeated steps that alternate between two handles
+ * start one step's transport on the SMs that the previous step's last, longest
+ * histories leave idle. */
 int rt_set_stream(rt_handle h, void *stream);
 
 int rt_set_options(rt_handle h, const rt_options *opt);

@@ -255,3 +255,54 @@ def test_batch_step_graph_replay_equals_eager_batch():
     finally:
         tA.close()
         tB.close()
+
+
+def test_two_recorded_steps_on_two_streams_equal_eager_batches():
+    """Two sets of scene handles, each with its own recorded step and stream:
+    replays that run at the same time give each set the fields of its own
+    seed, as the eager batched call does."""
+    torch = pytest.importorskip("torch")
+    scA = scenes.ellipsoid_scene(seed=0)
+    scB = scenes.cumulus_scene(seed=5, nx=48, ny=40, nz=32)
+    sets = [[batch_tracer(scA), batch_tracer(scB)] for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    total = 2 ** 20
+
+    def jobs_of(ts):
+        return [dict(scene=t, sza_deg=sza, azimuth_deg=15.0, toa_flux=f, gas_scale=s)
+                for t, sza in zip(ts, (30.0, 45.0)) for s, f in ((0.05, 300.0), (1.0, 500.0), (4.0, 200.0))]
+
+    try:
+        want = {}
+        for seed in (11, 12):
+            for t in sets[0]:
+                t.reset()
+            rt.rt_trace_batch(jobs_of(sets[0]), total_photons=total, seed=seed)
+            want[seed] = [(t.fields(split=True), t.stats()) for t in sets[0]]
+        for ts, s in zip(sets, streams):
+            for t in ts:
+                t.set_stream(s)
+        steps = [rt.rt_batch_step_create(jobs_of(ts), total_photons=total) for ts in sets]
+        try:
+            main = torch.cuda.current_stream()
+            for s in streams:
+                s.wait_stream(main)
+            for k in range(4):                    # seeds 11, 12, 11, 12 on sets 0, 1, 0, 1
+                rt.rt_batch_step_launch(steps[k % 2], 11 + k % 2)
+            torch.cuda.synchronize()
+            for ts, seed in zip(sets, (11, 12)):
+                for t, (wf, ws) in zip(ts, want[seed]):
+                    f, st = t.fields(split=True), t.stats()
+                    for k in ("photons", "events", "scatters", "crossings", "surface_hits", "roulette_kills"):
+                        assert st[k] == ws[k], (seed, k, st[k], ws[k])
+                    assert closes(st)
+                    for k in FIELDS:
+                        scale = np.abs(wf[k]).max()
+                        assert np.allclose(f[k], wf[k], rtol=1e-12, atol=1e-12 * scale), (seed, k)
+        finally:
+            for st in steps:
+                rt.rt_batch_step_destroy(st)
+    finally:
+        for ts in sets:
+            for t in ts:
+                t.close()
