@@ -279,6 +279,29 @@ def test_gpu_overhead_sun_commutes_with_swapping_x_and_y():
         assert abs(rep["domain_rel"]) < 4 * rep["domain_rel_se"] + 1e-9, (field, rep["domain_rel"])
 
 
+def test_gpu_scene_shifted_by_whole_cells_gives_shifted_fields():
+    """Periodic x and y: rolling the scene by (11, 5) cells, which carries the
+    clouds across both lateral edges, rolls the fields by the same cells
+    (cell-wise parity statistic between independent runs, slanted sun so that
+    paths cross the edges)."""
+    sc = scenes.ellipsoid_scene(seed=2)
+    sh = copy.deepcopy(sc)
+    dy, dx = 5, 11
+    for name in ("k_gas", "ssa_gas", "k_cld", "ssa_cld", "g_cld"):
+        setattr(sh, name, np.ascontiguousarray(np.roll(getattr(sc, name), (dy, dx), axis=(1, 2))))
+    sh.albedo = np.ascontiguousarray(np.roll(sc.albedo, (dy, dx), axis=(0, 1)))
+    a, _ = gpu_batches(sc, 45.0, 60.0, 1000.0, 2 ** 20, range(1100, 1116))
+    b, _ = gpu_batches(sh, 45.0, 60.0, 1000.0, 2 ** 20, range(1200, 1216))
+    ap, _ = gpu_batches(sc, 45.0, 60.0, 1000.0, 2 ** 20, range(1300, 1308))
+    bp, _ = gpu_batches(sh, 45.0, 60.0, 1000.0, 2 ** 20, range(1400, 1408))
+    for field in FIELDS:
+        back = np.roll(b[field], (-dy, -dx), axis=(-2, -1))
+        back_p = np.roll(bp[field], (-dy, -dx), axis=(-2, -1))
+        rep = refs.parity_report(back, a[field], pilot=(back_p, ap[field]))
+        assert rep["frac_over"] <= rep["bound"], (field, rep["frac_over"], rep["bound"])
+        assert abs(rep["domain_rel"]) < 4 * rep["domain_rel_se"] + 1e-9, (field, rep["domain_rel"])
+
+
 # --- reproducibility, launch-geometry and partition invariance -----------------------
 
 def _run(sc, seed, N, **opts):
