@@ -433,7 +433,9 @@ def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, se
     is non-finite or above 8x the running mean loss is skipped; 32 skipped
     steps in a row (the weights themselves have diverged, so every loss is
     out of range) or a running mean above 4x its lowest value roll the
-    weights back to their moving average with a fresh Adam state.
+    weights back to their moving average with a fresh Adam state, and the
+    learning-rate ramp starts again (a fresh Adam state takes full-size steps
+    at once, and at full rate one run diverged again after every rollback).
     `net.train_log` records skips and rollbacks.
     """
     torch = _torch()
@@ -445,6 +447,7 @@ def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, se
     k = 0
     t0 = time.time()
     run, best, skipped, rollbacks, streak = None, None, 0, 0, 0
+    ramp_from = 0                  # the learning-rate ramp restarts at every rollback
     for ep in range(epochs):
         for idx in rng.permutation(len(samples)):
             s = samples[idx]
@@ -459,6 +462,7 @@ def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, se
                     net.rollback()
                     rollbacks += 1
                     streak = 0
+                    ramp_from = k
                     # the averaged weights may sit above the old running mean:
                     # restart it, or every later step would be skipped
                     run = None
@@ -471,11 +475,12 @@ def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, se
                     net.rollback()
                     rollbacks += 1
                     run = best
+                    ramp_from = k
                     continue
             net.backward(s.x, s.shape)
             rate = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * (k - 1) / max(1, steps - 1)))
             if warmup > 0.0:
-                rate *= min(1.0, k / max(1.0, warmup * steps))
+                rate *= min(1.0, (k - ramp_from) / max(1.0, warmup * steps))
             net.step(rate)
             if ema:
                 net.ema(1.0 - 10.0 / max(steps, 20))
@@ -709,6 +714,7 @@ def main(argv=None):
     p.add_argument("--shape", type=int, nargs=3, default=(128, 128, 128), help="nz ny nx")
     p.add_argument("--truth-ppc", type=int, default=65536)
     p.add_argument("--hi-ppc", type=int, default=1024, help="photons/column of the training targets")
+    p.add_argument("--lo-ppc", type=int, default=4, help="photons/column of the network's traced input")
     p.add_argument("--plain-ppc", type=int, nargs="+", default=(4, 16, 64, 256, 1024, 4096, 16384))
     p.add_argument("--spectral", action="store_true",
                    help="broadband fields: all quadrature points of the g-point table in one batched launch")
@@ -722,7 +728,7 @@ def main(argv=None):
     a = p.parse_args(argv)
     shape = tuple(a.shape)
     t0 = time.time()
-    pairs = make_pairs(list(range(1000, 1000 + a.train)), shape, hi_ppc=a.hi_ppc, workers=a.workers,
+    pairs = make_pairs(list(range(1000, 1000 + a.train)), shape, lo_ppc=a.lo_ppc, hi_ppc=a.hi_ppc, workers=a.workers,
                        spectral=a.spectral, direct_features=a.direct_features)
     t_pairs = time.time() - t0
     net = UNet(seed=0)
@@ -732,10 +738,11 @@ def main(argv=None):
                    warmup=a.warmup, seed=a.seed)
     t_train = time.time() - t0
     del pairs
-    res = evaluate(net, list(range(1000 + a.train, 1000 + a.train + a.eval)), shape, truth_ppc=a.truth_ppc,
+    res = evaluate(net, list(range(1000 + a.train, 1000 + a.train + a.eval)), shape, lo_ppc=a.lo_ppc,
+                   truth_ppc=a.truth_ppc,
                    workers=a.workers, plain_ppc=tuple(a.plain_ppc), spectral=a.spectral,
                    direct_features=a.direct_features, exact_direct=not a.direct_loss)
-    res.update({"train_scenes": a.train, "epochs": a.epochs, "hi_ppc": a.hi_ppc, "warmup": a.warmup, "seed": a.seed,
+    res.update({"train_scenes": a.train, "epochs": a.epochs, "lo_ppc": a.lo_ppc, "hi_ppc": a.hi_ppc, "warmup": a.warmup, "seed": a.seed,
                 "direct_features": a.direct_features, "direct_loss": a.direct_loss, "guards": net.train_log, "pairs_s": t_pairs, "train_s": t_train,
                 "loss_first": losses[0][1], "loss_last": losses[-1][1], "params": net.n_params(),
                 "forward_gflop": net.flops(shape) / 1e9})

@@ -1,9 +1,11 @@
 """The time-to-RMSE arithmetic behind the denoiser speed-ups (CPU only):
 the plain tracer's RMSE is modelled as a / sqrt(ppc) (Monte Carlo error falls
-as N^-1/2, Sec. 3.2) and its wall time as t0 + t1 * ppc."""
+as N^-1/2, Sec. 3.2) and its wall time as t0 + t1 * ppc. Also the training
+loop's guard bookkeeping, driven by a fake network."""
 import math
 
 import numpy as np
+import pytest
 
 from paper_2208_05247_b300 import denoise
 
@@ -58,3 +60,71 @@ def test_truth_noise_term():
     # the noise-free-truth limit is the plain a / sqrt(p) model
     assert math.isclose(denoise.plain_ppc_to_match(PPC, [a / math.sqrt(p) for p in PPC], 8.0, truth_ppc=None),
                         (a / 8.0) ** 2, rel_tol=1e-12)
+
+
+class _FakeNet:
+    """Stands in for the U-Net in `denoise.train`: plays back a loss sequence
+    and records the learning rate of every optimizer step and every rollback."""
+
+    def __init__(self, losses):
+        self.losses = list(losses)
+        self.rates, self.rollbacks_at, self.k = [], [], 0
+
+    def forward(self, x, shape):
+        pass
+
+    def loss_and_grad(self, target, shape, chw):
+        self.k += 1
+        return _Scalar(self.losses[self.k - 1])
+
+    def backward(self, x, shape):
+        pass
+
+    def step(self, rate):
+        self.rates.append((self.k, rate))
+
+    def ema(self, decay):
+        pass
+
+    def apply_ema(self):
+        pass
+
+    def rollback(self):
+        self.rollbacks_at.append(self.k)
+
+
+class _Scalar:
+    def __init__(self, v):
+        self.v = v
+
+    def item(self):
+        return self.v
+
+
+def test_training_ramp_restarts_after_a_rollback(monkeypatch):
+    """32 non-finite losses in a row roll the weights back; the learning rate
+    then rises from the ramp's start again instead of resuming at full rate."""
+    from types import SimpleNamespace
+
+    import torch
+
+    from paper_2208_05247_b300 import denoise
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    n = 400
+    losses = [1.0] * 150 + [float("nan")] * 32 + [1.0] * (n - 182)
+    net = _FakeNet(losses)
+    samples = [SimpleNamespace(x=None, shape=None, target=None)] * n
+    denoise.train(net, samples, epochs=1, lr=1e-3, lr_final=1e-3, chw=[1.0], warmup=0.1)
+    assert net.rollbacks_at == [182]
+    assert net.train_log == {"skipped_steps": 32, "rollbacks": 1}
+    rate = dict(net.rates)
+    ramp = 0.1 * n
+    # before: the ramp from step 1, full rate once it ends
+    assert rate[1] == pytest.approx(1e-3 / ramp)
+    assert rate[150] == pytest.approx(1e-3)
+    # skipped steps take no optimizer step
+    assert not any(151 <= k <= 182 for k in rate)
+    # after the rollback at step 182 the ramp starts again
+    assert rate[183] == pytest.approx(1e-3 * 1 / ramp)
+    assert rate[200] == pytest.approx(1e-3 * 18 / ramp)
+    assert rate[182 + int(ramp)] == pytest.approx(1e-3)
