@@ -426,7 +426,9 @@ def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, se
     of 0.069-0.071 K/day against 0.081-0.083 without it).
 
     With `ema` the returned network holds the moving average of its weights
-    over roughly the last tenth of the steps (decay 1 - 10 / steps).
+    over roughly the last tenth of the steps (decay 1 - 10 / steps, capped
+    at (1 + n) / (10 + n) after n updates so that the average follows the
+    weights early on).
 
     Guards keep long runs from collapsing (a few runs diverged at full
     learning rate while repeats of the same run did not): a step whose loss
@@ -448,6 +450,7 @@ def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, se
     t0 = time.time()
     run, best, skipped, rollbacks, streak = None, None, 0, 0, 0
     ramp_from = 0                  # the learning-rate ramp restarts at every rollback
+    n_avg = 0                      # updates of the moving average so far
     for ep in range(epochs):
         for idx in rng.permutation(len(samples)):
             s = samples[idx]
@@ -463,9 +466,10 @@ def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, se
                     rollbacks += 1
                     streak = 0
                     ramp_from = k
-                    # the averaged weights may sit above the old running mean:
-                    # restart it, or every later step would be skipped
-                    run = None
+                    # the averaged weights may sit above the old running mean
+                    # and its lowest value: restart both, or every later step
+                    # would be skipped or rolled back again
+                    run = best = None
                 continue
             streak = 0
             run = lv if run is None else 0.98 * run + 0.02 * lv
@@ -474,7 +478,7 @@ def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, se
                 if ema and run > 4.0 * best:
                     net.rollback()
                     rollbacks += 1
-                    run = best
+                    run = best = None
                     ramp_from = k
                     continue
             net.backward(s.x, s.shape)
@@ -483,7 +487,11 @@ def train(net, samples, epochs=4, lr=1e-3, lr_final=1e-4, chw=None, log=None, se
                 rate *= min(1.0, (k - ramp_from) / max(1.0, warmup * steps))
             net.step(rate)
             if ema:
-                net.ema(1.0 - 10.0 / max(steps, 20))
+                # the average spans ~the last tenth of the steps at the end, and
+                # only the updates so far early on (a rollback in the first
+                # steps then returns to recent weights, not the initial ones)
+                n_avg += 1
+                net.ema(min(1.0 - 10.0 / max(steps, 20), (1.0 + n_avg) / (10.0 + n_avg)))
             if k % 16 == 0 or k == steps:
                 losses.append((k, lv))
                 if log:

@@ -68,7 +68,7 @@ class _FakeNet:
 
     def __init__(self, losses):
         self.losses = list(losses)
-        self.rates, self.rollbacks_at, self.k = [], [], 0
+        self.rates, self.rollbacks_at, self.decays, self.k = [], [], [], 0
 
     def forward(self, x, shape):
         pass
@@ -84,7 +84,7 @@ class _FakeNet:
         self.rates.append((self.k, rate))
 
     def ema(self, decay):
-        pass
+        self.decays.append(decay)
 
     def apply_ema(self):
         pass
@@ -101,30 +101,37 @@ class _Scalar:
         return self.v
 
 
-def test_training_ramp_restarts_after_a_rollback(monkeypatch):
-    """32 non-finite losses in a row roll the weights back; the learning rate
-    then rises from the ramp's start again instead of resuming at full rate."""
+def test_training_recovers_after_a_rollback(monkeypatch):
+    """32 non-finite losses in a row roll the weights back to their average.
+    The averaged weights may score far above the best running loss; the
+    running loss and its lowest value restart, so the loop trains on instead
+    of skipping and rolling back for ever, and the learning rate rises from
+    the ramp's start again instead of resuming at full rate."""
     from types import SimpleNamespace
 
     import torch
 
     from paper_2208_05247_b300 import denoise
     monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
-    n = 400
-    losses = [1.0] * 150 + [float("nan")] * 32 + [1.0] * (n - 182)
+    n = 600
+    losses = [0.02] * 300 + [float("nan")] * 32 + [0.5] * (n - 332)
     net = _FakeNet(losses)
     samples = [SimpleNamespace(x=None, shape=None, target=None)] * n
     denoise.train(net, samples, epochs=1, lr=1e-3, lr_final=1e-3, chw=[1.0], warmup=0.1)
-    assert net.rollbacks_at == [182]
+    assert net.rollbacks_at == [332]
     assert net.train_log == {"skipped_steps": 32, "rollbacks": 1}
     rate = dict(net.rates)
     ramp = 0.1 * n
     # before: the ramp from step 1, full rate once it ends
     assert rate[1] == pytest.approx(1e-3 / ramp)
-    assert rate[150] == pytest.approx(1e-3)
-    # skipped steps take no optimizer step
-    assert not any(151 <= k <= 182 for k in rate)
-    # after the rollback at step 182 the ramp starts again
-    assert rate[183] == pytest.approx(1e-3 * 1 / ramp)
-    assert rate[200] == pytest.approx(1e-3 * 18 / ramp)
-    assert rate[182 + int(ramp)] == pytest.approx(1e-3)
+    assert rate[300] == pytest.approx(1e-3)
+    # skipped steps take no optimizer step; every step after the rollback does
+    assert not any(301 <= k <= 332 for k in rate)
+    assert all(k in rate for k in range(333, n + 1))
+    # after the rollback the ramp starts again
+    assert rate[333] == pytest.approx(1e-3 / ramp)
+    assert rate[350] == pytest.approx(1e-3 * 18 / ramp)
+    assert rate[332 + int(ramp)] == pytest.approx(1e-3)
+    # the moving average follows the weights early on: decay (1 + n) / (10 + n)
+    assert net.decays[0] == pytest.approx(2 / 11)
+    assert net.decays[-1] == pytest.approx(1 - 10 / n)
