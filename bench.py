@@ -76,6 +76,8 @@ def parse():
     p.add_argument("--denoise-eval", type=int, default=64, help="held-out scenes of the denoiser leg")
     p.add_argument("--no-l2-probe", action="store_true", help="skip the L2 read-bandwidth probe")
     p.add_argument("--denoise-epochs", type=int, default=32, help="training epochs of the denoiser leg")
+    p.add_argument("--denoise-lo-ppc", type=int, default=4,
+                   help="photons/column of the denoiser's traced input (4: the configured workload)")
     p.add_argument("--streams", type=int, default=2,
                    help="tracer handles (one stream each) that the timed steps alternate between; 1 = one after "
                         "the other")
@@ -269,13 +271,14 @@ def sweep_leg(t, coarse):
 
 def denoise_leg(args):
     """Train the 3D U-Net on tracer pairs (4 vs 1024 photons/column of one
-    quadrature point, 128^3 cumulus scenes) and time denoised 4-photon runs
-    against the plain tracer at matched RMS error of GHI and heating rate on
-    held-out scenes."""
+    quadrature point, 128^3 cumulus scenes; --denoise-lo-ppc changes the 4)
+    and time denoised runs against the plain tracer at matched RMS error of
+    GHI and heating rate on held-out scenes."""
     from paper_2208_05247_b300 import denoise
     shape = (128, 128, 128)
     t0 = time.time()
-    pairs = denoise.make_pairs(list(range(1000, 1000 + args.denoise_train)), shape, workers=os.cpu_count() or 8)
+    pairs = denoise.make_pairs(list(range(1000, 1000 + args.denoise_train)), shape, lo_ppc=args.denoise_lo_ppc,
+                               workers=os.cpu_count() or 8)
     t_pairs = time.time() - t0
     net = denoise.UNet(seed=0)
     t0 = time.time()
@@ -284,11 +287,12 @@ def denoise_leg(args):
                            chw=denoise.channel_weights(pairs, direct=False))
     t_train = time.time() - t0
     del pairs
-    res = denoise.evaluate(net, list(range(1512, 1512 + args.denoise_eval)), shape, truth_ppc=65536,
-                           workers=os.cpu_count() or 8)
+    res = denoise.evaluate(net, list(range(1512, 1512 + args.denoise_eval)), shape, lo_ppc=args.denoise_lo_ppc,
+                           truth_ppc=65536, workers=os.cpu_count() or 8)
     return {"workload": "one quadrature point on cumulus 128x128x128 (dx=dy=50 m, dz=25 m), sza 0/30/60, "
                         f"{args.denoise_eval} held-out scenes (seeds 1512-{1511 + args.denoise_eval}), "
-                        "truth 65536 photons/column, plain runs 4-16384 photons/column",
+                        f"truth 65536 photons/column, plain runs 4-16384 photons/column, traced input "
+                        f"{args.denoise_lo_ppc} photons/column",
             "fit": res["fit"], "plain_time_fit_ms": res["plain_time_fit_ms"],
             "training": {"scenes": args.denoise_train, "epochs": args.denoise_epochs, "pairs_s": t_pairs,
                          "train_s": t_train, "weights": "moving average over the last tenth of the steps",
@@ -301,6 +305,9 @@ def denoise_leg(args):
                         "ghi_basis": "like for like: the plain tracer gets the same exact direct beam "
                                      "(its time includes the direct solve), so the GHI errors differ only in "
                                      "the diffuse part"},
+            "speedup_bracket": dict(res["speedup_bracket"],
+                                    note="no fit: the measured plain runs either side of the denoised error "
+                                         "(lower, upper; None where no run lies on that side)"),
             "surface": res.get("surface"),
             "network": {"params": net.n_params(), "forward_gflop": net.flops(shape) / 1e9}}
 

@@ -531,6 +531,22 @@ def plain_time_fit(plain_ppc, ms):
     return float(t0), float(t1)
 
 
+def speedup_bracket(plain_ppc, rmse, ms, target, t_denoised, extra_ms=0.0):
+    """Speed-up bounds that need no error or time model. The plain error falls
+    and its time grows with the photon count, so the plain tracer needs more
+    photons than the largest measured run whose error is still above `target`
+    (lower bound: that run's time over the denoised time) and no more than the
+    smallest run at or below it (upper bound). `extra_ms` is added to each
+    plain time (the direct-beam solve in the like-for-like comparison).
+    Returns [low, high]; a side without such a run is None."""
+    runs = sorted(zip(plain_ppc, rmse, ms))
+    above = [m for _, e, m in runs if e > target]
+    below = [m for _, e, m in runs if e <= target]
+    low = (above[-1] + extra_ms) / t_denoised if above else None
+    high = (below[0] + extra_ms) / t_denoised if below else None
+    return [low, high]
+
+
 def plain_ppc_to_match(plain_ppc, rmse, target, truth_ppc=None):
     """Photons/column at which the plain tracer's RMSE reaches `target`.
 
@@ -683,6 +699,9 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024, 4096,
         res["plain_ppc_to_match_" + name] = ppc_match
         res["plain_ms_to_match_" + name] = t_match
         res["speedup_" + name] = t_match / res["denoised"]["ms"]
+        res.setdefault("speedup_bracket", {})[name] = speedup_bracket(
+            plain_ppc, [plain[p][key] for p in plain_ppc], [plain[p]["ms"] for p in plain_ppc],
+            res["denoised"][key], res["denoised"]["ms"])
     res["surface"] = {"direct": "network"}
     if hybrid:
         res["surface"] = {"direct": "exact pixel-mean Beer-Lambert, %d x %d points per column" % (direct_nsub,
@@ -701,6 +720,10 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024, 4096,
         res["plain_ms_to_match_ghi"] = t0 + t1 * p_dif + dms_sum / n
         res["speedup_ghi"] = res["plain_ms_to_match_ghi"] / res["denoised"]["ms"]
         res["surface"]["speedup_ghi_vs_plain_exact_direct"] = res["speedup_ghi"]
+        res["speedup_bracket"]["ghi"] = speedup_bracket(
+            plain_ppc, [math.sqrt(comp["plain%d_dif" % p] / n) for p in plain_ppc],
+            [plain[p]["ms"] for p in plain_ppc], math.sqrt(comp["den_dif"] / n), res["denoised"]["ms"],
+            extra_ms=dms_sum / n)
         # the network's own surface-direct estimate, for comparison
         p_net = plain_ppc_to_match(plain_ppc, [plain[p]["rmse_ghi"] for p in plain_ppc],
                                    math.sqrt(comp["network_ghi"] / n), truth_ppc)

@@ -135,3 +135,20 @@ def test_training_recovers_after_a_rollback(monkeypatch):
     # the moving average follows the weights early on: decay (1 + n) / (10 + n)
     assert net.decays[0] == pytest.approx(2 / 11)
     assert net.decays[-1] == pytest.approx(1 - 10 / n)
+
+
+def test_speedup_bracket_from_the_runs_either_side():
+    ppc = (4, 16, 64, 256)
+    rmse = (8.0, 4.0, 2.0, 1.0)
+    ms = (1.0, 2.0, 5.0, 17.0)
+    # target 1.5 lies between the 64- and 256-photon runs
+    assert denoise.speedup_bracket(ppc, rmse, ms, 1.5, 0.5) == [10.0, 34.0]
+    # the direct-beam solve is added to every plain time
+    assert denoise.speedup_bracket(ppc, rmse, ms, 1.5, 0.5, extra_ms=0.5) == [11.0, 35.0]
+    # an error equal to a run's counts as reached by that run
+    assert denoise.speedup_bracket(ppc, rmse, ms, 2.0, 1.0) == [2.0, 5.0]
+    # below every run: only a lower bound; above every run: only an upper one
+    assert denoise.speedup_bracket(ppc, rmse, ms, 0.5, 1.0) == [17.0, None]
+    assert denoise.speedup_bracket(ppc, rmse, ms, 9.0, 1.0) == [None, 1.0]
+    # the order of the runs does not matter
+    assert denoise.speedup_bracket(ppc[::-1], rmse[::-1], ms[::-1], 1.5, 0.5) == [10.0, 34.0]
