@@ -525,6 +525,24 @@ def heating_factor(nz, dz):
     return 86400.0 / (1.225 * np.exp(-zc / 8000.0) * 1004.0)
 
 
+def plain_time_at(plain_ppc, ms, n):
+    """Plain-tracer time at n photons/column from the measured runs, with no
+    model: linear between the two runs around n; beyond the largest run,
+    extended at the rate of the last two (the bulk rate of long launches);
+    below the smallest, that run's time (a launch lasts at least as long as
+    its longest history, whatever the photon count)."""
+    runs = sorted(zip(plain_ppc, ms))
+    if math.isinf(n):
+        return math.inf
+    if n <= runs[0][0]:
+        return runs[0][1]
+    for (p0, m0), (p1, m1) in zip(runs, runs[1:]):
+        if n <= p1:
+            return m0 + (m1 - m0) * (n - p0) / (p1 - p0)
+    (p0, m0), (p1, m1) = runs[-2], runs[-1]
+    return m1 + (m1 - m0) / (p1 - p0) * (n - p1)
+
+
 def plain_time_fit(plain_ppc, ms):
     """Least-squares line time = t0 + t1 * ppc through the plain runs' times."""
     t1, t0 = np.polyfit(np.asarray(plain_ppc, dtype=np.float64), np.asarray(ms, dtype=np.float64), 1)
@@ -589,11 +607,13 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024, 4096,
     For each held-out scene: a truth run at `truth_ppc`, plain runs at each
     of `plain_ppc` (RMSE of GHI and heating rate, and wall time of the trace
     plus field read-out, CUDA events), and the denoised run (trace at `lo_ppc`
-    + packing + network + unpacking). The plain RMSE is fitted as a t^-1/2
-    (RMSE is proportional to N^-1/2, Sec. 3.2); the speed-up is the time the
-    fitted plain tracer needs to reach the denoised RMSE divided by the
-    denoised wall time. Every RMSE is measured against the truth run, whose
-    own noise is modelled in the match (plain_ppc_to_match with truth_ppc).
+    + packing + network + unpacking). The plain RMSE is fitted as a N^-1/2
+    (Sec. 3.2) to find the photon count that reaches the denoised RMSE; the
+    plain time at that count is interpolated between the measured runs
+    (plain_time_at), and the speed-up is that time over the denoised wall
+    time. Every RMSE is measured against the truth run, whose own noise is
+    modelled in the match (plain_ppc_to_match with truth_ppc).
+    `speedup_bracket` bounds the same speed-ups with no model at all.
 
     Surface direct irradiance of the denoised product (one quadrature point,
     `exact_direct`): the expected value from the pixel-mean Beer-Lambert
@@ -686,15 +706,23 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024, 4096,
            "denoised": {"ppc": lo_ppc, "rmse_ghi": math.sqrt(den[0] / n), "rmse_hr": math.sqrt(den[1] / n),
                         "ms": den[2] / n},
            "noisy_input": {"rmse_ghi": math.sqrt(noisy[0] / n), "rmse_hr": math.sqrt(noisy[1] / n)}}
-    # plain tracer: rmse^2 = a^2 (1/ppc + 1/truth_ppc) and time = t0 + t1 ppc
+    # plain tracer: rmse^2 = a^2 (1/ppc + 1/truth_ppc); its time at a photon
+    # count interpolated between the measured runs (the least-squares line is
+    # reported for reference only: the large runs pull it away from the
+    # small ones)
     t0, t1 = plain_time_fit(plain_ppc, [plain[p]["ms"] for p in plain_ppc])
     res["plain_time_fit_ms"] = {"t0": t0, "per_ppc": t1}
+    plain_ms = [plain[p]["ms"] for p in plain_ppc]
+
+    def t_plain(n):
+        return plain_time_at(plain_ppc, plain_ms, n)
     res["fit"] = ("plain rmse^2 = a^2 (1/ppc + 1/truth_ppc), a the geometric mean over the plain runs; "
-                  "plain time = t0 + t1 ppc, least squares over the plain runs")
+                  "plain time interpolated linearly between the measured runs, extended beyond the largest "
+                  "at the rate of the last two")
     for key in ("rmse_ghi", "rmse_hr"):
         ppc_match = plain_ppc_to_match(plain_ppc, [plain[p][key] for p in plain_ppc], res["denoised"][key],
                                        truth_ppc)
-        t_match = t0 + t1 * ppc_match
+        t_match = t_plain(ppc_match)
         name = key.split("_")[1]
         res["plain_ppc_to_match_" + name] = ppc_match
         res["plain_ms_to_match_" + name] = t_match
@@ -717,7 +745,7 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024, 4096,
         p_dif = plain_ppc_to_match(plain_ppc, [math.sqrt(comp["plain%d_dif" % p] / n) for p in plain_ppc],
                                    math.sqrt(comp["den_dif"] / n), truth_ppc)
         res["plain_ppc_to_match_ghi"] = p_dif
-        res["plain_ms_to_match_ghi"] = t0 + t1 * p_dif + dms_sum / n
+        res["plain_ms_to_match_ghi"] = t_plain(p_dif) + dms_sum / n
         res["speedup_ghi"] = res["plain_ms_to_match_ghi"] / res["denoised"]["ms"]
         res["surface"]["speedup_ghi_vs_plain_exact_direct"] = res["speedup_ghi"]
         res["speedup_bracket"]["ghi"] = speedup_bracket(
@@ -727,7 +755,7 @@ def evaluate(net, seeds, shape, lo_ppc=4, plain_ppc=(4, 16, 64, 256, 1024, 4096,
         # the network's own surface-direct estimate, for comparison
         p_net = plain_ppc_to_match(plain_ppc, [plain[p]["rmse_ghi"] for p in plain_ppc],
                                    math.sqrt(comp["network_ghi"] / n), truth_ppc)
-        res["surface"]["network_only_speedup_ghi"] = (t0 + t1 * p_net) / res["denoised"]["ms"]
+        res["surface"]["network_only_speedup_ghi"] = t_plain(p_net) / res["denoised"]["ms"]
     return res
 
 

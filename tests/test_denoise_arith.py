@@ -1,7 +1,8 @@
 """The time-to-RMSE arithmetic behind the denoiser speed-ups (CPU only):
 the plain tracer's RMSE is modelled as a / sqrt(ppc) (Monte Carlo error falls
-as N^-1/2, Sec. 3.2) and its wall time as t0 + t1 * ppc. Also the training
-loop's guard bookkeeping, driven by a fake network."""
+as N^-1/2, Sec. 3.2); its wall time is interpolated between the measured
+runs (a least-squares line is reported beside it). Also the training loop's
+guard bookkeeping, driven by a fake network."""
 import math
 
 import numpy as np
@@ -152,3 +153,25 @@ def test_speedup_bracket_from_the_runs_either_side():
     assert denoise.speedup_bracket(ppc, rmse, ms, 9.0, 1.0) == [None, 1.0]
     # the order of the runs does not matter
     assert denoise.speedup_bracket(ppc[::-1], rmse[::-1], ms[::-1], 1.5, 0.5) == [10.0, 34.0]
+
+
+def test_plain_time_interpolates_between_the_runs():
+    ppc = (4, 16, 64, 256)
+    ms = (1.5, 2.0, 3.0, 7.0)
+    # at a run: its time; between two runs: linear in photons/column
+    assert denoise.plain_time_at(ppc, ms, 16) == 2.0
+    assert denoise.plain_time_at(ppc, ms, 40) == pytest.approx(2.5)
+    assert denoise.plain_time_at(ppc, ms, 160) == pytest.approx(5.0)
+    # below the smallest run: that run's time (the launch floor)
+    assert denoise.plain_time_at(ppc, ms, 1) == 1.5
+    # beyond the largest: at the rate of the last two runs (4 ms per 192)
+    assert denoise.plain_time_at(ppc, ms, 448) == pytest.approx(11.0)
+    assert denoise.plain_time_at(ppc, ms, math.inf) == math.inf
+    # measured plain times of one short evaluation: the least-squares line
+    # through them, pulled by the 16384-photon run, starts below zero
+    runs = (4, 16, 64, 256, 1024, 4096, 16384)
+    times = (1.50, 1.79, 2.47, 4.09, 10.08, 36.21, 192.79)
+    t0, t1 = denoise.plain_time_fit(runs, times)
+    assert t0 + t1 * 4 < 0.0
+    assert denoise.plain_time_at(runs, times, 4) == 1.50
+    assert denoise.plain_time_at(runs, times, 2048) == pytest.approx(10.08 + (36.21 - 10.08) / 3)
