@@ -52,8 +52,14 @@ class StepRing:
         for t, s in zip(self.ts, self.streams):
             t.set_stream(s)
         n3, n2 = self.ts[0].ncell, self.ts[0].ncol
-        self.out = [{k: torch.empty(n3 if k in ("abs3d", "hr") else n2, dtype=torch.float64, device=dev)
-                     for k in OUT_KEYS} for _ in self.ts]
+        # each handle's outputs belong to its stream in torch's allocator, so
+        # their memory is not handed out again before that stream's work on
+        # them is done
+        self.out = []
+        for s in self.streams:
+            with torch.cuda.stream(s):
+                self.out.append({k: torch.empty(n3 if k in ("abs3d", "hr") else n2, dtype=torch.float64,
+                                                device=dev) for k in OUT_KEYS})
         self.k = 0
 
     def submit(self, fields, albedo, sza, az, flux, photons, seed, photon_begin=0, photons_total=None,
@@ -63,8 +69,9 @@ class StepRing:
         accelerator build, `photons` photons from id `photon_begin` of a run of
         `photons_total`, and the fields. `events` (two CUDA events) are
         recorded around the transport launch; `after(stream, out)` runs on the
-        handle's stream once the fields are written. Returns (handle index,
-        output dict)."""
+        handle's stream once the fields are written. Inputs written on another
+        stream must be ordered first (`wait_on`). Returns (handle index, output
+        dict)."""
         torch = self.torch
         j = self.k % len(self.ts)
         t, st, o = self.ts[j], self.streams[j], self.out[j]
