@@ -574,7 +574,7 @@ def run_ours(args):
     tuned = None
     if args.launch:
         tuned = {"coarse": list(coarse), "ready_threshold": args.launch[0], "max_inner": args.launch[1],
-                 "refill_chunk": args.launch[2], "block_size": 256, "blocks_per_sm": 0}
+                 "refill_chunk": args.launch[2], "block_size": 64, "blocks_per_sm": 0}
         t.set_options(**{k: v for k, v in tuned.items() if k != "coarse"})
     elif not args.no_autotune and not args.coarse:
         # untimed: pick coarse factors and launch parameters by photons/s

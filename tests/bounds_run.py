@@ -108,6 +108,6 @@ record("coupled_step", step)
 record("noalloc", noalloc)
 big = scenes.cumulus_scene(seed=1)
 record("cumulus_256_4ppc", handle_case(big, (2, 2, 2), 4 * big.ncol))
-record("cumulus_256_64ppc_thick_first", handle_case(big, (2, 2, 2), 64 * big.ncol, ready_threshold=16,
+record("cumulus_256_64ppc_thick_first", handle_case(big, (2, 2, 2), 64 * big.ncol, ready_threshold=16, block_size=64,
                                                     max_inner=64, refill_chunk=128))
 print(json.dumps(results), flush=True)

@@ -57,7 +57,7 @@ def test_autotune_needs_a_clear_gain_to_move(monkeypatch, gain, moves):
             ms = 10.0 / (1.0 + gain)
         elif (tuple(coarse) != (2, 2, 2) or opts.get("box_levels") != 4 or opts.get("ready_threshold") != 16
               or opts.get("max_inner") != 64 or opts.get("refill_min") != 8 or opts.get("refill_chunk") != 128
-              or opts.get("block_size") != 256 or opts.get("blocks_per_sm") != 0):
+              or opts.get("block_size") != 64 or opts.get("blocks_per_sm") != 0):
             ms = 12.0
         return ms, {"events": 1000, "crossings": 3000}
     monkeypatch.setattr(autotune, "time_config", fake_time)

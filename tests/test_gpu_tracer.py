@@ -543,7 +543,7 @@ def test_fullsize_cumulus_direct_beam_and_closure(c1_scene):
 # --- parity with the oracle on the full 256x256x128 cumulus scene -------------------
 
 # the benchmark's launch configuration (majorant boxes on a 2x2x2 grid)
-C1_LAUNCH = dict(ready_threshold=16, max_inner=64, refill_chunk=128)
+C1_LAUNCH = dict(ready_threshold=16, max_inner=64, refill_chunk=128, block_size=64)
 C1_PPC, C1_B, C1_PILOT = 64, 16, 8
 
 
