@@ -10,7 +10,6 @@ fit that array are rejected with a clear error.
 
 This file is collected last on purpose.
 """
-import ctypes
 
 import numpy as np
 import pytest
