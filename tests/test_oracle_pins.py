@@ -439,3 +439,69 @@ def test_sobol_birth_is_unbiased_and_stratifies_the_direct_beam(small_scene):
         assert abs(m.mean() - truth.mean()) < 4 * se + 1e-9, birth
         err[birth] = np.sqrt(((r - truth) ** 2).mean())
     assert err["sobol"] < 0.7 * err["philox"], err
+
+
+# --- symmetries of the periodic domain ------------------------------------------------
+
+_SYM_FIELDS = ("abs_dir", "abs_dif", "sfc_dir", "sfc_dif", "toa_up")
+
+
+def _oracle_batches(scene, sza, az, photons, seeds):
+    out = {f: [] for f in _SYM_FIELDS}
+    for s in seeds:
+        r = oracle.trace(scene, sza, az, 1000.0, photons, s)
+        for k in _SYM_FIELDS:
+            out[k].append(getattr(r, k))
+    return {k: np.stack(v) for k, v in out.items()}
+
+
+def _with_fields(scene, fn):
+    """A copy of `scene` with `fn` applied to every optics field ([nz][ny][nx])
+    and to the albedo ([ny][nx])."""
+    import copy
+    sc = copy.deepcopy(scene)
+    for name in ("k_gas", "ssa_gas", "k_cld", "ssa_cld", "g_cld"):
+        setattr(sc, name, np.ascontiguousarray(fn(getattr(scene, name))))
+    sc.albedo = np.ascontiguousarray(fn(scene.albedo[None])[0])
+    return sc
+
+
+def _assert_same_expectation(a, b, pa, pb):
+    for field in _SYM_FIELDS:
+        rep = refs.parity_report(a[field], b[field], pilot=(pa[field], pb[field]))
+        assert rep["frac_over"] <= rep["bound"], (field, rep["frac_over"], rep["bound"])
+        assert rep["pooled_p_family"] >= 1e-3, (field, rep["pooled_p_family"])
+        assert abs(rep["domain_rel"]) < 4 * rep["domain_rel_se"] + 1e-9, (field, rep["domain_rel"])
+
+
+def test_oracle_overhead_sun_commutes_with_swapping_x_and_y():
+    """With the sun overhead no horizontal axis is preferred: the x-y transposed
+    scene gives the transposed fields (independent batches, the parity
+    statistic). A swapped index or spacing in the fine-cell walk fails it."""
+    sc = scenes.ellipsoid_scene(seed=3)
+    sw = _with_fields(sc, lambda a: np.swapaxes(a, -1, -2))
+    sw.nx, sw.ny, sw.dx, sw.dy = sc.ny, sc.nx, sc.dy, sc.dx
+    n = 2 ** 20
+    a = _oracle_batches(sc, 0.0, 0.0, n, range(3100, 3116))
+    b = _oracle_batches(sw, 0.0, 0.0, n, range(3200, 3216))
+    pa = _oracle_batches(sc, 0.0, 0.0, n, range(3300, 3308))
+    pb = _oracle_batches(sw, 0.0, 0.0, n, range(3400, 3408))
+    t = lambda d: {k: np.swapaxes(v, -1, -2) for k, v in d.items()}   # noqa: E731
+    _assert_same_expectation(t(b), a, t(pb), pa)
+
+
+def test_oracle_scene_rolled_by_whole_cells_gives_rolled_fields():
+    """Periodic x and y: rolling the scene by (11, 5) cells, which carries the
+    clouds across both lateral edges, rolls the fields by the same cells under
+    a slanted sun whose paths cross the edges. A wrong wrap in the walk or in
+    the birth column fails it."""
+    sc = scenes.ellipsoid_scene(seed=2)
+    dy, dx = 5, 11
+    sh = _with_fields(sc, lambda a: np.roll(a, (dy, dx), axis=(-2, -1)))
+    n = 2 ** 20
+    a = _oracle_batches(sc, 45.0, 60.0, n, range(3500, 3516))
+    b = _oracle_batches(sh, 45.0, 60.0, n, range(3600, 3616))
+    pa = _oracle_batches(sc, 45.0, 60.0, n, range(3700, 3708))
+    pb = _oracle_batches(sh, 45.0, 60.0, n, range(3800, 3808))
+    back = lambda d: {k: np.roll(v, (-dy, -dx), axis=(-2, -1)) for k, v in d.items()}   # noqa: E731
+    _assert_same_expectation(back(b), a, back(pb), pa)
