@@ -481,11 +481,11 @@ def test_oracle_overhead_sun_commutes_with_swapping_x_and_y():
     sc = scenes.ellipsoid_scene(seed=3)
     sw = _with_fields(sc, lambda a: np.swapaxes(a, -1, -2))
     sw.nx, sw.ny, sw.dx, sw.dy = sc.ny, sc.nx, sc.dy, sc.dx
-    n = 2 ** 20
-    a = _oracle_batches(sc, 0.0, 0.0, n, range(3100, 3116))
-    b = _oracle_batches(sw, 0.0, 0.0, n, range(3200, 3216))
-    pa = _oracle_batches(sc, 0.0, 0.0, n, range(3300, 3308))
-    pb = _oracle_batches(sw, 0.0, 0.0, n, range(3400, 3408))
+    n = 2 ** 19
+    a = _oracle_batches(sc, 0.0, 0.0, n, range(3100, 3112))
+    b = _oracle_batches(sw, 0.0, 0.0, n, range(3200, 3212))
+    pa = _oracle_batches(sc, 0.0, 0.0, n, range(3300, 3306))
+    pb = _oracle_batches(sw, 0.0, 0.0, n, range(3400, 3406))
     t = lambda d: {k: np.swapaxes(v, -1, -2) for k, v in d.items()}   # noqa: E731
     _assert_same_expectation(t(b), a, t(pb), pa)
 
@@ -498,10 +498,10 @@ def test_oracle_scene_rolled_by_whole_cells_gives_rolled_fields():
     sc = scenes.ellipsoid_scene(seed=2)
     dy, dx = 5, 11
     sh = _with_fields(sc, lambda a: np.roll(a, (dy, dx), axis=(-2, -1)))
-    n = 2 ** 20
-    a = _oracle_batches(sc, 45.0, 60.0, n, range(3500, 3516))
-    b = _oracle_batches(sh, 45.0, 60.0, n, range(3600, 3616))
-    pa = _oracle_batches(sc, 45.0, 60.0, n, range(3700, 3708))
-    pb = _oracle_batches(sh, 45.0, 60.0, n, range(3800, 3808))
+    n = 2 ** 19
+    a = _oracle_batches(sc, 45.0, 60.0, n, range(3500, 3512))
+    b = _oracle_batches(sh, 45.0, 60.0, n, range(3600, 3612))
+    pa = _oracle_batches(sc, 45.0, 60.0, n, range(3700, 3706))
+    pb = _oracle_batches(sh, 45.0, 60.0, n, range(3800, 3806))
     back = lambda d: {k: np.roll(v, (-dy, -dx), axis=(-2, -1)) for k, v in d.items()}   # noqa: E731
     _assert_same_expectation(back(b), a, back(pb), pa)
