@@ -38,7 +38,7 @@ def _compare(got_list, want):
             assert np.allclose(got, w[k], rtol=1e-12, atol=1e-12 * scale), k
 
 
-@pytest.mark.parametrize("handles", [1, 2])
+@pytest.mark.parametrize("handles", [1, 2, 3])
 def test_pipelined_steps_equal_sequential_calls(small_scene, handles):
     sc = small_scene
     N = 64 * sc.ncol
