@@ -40,7 +40,9 @@ class StepRing:
     """Steps on device-resident inputs, alternating between the given Tracer
     handles (one stream each; two are enough to cover the tail). Step k runs
     on handle k mod len(tracers) and writes that handle's own output buffers,
-    which stay valid until the handle's next step is submitted."""
+    which stay valid until the handle's next step is submitted. The handles
+    keep the ring's streams: give them another one (Tracer.set_stream) before
+    using them outside the ring."""
 
     def __init__(self, tracers, coarse=(0, 0, 0)):
         import torch
@@ -110,7 +112,9 @@ class StepRing:
 class HostPipeline:
     """Pipelined steps of one Tracer, or alternating between several (one
     stream each). Host buffers must be pinned (torch tensors with
-    pin_memory()) for the copies to overlap."""
+    pin_memory()) for the copies to overlap. The device buffers serve several
+    streams: call synchronize() before dropping the pipeline, so that no copy
+    or kernel still uses them when torch's allocator takes them back."""
 
     def __init__(self, tracers, coarse=(0, 0, 0)):
         import torch
